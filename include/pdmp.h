@@ -1,0 +1,190 @@
+/*
+ * pdmp.h -- C ABI of libpdmp, the GB300 (sm_103a) library for the sample-
+ * morphing hot path of "Parallelised Diffeomorphic Sampling-based Motion
+ * Planning" (Lai, Zhi, Hermans, Ramos; arXiv 2108.11775).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Memory     Array arguments are DEVICE pointers unless a comment says "host".
+ *            Float arrays are float32, row-major, torch-contiguous: a batch of
+ *            N points in d dimensions is N x d with the d coordinates of a point
+ *            adjacent.  The caller owns every buffer, including workspaces; the
+ *            library allocates no device memory.
+ * Alignment  Every device array must be 16-byte aligned (cudaMalloc and torch
+ *            allocations are).  Misaligned pointers give PDMP_ERR_INVALID_ARG.
+ * Ordering   Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *            legacy default stream) unless it says it synchronises.  Arguments
+ *            are validated on the host before anything is launched; a call that
+ *            returns an error has launched nothing.
+ * Errors     Each call returns a pdmp_status.  Errors raised while kernels run
+ *            are reported by pdmp_stream_status().  No kernel traps.
+ *
+ * The occupancy field (Sec. 3.1)
+ * ------------------------------
+ * c(x) = sigmoid(s(x)),  s(x) = sum_m w_m phi_m(x) + bias,  with
+ *   RBF  phi_m(x) = exp(-gamma |x - mu_m|^2)       (centres = mu, M x d)
+ *   RFF  phi_m(x) = cos(omega_m . x + b_m)          (centres = omega, M x d;
+ *                                                    phase = b, M)
+ * The map (Sec. 3.2, Eq. 1 integrated with Euler's method):
+ *   x_{t+1} = x_t - eta * grad c(x_t),  t = 0 .. T-1.
+ * Each step is a diffeomorphism when eta * L < 1, L a Lipschitz constant of
+ * grad c (Sec. 3.2: Picard-Lindelof needs a Lipschitz gradient).
+ */
+#ifndef PDMP_H
+#define PDMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pdmp_status;
+
+#define PDMP_OK                       0
+#define PDMP_ERR_INVALID_ARG          1  /* bad size, pointer, alignment or option */
+#define PDMP_ERR_STEP_TOO_LARGE       2  /* eta * L >= 1 for a field that carries L */
+#define PDMP_ERR_WORKSPACE_TOO_SMALL  3
+#define PDMP_ERR_CUDA                 4  /* a CUDA runtime call failed */
+#define PDMP_ERR_NOT_CONVERGED        5
+#define PDMP_ERR_TIMEOUT              6
+#define PDMP_ERR_DEVICE_FLAG          7  /* a kernel recorded a numerical failure */
+#define PDMP_ERR_UNSUPPORTED          8  /* valid request this build does not handle */
+
+#define PDMP_KIND_RBF 0
+#define PDMP_KIND_RFF 1
+
+/* The learned occupancy field.  All pointers are device pointers to float32.
+ * RBF: d in {1, 2, 3}.  RFF: 1 <= d <= 8.  M >= 1.
+ * `lipschitz` is optional: when > 0 it is a bound L on |Hess c|_2 over the
+ * region the samples visit, and calls that take a step size reject
+ * eta * L >= 1 with PDMP_ERR_STEP_TOO_LARGE. */
+typedef struct {
+  int32_t kind;            /* PDMP_KIND_RBF or PDMP_KIND_RFF */
+  int32_t d;               /* dimension of x */
+  int64_t M;               /* number of features */
+  const float* centres;    /* RBF: mu (M x d).  RFF: omega (M x d) */
+  const float* phase;      /* RFF: b (M).  RBF: must be NULL */
+  float gamma;             /* RBF width (> 0).  RFF: ignored */
+  const float* w;          /* M feature weights */
+  float bias;              /* logit bias */
+  double lipschitz;        /* 0, or a bound on |Hess c| checked against eta */
+} pdmp_field;
+
+/* Static, NUL-terminated description of a status code (never NULL). */
+const char* pdmp_status_string(pdmp_status s);
+
+/* Library version, as major * 10000 + minor * 100 + patch. */
+int32_t pdmp_version(void);
+
+/* Synchronises `stream`, then reports the first error raised on it since the
+ * previous call: a CUDA error (PDMP_ERR_CUDA) or a numerical failure a kernel
+ * recorded in the library's device flag (PDMP_ERR_DEVICE_FLAG; the flag is
+ * cleared by this call).  *detail (host, may be NULL) receives the CUDA error
+ * code or the flag value. */
+pdmp_status pdmp_stream_status(void* stream, int32_t* detail);
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 3.2 (Eq. 1, "Drawing Samples"): morph a batch of base samples.      */
+/* ---------------------------------------------------------------------- */
+/* x0: N x d base samples.  xT: N x d output; may alias x0 exactly (in place).
+ * T >= 0 Euler steps of size eta > 0.  N = 0 or T = 0 are valid (T = 0
+ * copies x0 to xT).
+ * ckpt: NULL, or a (T/k) x N x d buffer that receives x_{k}, x_{2k}, ..., x_T
+ * (checkpoints for pdmp_morph_vjp); then k >= 1 must divide T.
+ * Sample state lives in registers for all T steps; features are evaluated
+ * in FP32 with exp2 / sin / cos on the special-function unit. */
+pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta,
+                       float* xT, float* ckpt, int32_t k, void* stream);
+
+/* Diagnostic twin of pdmp_morph with the same kernel arithmetic: traj
+ * ((T+1) x N x d) receives x_0 .. x_T and steps (T x N x d) the FP32 increment
+ * -eta sigma'(s) grad s(x_t) of every step as computed, before it is added
+ * to x_t (so that the accuracy of a step can be checked apart from the
+ * rounding of the float32 state).  steps may be NULL only when T = 0. */
+pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* traj,
+                             float* steps, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Chain rule through Eq. (1): vector-Jacobian product of the T-step map.   */
+/* ---------------------------------------------------------------------- */
+/* g0[n] = (d x_T / d x_0)^T gT[n] for every sample, computed backwards as
+ * g_t = (I - eta Hess c(x_t)) g_{t+1} with Hessian-vector products.
+ * Intermediate states are recomputed segment by segment from checkpoints:
+ * ckpt is the buffer pdmp_morph filled with the same (f, x0, T, eta, k), or
+ * NULL to recompute each segment from x0.  k >= 1 must divide T.
+ * gw: NULL, or an M vector that receives d/dw of sum_n <gT[n], x_T[n]>
+ * (overwritten, not accumulated); gbias: NULL or one float, likewise for the
+ * bias.  Both need the workspace: ws must hold pdmp_morph_vjp_workspace(...)
+ * bytes (0 when gw and gbias are NULL, and then ws may be NULL). */
+size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32_t k, int32_t want_param_grad);
+pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, int32_t k,
+                           const float* ckpt, const float* gT, float* g0, float* gw, float* gbias,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 3.2 ("Drawing Samples"): log-determinant of the map's Jacobian.     */
+/* ---------------------------------------------------------------------- */
+/* logdet[n] = sum_t log det(I - eta Hess c(x_t)) for sample n; xT (N x d, may
+ * be NULL) receives x_T.  I - eta Hess c is symmetric positive definite when
+ * eta L < 1; a step where it is not records a device flag (read with
+ * pdmp_stream_status) and that sample's logdet is NaN. */
+pdmp_status pdmp_logdet(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta,
+                        float* logdet, float* xT, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 3.1: occupancy queries and ground-truth labels.                     */
+/* ---------------------------------------------------------------------- */
+/* c (N, may be NULL) = sigmoid(s(x)); s (N, may be NULL) = s(x);
+ * grad (N x d, may be NULL) = grad c(x). */
+pdmp_status pdmp_occupancy_query(const pdmp_field* f, const float* x, int64_t N, float* c, float* s, float* grad,
+                                 void* stream);
+
+/* label[n] = 1 iff x[n] lies in some closed axis-aligned box:
+ * lo_j <= x_j <= hi_j on every axis, compared exactly in float32.
+ * boxes: nb x 2d (lo_0..lo_{d-1}, hi_0..hi_{d-1}); nb >= 0; 1 <= d <= 8. */
+pdmp_status pdmp_box_labels(int32_t d, const float* boxes, int64_t nb, const float* x, int64_t N, uint8_t* label,
+                            void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 3.2: a certified Lipschitz constant of grad c, which sets eta < 1/L. */
+/* ---------------------------------------------------------------------- */
+/* Computed in FP64 on the device, then copied to the host (this call
+ * synchronises `stream`).
+ *   |Hess c| <= |Hess s| / 4 + |grad s|^2 / (6 sqrt 3).
+ * RBF: |grad phi_m| and |Hess phi_m| are radial functions of r = |x - mu_m|;
+ * the box [lo, hi] (host, d doubles each) is cut into cells^d cells, each
+ * radial factor is replaced by its maximum over the cell's range of r, and the
+ * bound is the maximum over cells.  1 <= cells and cells^d <= 2^24.
+ * RFF: |grad phi_m| <= |omega_m|, |Hess phi_m| <= |omega_m|^2 everywhere;
+ * lo, hi and cells are ignored.
+ * L (host) receives the bound on |Hess c|_2, G (host, may be NULL) a bound
+ * on |grad c|_2 over the same region. */
+pdmp_status pdmp_lipschitz_bound(const pdmp_field* f, const double* lo, const double* hi, int32_t cells, double* L,
+                                 double* G, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 3.1: fit the weights to labelled occupancy points (BCE, gradient     */
+/* descent).                                                                */
+/* ---------------------------------------------------------------------- */
+/* Minimises mean_i BCE(sigmoid(s(X_i)), y_i) + (l2 / 2) |w|^2 over w and the
+ * bias, starting from zero.  The step is alpha = 1 / (lambda / 4 + l2), where
+ * lambda estimates the top eigenvalue of (1/n) [Phi 1]^T [Phi 1] by
+ * power_iters power iterations from the normalised all-ones vector; then
+ * `iters` Nesterov iterations  v = w_k + (k-1)/(k+2) (w_k - w_{k-1}),
+ * w_{k+1} = v - alpha grad(v).
+ * f gives kind, d, M, centres, phase and gamma; f->w and f->bias are ignored.
+ * X: n x d points, y: n labels in {0, 1}.  w_out: M (device).  bias_out,
+ * loss_out (final objective), alpha_out: host, each may be NULL; when any is
+ * given the call synchronises `stream`.
+ * ws must hold pdmp_fit_workspace(M, n) bytes. */
+size_t pdmp_fit_workspace(int64_t M, int64_t n);
+pdmp_status pdmp_fit_occupancy(const pdmp_field* f, const float* X, const uint8_t* y, int64_t n, float l2,
+                               int32_t power_iters, int32_t iters, float* w_out, float* bias_out, float* loss_out,
+                               float* alpha_out, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDMP_H */

@@ -1,0 +1,235 @@
+// extern "C" entry points of libpdmp: argument validation on the host, then
+// the launchers in the other translation units.  Nothing here computes.
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace pdmp {
+__device__ int32_t g_device_flag = 0;
+}
+
+using namespace pdmp_host;
+
+namespace pdmp_host {
+
+pdmp_status check_field(const pdmp_field* f) {
+  if (f == nullptr) return PDMP_ERR_INVALID_ARG;
+  if (f->M < 1) return PDMP_ERR_INVALID_ARG;
+  if (f->kind == PDMP_KIND_RBF) {
+    if (f->d < 1 || f->d > 3) return PDMP_ERR_INVALID_ARG;
+    if (!(f->gamma > 0.0f) || !std::isfinite(f->gamma)) return PDMP_ERR_INVALID_ARG;
+    if (f->phase != nullptr) return PDMP_ERR_INVALID_ARG;
+  } else if (f->kind == PDMP_KIND_RFF) {
+    if (f->d < 1 || f->d > 8) return PDMP_ERR_INVALID_ARG;
+    if (!ok_ptr(f->phase, true)) return PDMP_ERR_INVALID_ARG;
+  } else {
+    return PDMP_ERR_INVALID_ARG;
+  }
+  if (!ok_ptr(f->centres, true) || !ok_ptr(f->w, true)) return PDMP_ERR_INVALID_ARG;
+  if (!std::isfinite(f->bias)) return PDMP_ERR_INVALID_ARG;
+  if (f->lipschitz < 0.0 || std::isnan(f->lipschitz)) return PDMP_ERR_INVALID_ARG;
+  return PDMP_OK;
+}
+
+pdmp_status check_step(const pdmp_field* f, float eta) {
+  if (!(eta > 0.0f) || !std::isfinite(eta)) return PDMP_ERR_INVALID_ARG;
+  if (f->lipschitz > 0.0 && (double)eta * f->lipschitz >= 1.0) return PDMP_ERR_STEP_TOO_LARGE;
+  return PDMP_OK;
+}
+
+}  // namespace pdmp_host
+
+static pdmp::FieldArgs field_args(const pdmp_field* f) {
+  pdmp::FieldArgs a;
+  a.centres = f->centres;
+  a.phase = f->phase;
+  a.w = f->w;
+  a.M = f->M;
+  a.gamma = f->gamma;
+  a.bias = f->bias;
+  return a;
+}
+
+static inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char* pdmp_status_string(pdmp_status s) {
+  switch (s) {
+    case PDMP_OK: return "ok";
+    case PDMP_ERR_INVALID_ARG: return "invalid argument";
+    case PDMP_ERR_STEP_TOO_LARGE: return "step too large: eta * L >= 1 breaks the diffeomorphism";
+    case PDMP_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case PDMP_ERR_CUDA: return "CUDA runtime error";
+    case PDMP_ERR_NOT_CONVERGED: return "not converged";
+    case PDMP_ERR_TIMEOUT: return "timed out";
+    case PDMP_ERR_DEVICE_FLAG: return "a kernel recorded a numerical failure";
+    case PDMP_ERR_UNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+int32_t pdmp_version(void) { return 100; }
+
+pdmp_status pdmp_stream_status(void* stream, int32_t* detail) {
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (detail) *detail = (int32_t)e;
+    return PDMP_ERR_CUDA;
+  }
+  int32_t flag = 0, zero = 0;
+  e = cudaMemcpyFromSymbolAsync(&flag, pdmp::g_device_flag, sizeof(flag), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(pdmp::g_device_flag, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    if (detail) *detail = (int32_t)e;
+    return PDMP_ERR_CUDA;
+  }
+  if (detail) *detail = flag;
+  return flag ? PDMP_ERR_DEVICE_FLAG : PDMP_OK;
+}
+
+pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* xT,
+                       float* ckpt, int32_t k, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0) return PDMP_ERR_INVALID_ARG;
+  if (ckpt != nullptr && (k < 1 || T % k != 0)) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || !ok_ptr(ckpt, false)) return PDMP_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  if (T == 0) {
+    if (xT != x0) return cuda_status(cudaMemcpyAsync(xT, x0, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st));
+    return PDMP_OK;
+  }
+  return cuda_status(pdmp::morph_dispatch(f->kind, f->d, field_args(f), x0, N, T, eta, xT, ckpt, k, nullptr,
+                                          nullptr, st));
+}
+
+pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* traj,
+                             float* steps, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(traj, true) || !ok_ptr(steps, T > 0)) return PDMP_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  if (T == 0) return cuda_status(cudaMemcpyAsync(traj, x0, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st));
+  return cuda_status(pdmp::morph_dispatch(f->kind, f->d, field_args(f), x0, N, T, eta, nullptr, nullptr, 0, traj,
+                                          steps, st));
+}
+
+size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32_t k, int32_t want_param_grad) {
+  (void)T;
+  (void)k;
+  if (f == nullptr || !want_param_grad || N <= 0 || f->M < 1) return 0;
+  return sizeof(float) * (size_t)pdmp::vjp_blocks(N) * (size_t)(f->M + 1);
+}
+
+pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, int32_t k,
+                           const float* ckpt, const float* gT, float* g0, float* gw, float* gbias, void* ws,
+                           size_t ws_bytes, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0 || k < 1 || k > pdmp::kMaxSegment || T % k != 0) return PDMP_ERR_INVALID_ARG;
+  if (!ok_ptr(ckpt, false) || !ok_ptr(gw, false) || !ok_ptr(gbias, false)) return PDMP_ERR_INVALID_ARG;
+  const bool want = gw != nullptr || gbias != nullptr;
+  if (want) {
+    size_t need = pdmp_morph_vjp_workspace(f, N, T, k, 1);
+    if (need > 0 && (ws == nullptr || !aligned16(ws))) return PDMP_ERR_INVALID_ARG;
+    if (ws_bytes < need) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  }
+  cudaStream_t st = as_stream(stream);
+  if (N > 0) {
+    if (!ok_ptr(x0, true) || !ok_ptr(gT, true) || !ok_ptr(g0, true)) return PDMP_ERR_INVALID_ARG;
+  }
+  if (T == 0) {
+    if (N > 0 && g0 != gT) {
+      cudaError_t e = cudaMemcpyAsync(g0, gT, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return PDMP_ERR_CUDA;
+    }
+    if (gw) cudaMemsetAsync(gw, 0, sizeof(float) * f->M, st);
+    if (gbias) cudaMemsetAsync(gbias, 0, sizeof(float), st);
+    return launch_status();
+  }
+  return cuda_status(pdmp::morph_vjp(f->kind, f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0,
+                                     want ? (float*)ws : nullptr, gw, gbias, st));
+}
+
+pdmp_status pdmp_logdet(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* logdet,
+                        float* xT, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(logdet, true) || !ok_ptr(xT, false)) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::logdet(f->kind, f->d, field_args(f), x0, N, T, eta, logdet, xT, as_stream(stream)));
+}
+
+pdmp_status pdmp_occupancy_query(const pdmp_field* f, const float* x, int64_t N, float* c, float* s_out, float* grad,
+                                 void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if (N < 0) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x, true) || !ok_ptr(c, false) || !ok_ptr(s_out, false) || !ok_ptr(grad, false))
+    return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::occupancy_query(f->kind, f->d, field_args(f), x, N, c, s_out, grad, as_stream(stream)));
+}
+
+pdmp_status pdmp_box_labels(int32_t d, const float* boxes, int64_t nb, const float* x, int64_t N, uint8_t* label,
+                            void* stream) {
+  if (d < 1 || d > 8 || nb < 0 || N < 0) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x, true) || !ok_ptr(label, true) || !ok_ptr(boxes, nb > 0)) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::box_labels(d, boxes, nb, x, N, label, as_stream(stream)));
+}
+
+pdmp_status pdmp_lipschitz_bound(const pdmp_field* f, const double* lo, const double* hi, int32_t cells, double* L,
+                                 double* G, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if (L == nullptr) return PDMP_ERR_INVALID_ARG;
+  if (f->kind == PDMP_KIND_RBF) {
+    if (lo == nullptr || hi == nullptr || cells < 1) return PDMP_ERR_INVALID_ARG;
+    double ncells = 1.0;
+    for (int j = 0; j < f->d; ++j) {
+      if (!(hi[j] > lo[j]) || !std::isfinite(lo[j]) || !std::isfinite(hi[j])) return PDMP_ERR_INVALID_ARG;
+      ncells *= cells;
+    }
+    if (ncells > (double)(1 << 24)) return PDMP_ERR_INVALID_ARG;
+  }
+  return cuda_status(pdmp::lipschitz_bound(f->kind, f->d, field_args(f), lo, hi, cells, L, G, as_stream(stream)));
+}
+
+size_t pdmp_fit_workspace(int64_t M, int64_t n) {
+  if (M < 1 || n < 1) return 0;
+  return pdmp::fit_workspace(M, n);
+}
+
+pdmp_status pdmp_fit_occupancy(const pdmp_field* f, const float* X, const uint8_t* y, int64_t n, float l2,
+                               int32_t power_iters, int32_t iters, float* w_out, float* bias_out, float* loss_out,
+                               float* alpha_out, void* ws, size_t ws_bytes, void* stream) {
+  if (f == nullptr) return PDMP_ERR_INVALID_ARG;
+  pdmp_field g = *f;
+  g.w = w_out;  // the fit ignores f->w; validate the geometry with the output in its place
+  g.bias = 0.0f;
+  g.lipschitz = 0.0;
+  pdmp_status s = check_field(&g);
+  if (s != PDMP_OK) return s;
+  if (n < 1 || power_iters < 1 || iters < 0 || !(l2 >= 0.0f) || !std::isfinite(l2)) return PDMP_ERR_INVALID_ARG;
+  if (!ok_ptr(X, true) || !ok_ptr(y, true) || !ok_ptr(w_out, true)) return PDMP_ERR_INVALID_ARG;
+  if (ws == nullptr || !aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::fit_workspace(g.M, n)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  return cuda_status(pdmp::fit_occupancy(g.kind, g.d, field_args(&g), X, y, n, l2, power_iters, iters, w_out,
+                                         bias_out, loss_out, alpha_out, ws, as_stream(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+"""The C ABI: the library loads without a GPU, exports every function the
+header declares, and rejects bad arguments on the host before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2108_11775_gb300 as pdmp
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "pdmp.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(pdmp_[a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for must in ("pdmp_morph", "pdmp_morph_vjp", "pdmp_logdet", "pdmp_fit_occupancy", "pdmp_lipschitz_bound",
+                 "pdmp_box_labels", "pdmp_occupancy_query", "pdmp_status_string", "pdmp_stream_status"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = pdmp.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), f"{name} declared in pdmp.h but not exported"
+
+
+def test_status_strings():
+    L = pdmp.lib()
+    for s in range(0, 9):
+        assert L.pdmp_status_string(s)
+    assert L.pdmp_status_string(12345) == b"unknown status"
+    assert L.pdmp_version() >= 100
+
+
+# Fake, never-dereferenced device addresses: every call below fails host
+# validation before any CUDA call.  They run only where no GPU is visible, so
+# that a validation gap can never turn into a launch on a bogus pointer.
+import torch
+
+nogpu = pytest.mark.skipif(torch.cuda.is_available(), reason="fake-pointer validation tests run without a GPU only")
+A = 1 << 20          # 16-byte aligned
+MIS = (1 << 20) + 4  # misaligned
+
+
+def fld(kind=0, d=2, M=16, gamma=4.0, centres=A, w=A, phase=None, lipschitz=0.0):
+    f = pdmp._Field()
+    f.kind, f.d, f.M, f.gamma, f.bias, f.lipschitz = kind, d, M, gamma, 0.0, lipschitz
+    f.centres, f.w, f.phase = centres, w, phase
+    return f
+
+
+def morph_call(f, x0=A, N=8, T=4, eta=0.01, xT=A, ckpt=None, k=0):
+    return pdmp.lib().pdmp_morph(ctypes.byref(f), x0, N, T, eta, xT, ckpt, k, None)
+
+
+@nogpu
+@pytest.mark.parametrize("bad", [
+    dict(M=0), dict(d=4), dict(d=0), dict(kind=2), dict(gamma=0.0), dict(gamma=float("nan")),
+    dict(centres=None), dict(centres=MIS), dict(w=MIS), dict(phase=A), dict(lipschitz=-1.0),
+])
+def test_morph_rejects_bad_rbf_fields(bad):
+    assert morph_call(fld(**bad)) == 1
+
+
+@nogpu
+def test_rff_field_needs_phase_and_allows_d8():
+    assert morph_call(fld(kind=1, d=7, phase=None)) == 1
+    assert morph_call(fld(kind=1, d=9, phase=A)) == 1
+    assert morph_call(fld(kind=1, d=8, phase=MIS)) == 1
+
+
+@nogpu
+@pytest.mark.parametrize("kw,code", [
+    (dict(N=-1), 1), (dict(T=-1), 1), (dict(eta=0.0), 1), (dict(eta=-1.0), 1), (dict(eta=float("inf")), 1),
+    (dict(x0=MIS), 1), (dict(xT=None), 1), (dict(ckpt=A, k=3), 1), (dict(ckpt=A, k=0), 1), (dict(ckpt=MIS, k=2), 1),
+])
+def test_morph_rejects_bad_arguments(kw, code):
+    assert morph_call(fld(), **kw) == code
+
+
+@nogpu
+def test_step_too_large_when_field_carries_L():
+    assert morph_call(fld(lipschitz=100.0), eta=0.0101) == 2
+    assert morph_call(fld(lipschitz=100.0), eta=0.5) == 2
+
+
+@nogpu
+def test_empty_batch_is_a_noop():
+    assert morph_call(fld(), N=0, x0=None, xT=None) == 0
+
+
+@nogpu
+def test_vjp_validation():
+    L = pdmp.lib()
+    f = fld()
+    # k must divide T and be at most the longest segment
+    assert L.pdmp_morph_vjp(ctypes.byref(f), A, 8, 10, 0.01, 3, None, A, A, None, None, None, 0, None) == 1
+    assert L.pdmp_morph_vjp(ctypes.byref(f), A, 8, 64, 0.01, 64, None, A, A, None, None, None, 0, None) == 1
+    need = L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 1)
+    assert need > 0
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 0) == 0
+    assert L.pdmp_morph_vjp(ctypes.byref(f), A, 1000, 10, 0.01, 5, None, A, A, A, None, A, need - 1, None) == 3
+    assert L.pdmp_morph_vjp(ctypes.byref(f), A, 1000, 10, 0.01, 5, None, A, A, A, None, None, need, None) == 1
+
+
+@nogpu
+def test_fit_and_lipschitz_validation():
+    L = pdmp.lib()
+    f = fld()
+    assert L.pdmp_fit_workspace(16, 100) > 0
+    ws = L.pdmp_fit_workspace(16, 100)
+    assert L.pdmp_fit_occupancy(ctypes.byref(f), A, A, 100, 1e-3, 0, 10, A, None, None, None, A, ws, None) == 1
+    assert L.pdmp_fit_occupancy(ctypes.byref(f), A, A, 100, 1e-3, 5, 10, A, None, None, None, A, ws - 1, None) == 3
+    assert L.pdmp_fit_occupancy(ctypes.byref(f), A, A, 0, 1e-3, 5, 10, A, None, None, None, A, ws, None) == 1
+    Lo = ctypes.c_double(0)
+    lo = (ctypes.c_double * 2)(0, 0)
+    hi = (ctypes.c_double * 2)(10, 0)      # empty extent on axis 1
+    assert L.pdmp_lipschitz_bound(ctypes.byref(f), lo, hi, 8, ctypes.byref(Lo), None, None) == 1
+    hi = (ctypes.c_double * 2)(10, 10)
+    assert L.pdmp_lipschitz_bound(ctypes.byref(f), lo, hi, 0, ctypes.byref(Lo), None, None) == 1
+    assert L.pdmp_lipschitz_bound(ctypes.byref(f), lo, hi, 5000, ctypes.byref(Lo), None, None) == 1
+
+
+@nogpu
+def test_labels_validation():
+    L = pdmp.lib()
+    assert L.pdmp_box_labels(0, A, 1, A, 10, A, None) == 1
+    assert L.pdmp_box_labels(9, A, 1, A, 10, A, None) == 1
+    assert L.pdmp_box_labels(2, None, 3, A, 10, A, None) == 1
+    assert L.pdmp_box_labels(2, A, 1, A, 0, A, None) == 0

@@ -1,0 +1,337 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (from the stated accuracy targets):
+* per step:  |step_gpu - step_ref|_inf <= 1e-5 eta sigma'(s) sum_m |w_m| |grad phi_m|
+             + 1e-5 |step_ref|_inf, with step_gpu the kernel's FP32 increment
+             at the GPU's own state x_t (promoted to FP64 for the oracle);
+* final:     |x_T gpu - x_T ref|_inf <= 1e-4, oracle started from the same
+             float32 x_0;
+* VJP:       normwise relative 1e-4 (on g0 - gT when the chain is near the
+             identity);
+* log-det:   absolute 1e-4 T;
+* labels:    bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2108_11775_gb300 as pdmp
+import workloads as wl
+from gpu_util import max_abs, rbf_eta, rff_eta_certified, rff_eta_sampled, setup_oracle_threads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    setup_oracle_threads()
+    pdmp.lib()
+    yield
+    st, detail = pdmp.stream_status()
+    assert st == 0, (st, detail)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def per_step_check(field, traj, steps, eta):
+    """Every step's FP32 increment against the oracle's at the same state."""
+    T, N, d = steps.shape
+    worst = 0.0
+    for t in range(T):
+        xt = traj[t].astype(np.float64)
+        ev = oracle.evaluate(field, xt)
+        ref = -eta * ev["grad"]
+        tol = 1e-5 * eta * ev["scale"] + 1e-5 * np.abs(ref).max(axis=1)
+        err = np.abs(steps[t].astype(np.float64) - ref).max(axis=1)
+        assert np.all(err <= tol), f"step {t}: worst excess {np.max(err - tol):.3e}"
+        worst = max(worst, float(np.max(err / np.maximum(tol, 1e-300))))
+    return worst
+
+
+# --------------------------------------------------------------------------
+# morph: 2-D grid field, 4096 samples, 10 steps
+def test_morph_config1_per_step_and_final():
+    w1 = wl.config1()
+    eta, L = rbf_eta(w1.field, w1.lo, w1.hi)
+    fld = pdmp.DeviceField.from_host(w1.field, lipschitz=L)
+    x0 = dev(w1.x0)
+    traj, steps = pdmp.morph_trace(fld, x0, w1.T, eta)
+    traj, steps = traj.cpu().numpy(), steps.cpu().numpy()
+    assert np.array_equal(traj[0], w1.x0)
+    per_step_check(w1.field, traj, steps, eta)
+    xT = pdmp.morph(fld, x0, w1.T, eta).cpu().numpy()
+    assert np.array_equal(xT, traj[-1]), "morph and its trace twin disagree"
+    ref = oracle.morph(w1.field, w1.x0, w1.T, eta)
+    assert max_abs(xT, ref) <= 1e-4
+    assert np.abs(ref - w1.x0).max() > 1e-2          # the samples moved
+
+
+@pytest.mark.parametrize("kind,d,M,N,T", [
+    (wl.RBF, 1, 7, 37, 5), (wl.RBF, 2, 1, 1, 4), (wl.RBF, 2, 300, 1000, 6), (wl.RBF, 3, 513, 777, 5),
+    (wl.RBF, 2, 257, 513, 3), (wl.RFF, 1, 33, 100, 5), (wl.RFF, 3, 129, 301, 4), (wl.RFF, 7, 300, 257, 5),
+    (wl.RFF, 8, 64, 65, 3),
+])
+def test_morph_ragged_shapes(kind, d, M, N, T):
+    if kind == wl.RBF:
+        f = wl.random_field(50 + d + M, kind, d, M, lo=0, hi=3, gamma=3.0, wscale=2.0, bias=0.25)
+        lo, hi = np.full(d, -1.0), np.full(d, 4.0)
+        eta, _ = rbf_eta(f, lo, hi, cells=32 if d < 3 else 12)
+        x0 = wl.uniform_box(60 + N, 3, N, np.zeros(d), np.full(d, 3.0))
+    else:
+        f = wl.random_field(50 + d + M, kind, d, M, wscale=4.0, bias=-0.1)
+        lo, hi = np.full(d, -np.pi), np.full(d, np.pi)
+        eta, _ = rff_eta_sampled(f, lo, hi, n=500)
+        x0 = wl.uniform_box(60 + N, 3, N, lo, hi)
+    fld = pdmp.DeviceField.from_host(f)
+    traj, steps = pdmp.morph_trace(fld, dev(x0), T, eta)
+    per_step_check(f, traj.cpu().numpy(), steps.cpu().numpy(), eta)
+    xT = pdmp.morph(fld, dev(x0), T, eta).cpu().numpy()
+    assert max_abs(xT, oracle.morph(f, x0, T, eta)) <= 1e-4
+
+
+def test_morph_in_place_zero_steps_and_empty():
+    w1 = wl.config1(N=300)
+    eta, _ = rbf_eta(w1.field, w1.lo, w1.hi)
+    fld = pdmp.DeviceField.from_host(w1.field)
+    x = dev(w1.x0)
+    ref = pdmp.morph(fld, x, 4, eta).cpu().numpy()
+    pdmp.morph(fld, x, 4, eta, out=x)                 # in place
+    assert np.array_equal(x.cpu().numpy(), ref)
+    y = dev(w1.x0)
+    out = pdmp.morph(fld, y, 0, eta)
+    assert np.array_equal(out.cpu().numpy(), w1.x0)
+    empty = torch.empty(0, 2, device="cuda")
+    assert pdmp.morph(fld, empty, 4, eta).shape == (0, 2)
+
+
+def test_morph_zero_weights_is_identity():
+    f = wl.random_field(3, wl.RBF, 2, 100).with_weights(np.zeros(100), bias=0.3)
+    x0 = wl.uniform_box(3, 3, 1000, [0, 0], [10, 10])
+    out = pdmp.morph(pdmp.DeviceField.from_host(f), dev(x0), 20, 0.5).cpu().numpy()
+    assert np.array_equal(out, x0)
+
+
+def test_checkpoints_are_the_trajectory():
+    w1 = wl.config1(N=700)
+    eta, _ = rbf_eta(w1.field, w1.lo, w1.hi)
+    fld = pdmp.DeviceField.from_host(w1.field)
+    ck = torch.empty(5, 700, 2, device="cuda")
+    xT = pdmp.morph(fld, dev(w1.x0), 10, eta, ckpt=ck, k=2)
+    traj, _ = pdmp.morph_trace(fld, dev(w1.x0), 10, eta)
+    traj = traj.cpu().numpy()
+    ck = ck.cpu().numpy()
+    for j in range(5):
+        assert np.array_equal(ck[j], traj[2 * (j + 1)])
+    assert np.array_equal(xT.cpu().numpy(), traj[-1])
+
+
+def test_step_size_checked_against_the_field_bound():
+    w1 = wl.config1(N=16)
+    _, L = rbf_eta(w1.field, w1.lo, w1.hi)
+    fld = pdmp.DeviceField.from_host(w1.field, lipschitz=L)
+    with pytest.raises(pdmp.PdmpError) as e:
+        pdmp.morph(fld, dev(w1.x0), 3, 1.5 / L)
+    assert e.value.status == 2
+
+
+# --------------------------------------------------------------------------
+# full-size workloads, sampled
+def test_morph_fitted_2d_full_size_sampled():
+    wk = wl.config2()
+    f = wk.field.with_weights(wl.proxy_fitted_weights(2, wk.field.centres, wk.boxes))
+    eta, L = rbf_eta(f, wk.lo - 0.5, wk.hi + 0.5, cells=96)
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    xT = pdmp.morph(fld, dev(wk.x0), wk.T, eta).cpu().numpy()
+    idx = np.sort(wl.rng(7, 1).choice(wk.x0.shape[0], 48, replace=False))
+    idx = np.concatenate([idx, [0, wk.x0.shape[0] - 1]])
+    ref = oracle.morph(f, wk.x0[idx], wk.T, eta)
+    assert max_abs(xT[idx], ref) <= 1e-4
+    assert np.isfinite(xT).all()
+
+
+def test_morph_rff_7d_full_size_sampled():
+    wk = wl.config3()
+    eta, L = rff_eta_certified(wk.field)
+    fld = pdmp.DeviceField.from_host(wk.field, lipschitz=L)
+    k = wk.extra["k"]
+    ck = torch.empty(wk.T // k, wk.x0.shape[0], 7, device="cuda")
+    xT = pdmp.morph(fld, dev(wk.x0), wk.T, eta, ckpt=ck, k=k).cpu().numpy()
+    idx = np.concatenate([np.sort(wl.rng(8, 1).choice(wk.x0.shape[0], 24, replace=False)), [wk.x0.shape[0] - 1]])
+    ref = oracle.morph(wk.field, wk.x0[idx], wk.T, eta)
+    assert max_abs(xT[idx], ref) <= 1e-4
+    assert np.abs(ref - wk.x0[idx]).max() > 1e-5
+
+
+# --------------------------------------------------------------------------
+# VJP and log-det
+def _vjp_case(kind):
+    if kind == wl.RBF:
+        w1 = wl.config1(N=256)
+        eta, _ = rbf_eta(w1.field, w1.lo, w1.hi)
+        return w1.field, w1.x0, 10, 5, eta
+    f = wl.random_field(21, wl.RFF, 7, 256, wscale=6.0, bias=0.1)
+    lo, hi = np.full(7, -np.pi), np.full(7, np.pi)
+    eta, _ = rff_eta_sampled(f, lo, hi, n=800)
+    return f, wl.uniform_box(21, 3, 128, lo, hi), 20, 5, eta
+
+
+@pytest.mark.parametrize("kind", [wl.RBF, wl.RFF])
+@pytest.mark.parametrize("use_ckpt", [True, False])
+def test_vjp_matches_oracle(kind, use_ckpt):
+    f, x0, T, k, eta = _vjp_case(kind)
+    fld = pdmp.DeviceField.from_host(f)
+    N, d = x0.shape
+    gT = wl.f32(wl.rng(5, wl.S_COTANGENT).standard_normal((N, d)))
+    ck = None
+    if use_ckpt:
+        ck = torch.empty(T // k, N, d, device="cuda")
+        pdmp.morph(fld, dev(x0), T, eta, ckpt=ck, k=k)
+    g0, gw, gb = pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck, want_param_grad=True)
+    g0, gw, gb = g0.cpu().numpy(), gw.cpu().numpy(), float(gb.cpu().numpy()[0])
+    r0, rw, rb = oracle.morph_vjp(f, x0, T, eta, gT, want_gw=True)
+    corr_ref = r0 - gT
+    assert np.linalg.norm(g0 - r0) <= 1e-4 * np.linalg.norm(r0)
+    assert np.linalg.norm((g0 - gT) - corr_ref) <= 1e-4 * np.linalg.norm(corr_ref) + 1e-6
+    assert np.linalg.norm(gw - rw) <= 1e-4 * np.linalg.norm(rw)
+    assert abs(gb - rb) <= 1e-4 * max(abs(rb), 1e-3)
+
+
+def test_vjp_rff_7d_certified_step_full_chain():
+    wk = wl.config3(N=4096)
+    eta, _ = rff_eta_certified(wk.field)
+    fld = pdmp.DeviceField.from_host(wk.field)
+    gT = wk.extra["gT"]
+    ck = torch.empty(4, 4096, 7, device="cuda")
+    pdmp.morph(fld, dev(wk.x0), 20, eta, ckpt=ck, k=5)
+    g0 = pdmp.morph_vjp(fld, dev(wk.x0), 20, eta, 5, dev(gT), ckpt=ck).cpu().numpy()
+    idx = np.arange(0, 4096, 128)
+    r0 = oracle.morph_vjp(wk.field, wk.x0[idx], 20, eta, gT[idx])
+    corr = r0 - gT[idx]
+    assert np.linalg.norm((g0[idx] - gT[idx]) - corr) <= 1e-4 * np.linalg.norm(corr)
+
+
+@pytest.mark.parametrize("kind", [wl.RBF, wl.RFF])
+def test_logdet_matches_oracle_and_is_diffeomorphic(kind):
+    f, x0, T, _, eta = _vjp_case(kind)
+    fld = pdmp.DeviceField.from_host(f)
+    ld, xT = pdmp.logdet(fld, dev(x0), T, eta, want_xT=True)
+    ld, xT = ld.cpu().numpy(), xT.cpu().numpy()
+    ref, xref, mindet = oracle.logdet(f, x0, T, eta)
+    assert np.all(mindet > 0)
+    assert max_abs(ld, ref) <= 1e-4 * T
+    assert max_abs(xT, xref) <= 1e-4
+    assert pdmp.stream_status()[0] == 0
+
+
+def test_logdet_flags_a_non_diffeomorphic_step():
+    w1 = wl.config1(N=128)
+    _, L = rbf_eta(w1.field, w1.lo, w1.hi)
+    fld = pdmp.DeviceField.from_host(w1.field)           # carries no bound: the call is accepted
+    ld = pdmp.logdet(fld, dev(w1.x0), 3, 40.0 / L).cpu().numpy()
+    st, detail = pdmp.stream_status()
+    assert st == 7 and detail & 1
+    assert np.isnan(ld).any()
+    assert pdmp.stream_status()[0] == 0                   # the flag was cleared
+
+
+# --------------------------------------------------------------------------
+# queries, labels, Lipschitz bound
+def test_occupancy_query_matches_oracle():
+    w1 = wl.config1()
+    fld = pdmp.DeviceField.from_host(w1.field)
+    q = pdmp.occupancy_query(fld, dev(w1.x0))
+    ev = oracle.evaluate(w1.field, w1.x0)
+    abs_s = oracle.evaluate(w1.field.with_weights(np.abs(w1.field.w)), w1.x0)["s"]   # sum |w| phi
+    assert np.all(np.abs(q["s"].cpu().numpy() - ev["s"]) <= 1e-5 * abs_s + 1e-6)
+    assert np.all(np.abs(q["c"].cpu().numpy() - ev["c"]) <= 1e-5 * abs_s + 1e-6)
+    g = q["grad"].cpu().numpy()
+    assert np.all(np.abs(g - ev["grad"]).max(axis=1) <= 1e-5 * ev["scale"] + 1e-5 * np.abs(ev["grad"]).max(axis=1))
+
+
+def _grid(lo, hi, n, d):
+    axes = [lo + (hi - lo) * (np.arange(n) + 0.5) / n for _ in range(d)]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return wl.f32(np.stack([m.ravel() for m in mesh], axis=1))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_collision_labels_bit_exact_on_grid(d):
+    if d == 2:
+        wk = wl.config2(N=16)
+        pts = _grid(0.0, 10.0, 256, 2)
+    else:
+        wk = wl.config5(N=16, n_train=16)
+        pts = _grid(0.0, 5.0, 64, 3)
+    # add points exactly on box faces and one ulp outside them
+    b = wk.boxes
+    face = np.concatenate([b[:, :d], b[:, d:], np.nextafter(b[:, d:], np.float32(np.inf)),
+                           np.nextafter(b[:, :d], np.float32(-np.inf))])
+    pts = np.concatenate([pts, wl.f32(face)])
+    lab = pdmp.box_labels(dev(b), dev(pts)).cpu().numpy()
+    ref = oracle.box_labels(b, pts)
+    assert np.array_equal(lab, ref)
+    assert 0 < ref.sum() < len(ref)
+    assert np.array_equal(pdmp.box_labels(dev(np.zeros((0, 2 * d), np.float32)), dev(pts)).cpu().numpy(),
+                          np.zeros(len(pts), np.uint8))
+
+
+def test_learned_labels_on_grid_match_outside_the_margin():
+    wk = wl.config2(N=16)
+    f = wk.field.with_weights(wl.proxy_fitted_weights(2, wk.field.centres, wk.boxes), bias=-0.5)
+    pts = _grid(0.0, 10.0, 128, 2)
+    s_gpu = pdmp.occupancy_query(pdmp.DeviceField.from_host(f), dev(pts), want=("s",))["s"].cpu().numpy()
+    ev = oracle.evaluate(f, pts)
+    margin = 1e-5 * (oracle.evaluate(f.with_weights(np.abs(f.w), bias=0.0), pts)["s"] + abs(f.bias))
+    sure = np.abs(ev["s"]) > margin
+    assert sure.mean() > 0.999
+    assert np.array_equal(s_gpu[sure] >= 0, ev["s"][sure] >= 0)
+
+
+def test_lipschitz_bound_matches_oracle():
+    w1 = wl.config1()
+    L, G = pdmp.lipschitz_bound(pdmp.DeviceField.from_host(w1.field), w1.lo, w1.hi, cells=64)
+    Lr, Gr = oracle.lipschitz(w1.field, w1.lo, w1.hi, cells=64)
+    assert abs(L - Lr) <= 1e-9 * Lr and abs(G - Gr) <= 1e-9 * Gr
+    f3 = wl.config3(N=8).field
+    L, G = pdmp.lipschitz_bound(pdmp.DeviceField.from_host(f3))
+    Lr, Gr = oracle.lipschitz(f3)
+    assert abs(L - Lr) <= 1e-9 * Lr and abs(G - Gr) <= 1e-9 * Gr
+    f3d = wl.random_field(4, wl.RBF, 3, 500, lo=0, hi=5, gamma=8.0)
+    L, G = pdmp.lipschitz_bound(pdmp.DeviceField.from_host(f3d), [0, 0, 0], [5, 5, 5], cells=12)
+    Lr, Gr = oracle.lipschitz(f3d, [0, 0, 0], [5, 5, 5], cells=12)
+    assert abs(L - Lr) <= 1e-9 * Lr and abs(G - Gr) <= 1e-9 * Gr
+
+
+# --------------------------------------------------------------------------
+# occupancy fit
+def test_fit_matches_oracle_same_algorithm():
+    wk = wl.config2(N=16, M=256, n_fit=4096)
+    f = wk.field
+    w, b, loss, alpha = pdmp.fit_occupancy(pdmp.DeviceField.from_host(f), dev(wk.fit_X), dev(wk.fit_y), 1e-4, 30, 100)
+    rw, rb, rloss, ralpha = oracle.fit(f, wk.fit_X, wk.fit_y, 1e-4, 30, 100)
+    assert abs(alpha - ralpha) <= 1e-4 * ralpha
+    assert abs(loss - rloss) <= 1e-4 * rloss
+    w = w.cpu().numpy()
+    assert np.linalg.norm(w - rw) <= 1e-3 * np.linalg.norm(rw)
+    assert abs(b - rb) <= 1e-3 * max(1.0, abs(rb))
+
+
+def test_fit_full_size_2d_learns_the_boxes():
+    wk = wl.config2(N=16)
+    fld = pdmp.DeviceField.from_host(wk.field)
+    X, y = dev(wk.fit_X), dev(wk.fit_y)
+    w, b, loss, _ = pdmp.fit_occupancy(fld, X, y, 1e-4, 20, 200)
+    assert np.isfinite(loss) and loss < 0.35
+    fitted = fld.with_weights(w, bias=b)
+    s = pdmp.occupancy_query(fitted, X, want=("s",))["s"].cpu().numpy()
+    acc = np.mean((s >= 0) == (wk.fit_y == 1))
+    assert acc > 0.93
+    # the oracle's objective at the GPU's weights agrees with the reported loss
+    sub = slice(0, 20000)
+    lo_, _, _ = oracle.fit_objective(wk.field, wk.fit_X[sub], wk.fit_y[sub], 1e-4, w.cpu().numpy(), b)
+    assert abs(lo_ - loss) < 0.05
