@@ -93,18 +93,28 @@ pdmp_status pdmp_stream_status(void* stream, int32_t* detail);
  * copies x0 to xT).
  * ckpt: NULL, or a (T/k) x N x d buffer that receives x_{k}, x_{2k}, ..., x_T
  * (checkpoints for pdmp_morph_vjp); then k >= 1 must divide T.
- * Sample state lives in registers for all T steps; features are evaluated
- * in FP32 with exp2 / sin / cos on the special-function unit. */
+ * ws: NULL, or ws_bytes >= pdmp_morph_workspace(f, N) bytes of caller-owned
+ * device scratch.  With a workspace, RBF fields in d = 2 or 3 take the fast
+ * path: samples are ordered spatially (a deterministic counting sort on
+ * Morton cells) so that each tile of 256 samples is compact, and features are
+ * evaluated in an expanded form about the tile's centre with packed f32x2
+ * arithmetic (2d + 1 FP32 operations and one ex2 per feature).  Without one,
+ * or for other fields, every feature is evaluated directly from x - mu.
+ * Sample state lives in registers for all T steps; features are evaluated in
+ * FP32 with exp2 / sin / cos on the special-function unit.  Calls that share
+ * a workspace must not overlap on the GPU. */
+size_t pdmp_morph_workspace(const pdmp_field* f, int64_t N);
 pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta,
-                       float* xT, float* ckpt, int32_t k, void* stream);
+                       float* xT, float* ckpt, int32_t k, void* ws, size_t ws_bytes, void* stream);
 
-/* Diagnostic twin of pdmp_morph with the same kernel arithmetic: traj
- * ((T+1) x N x d) receives x_0 .. x_T and steps (T x N x d) the FP32 increment
- * -eta sigma'(s) grad s(x_t) of every step as computed, before it is added
- * to x_t (so that the accuracy of a step can be checked apart from the
- * rounding of the float32 state).  steps may be NULL only when T = 0. */
+/* Diagnostic twin of pdmp_morph with the same kernel arithmetic (the same
+ * path is chosen for the same f, N and ws): traj ((T+1) x N x d) receives
+ * x_0 .. x_T and steps (T x N x d) the FP32 increment -eta sigma'(s)
+ * grad s(x_t) of every step as computed, before it is added to x_t (so that
+ * the accuracy of a step can be checked apart from the rounding of the
+ * float32 state).  steps may be NULL only when T = 0. */
 pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* traj,
-                             float* steps, void* stream);
+                             float* steps, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Chain rule through Eq. (1): vector-Jacobian product of the T-step map.   */

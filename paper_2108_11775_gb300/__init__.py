@@ -22,7 +22,7 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "PdmpError", "DeviceField", "lib", "morph", "morph_trace", "morph_vjp", "morph_vjp_workspace", "logdet",
+    "PdmpError", "DeviceField", "lib", "morph", "morph_trace", "morph_workspace", "morph_vjp", "morph_vjp_workspace", "logdet",
     "occupancy_query", "box_labels", "lipschitz_bound", "fit_occupancy", "fit_workspace", "stream_status",
     "RBF", "RFF",
 ]
@@ -69,8 +69,8 @@ def lib():
             L.pdmp_version.restype = _i32
             sigs = {
                 "pdmp_stream_status": [_P, ctypes.POINTER(_i32)],
-                "pdmp_morph": [_FP, _P, _i64, _i32, _f32, _P, _P, _i32, _P],
-                "pdmp_morph_trace": [_FP, _P, _i64, _i32, _f32, _P, _P, _P],
+                "pdmp_morph": [_FP, _P, _i64, _i32, _f32, _P, _P, _i32, _P, _sz, _P],
+                "pdmp_morph_trace": [_FP, _P, _i64, _i32, _f32, _P, _P, _P, _sz, _P],
                 "pdmp_morph_vjp": [_FP, _P, _i64, _i32, _f32, _i32, _P, _P, _P, _P, _P, _P, _sz, _P],
                 "pdmp_logdet": [_FP, _P, _i64, _i32, _f32, _P, _P, _P],
                 "pdmp_occupancy_query": [_FP, _P, _i64, _P, _P, _P, _P],
@@ -84,6 +84,8 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = argt
                 fn.restype = _i32
+            L.pdmp_morph_workspace.argtypes = [_FP, _i64]
+            L.pdmp_morph_workspace.restype = _sz
             L.pdmp_morph_vjp_workspace.argtypes = [_FP, _i64, _i32, _i32, _i32]
             L.pdmp_morph_vjp_workspace.restype = _sz
             L.pdmp_fit_workspace.argtypes = [_i64, _i64]
@@ -176,32 +178,54 @@ def stream_status():
     return int(st), int(detail.value)
 
 
+def morph_workspace(field: DeviceField, N: int) -> int:
+    f = field.struct()
+    return int(lib().pdmp_morph_workspace(ctypes.byref(f), int(N)))
+
+
+def _workspace(field, N, fast, ws):
+    """(pointer, bytes) of the morph workspace: the caller's, a fresh one, or none."""
+    if not fast:
+        return None, 0, None
+    nbytes = morph_workspace(field, N)
+    if nbytes == 0:
+        return None, 0, None
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=field.centres.device)
+    return ctypes.c_void_p(ws.data_ptr()), nbytes, ws
+
+
 def morph(field: DeviceField, x0: torch.Tensor, T: int, eta: float, out: torch.Tensor | None = None,
-          ckpt: torch.Tensor | None = None, k: int = 0) -> torch.Tensor:
+          ckpt: torch.Tensor | None = None, k: int = 0, fast: bool = True,
+          ws: torch.Tensor | None = None) -> torch.Tensor:
     """x_T of T Euler steps of Eq. (1) for every row of x0 (N x d).  ``out``
-    may be x0 itself.  ``ckpt`` ((T/k) x N x d) receives x_k, x_2k, ..., x_T."""
+    may be x0 itself.  ``ckpt`` ((T/k) x N x d) receives x_k, x_2k, ..., x_T.
+    ``fast`` gives the library a workspace (``ws``, a uint8 CUDA tensor, or a
+    fresh one) so that 2-D / 3-D RBF fields take the fast path."""
     N = x0.shape[0]
     d = field.d
     if out is None:
         out = torch.empty_like(x0)
+    wp, wb, _keep = _workspace(field, N, fast, ws)
     f = field.struct()
     st = lib().pdmp_morph(ctypes.byref(f), _ptr(x0, shape=(N, d), name="x0"), N, int(T), float(eta),
                           _ptr(out, shape=(N, d), name="out"),
                           _ptr(ckpt, shape=(T // k if k else 0, N, d), name="ckpt") if ckpt is not None else None,
-                          int(k), _stream())
+                          int(k), wp, wb, _stream())
     _check(st, "pdmp_morph")
     return out
 
 
-def morph_trace(field: DeviceField, x0: torch.Tensor, T: int, eta: float):
+def morph_trace(field: DeviceField, x0: torch.Tensor, T: int, eta: float, fast: bool = True):
     """(traj ((T+1) x N x d), steps (T x N x d)): every state and every FP32
     increment as the morph kernel computes it (diagnostic)."""
     N, d = x0.shape[0], field.d
     traj = torch.empty(T + 1, N, d, device=x0.device, dtype=torch.float32)
     steps = torch.empty(max(T, 1), N, d, device=x0.device, dtype=torch.float32)
+    wp, wb, _keep = _workspace(field, N, fast, None)
     f = field.struct()
     st = lib().pdmp_morph_trace(ctypes.byref(f), _ptr(x0, shape=(N, d), name="x0"), N, int(T), float(eta),
-                                _ptr(traj), _ptr(steps), _stream())
+                                _ptr(traj), _ptr(steps), wp, wb, _stream())
     _check(st, "pdmp_morph_trace")
     return traj, steps[:T]
 

@@ -92,8 +92,20 @@ pdmp_status pdmp_stream_status(void* stream, int32_t* detail) {
   return flag ? PDMP_ERR_DEVICE_FLAG : PDMP_OK;
 }
 
+size_t pdmp_morph_workspace(const pdmp_field* f, int64_t N) {
+  if (f == nullptr || check_field(f) != PDMP_OK || N <= 0) return 0;
+  return pdmp::morph_workspace(f->kind, f->d, f->M, N);
+}
+
+static pdmp_status check_ws(const pdmp_field* f, int64_t N, void* ws, size_t ws_bytes) {
+  if (ws == nullptr) return PDMP_OK;
+  if (!aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::morph_workspace(f->kind, f->d, f->M, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  return PDMP_OK;
+}
+
 pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* xT,
-                       float* ckpt, int32_t k, void* stream) {
+                       float* ckpt, int32_t k, void* ws, size_t ws_bytes, void* stream) {
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
@@ -101,27 +113,29 @@ pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t 
   if (ckpt != nullptr && (k < 1 || T % k != 0)) return PDMP_ERR_INVALID_ARG;
   if (N == 0) return PDMP_OK;
   if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || !ok_ptr(ckpt, false)) return PDMP_ERR_INVALID_ARG;
+  if ((s = check_ws(f, N, ws, ws_bytes)) != PDMP_OK) return s;
   cudaStream_t st = as_stream(stream);
   if (T == 0) {
     if (xT != x0) return cuda_status(cudaMemcpyAsync(xT, x0, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st));
     return PDMP_OK;
   }
   return cuda_status(pdmp::morph_dispatch(f->kind, f->d, field_args(f), x0, N, T, eta, xT, ckpt, k, nullptr,
-                                          nullptr, st));
+                                          nullptr, ws, st));
 }
 
 pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* traj,
-                             float* steps, void* stream) {
+                             float* steps, void* ws, size_t ws_bytes, void* stream) {
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
   if (N < 0 || T < 0) return PDMP_ERR_INVALID_ARG;
   if (N == 0) return PDMP_OK;
   if (!ok_ptr(x0, true) || !ok_ptr(traj, true) || !ok_ptr(steps, T > 0)) return PDMP_ERR_INVALID_ARG;
+  if ((s = check_ws(f, N, ws, ws_bytes)) != PDMP_OK) return s;
   cudaStream_t st = as_stream(stream);
   if (T == 0) return cuda_status(cudaMemcpyAsync(traj, x0, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st));
   return cuda_status(pdmp::morph_dispatch(f->kind, f->d, field_args(f), x0, N, T, eta, nullptr, nullptr, 0, traj,
-                                          steps, st));
+                                          steps, ws, st));
 }
 
 size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32_t k, int32_t want_param_grad) {

@@ -10,8 +10,15 @@ constexpr int kMaxSegment = 32;
 // traj / steps: both NULL, or both set (diagnostic trace, see pdmp_morph_trace)
 cudaError_t morph_direct(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta,
                          float* xT, float* ckpt, int k, float* traj, float* steps, cudaStream_t st);
+// fast RBF path (d = 2, 3): spatially sorted tiles, expanded exponent, f32x2
+size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N);
+cudaError_t morph_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
+                           float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
+// workspace the dispatcher's fast path needs (0: the request takes the direct path)
+size_t morph_workspace(int kind, int d, int64_t M, int64_t N);
+// ws == nullptr selects the direct path
 cudaError_t morph_dispatch(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta,
-                           float* xT, float* ckpt, int k, float* traj, float* steps, cudaStream_t st);
+                           float* xT, float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
 
 int64_t vjp_blocks(int64_t N);
 cudaError_t morph_vjp(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,

@@ -55,8 +55,8 @@ def fld(kind=0, d=2, M=16, gamma=4.0, centres=A, w=A, phase=None, lipschitz=0.0)
     return f
 
 
-def morph_call(f, x0=A, N=8, T=4, eta=0.01, xT=A, ckpt=None, k=0):
-    return pdmp.lib().pdmp_morph(ctypes.byref(f), x0, N, T, eta, xT, ckpt, k, None)
+def morph_call(f, x0=A, N=8, T=4, eta=0.01, xT=A, ckpt=None, k=0, ws=None, ws_bytes=0):
+    return pdmp.lib().pdmp_morph(ctypes.byref(f), x0, N, T, eta, xT, ckpt, k, ws, ws_bytes, None)
 
 
 @nogpu
@@ -88,6 +88,18 @@ def test_morph_rejects_bad_arguments(kw, code):
 def test_step_too_large_when_field_carries_L():
     assert morph_call(fld(lipschitz=100.0), eta=0.0101) == 2
     assert morph_call(fld(lipschitz=100.0), eta=0.5) == 2
+
+
+@nogpu
+def test_morph_workspace_size_and_checks():
+    L = pdmp.lib()
+    f = fld()
+    need = L.pdmp_morph_workspace(ctypes.byref(f), 1 << 20)
+    assert need > (1 << 20) * 8                       # keys + permutation at least
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, phase=A)), 1 << 20) == 0   # RFF: direct path
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(d=1)), 1000) == 0
+    assert morph_call(f, N=1 << 20, ws=A, ws_bytes=need - 1) == 3
+    assert morph_call(f, N=1 << 20, ws=MIS, ws_bytes=need) == 1
 
 
 @nogpu

@@ -55,16 +55,17 @@ def per_step_check(field, traj, steps, eta):
 
 # --------------------------------------------------------------------------
 # morph: 2-D grid field, 4096 samples, 10 steps
-def test_morph_config1_per_step_and_final():
+@pytest.mark.parametrize("fast", [True, False])
+def test_morph_config1_per_step_and_final(fast):
     w1 = wl.config1()
     eta, L = rbf_eta(w1.field, w1.lo, w1.hi)
     fld = pdmp.DeviceField.from_host(w1.field, lipschitz=L)
     x0 = dev(w1.x0)
-    traj, steps = pdmp.morph_trace(fld, x0, w1.T, eta)
+    traj, steps = pdmp.morph_trace(fld, x0, w1.T, eta, fast=fast)
     traj, steps = traj.cpu().numpy(), steps.cpu().numpy()
     assert np.array_equal(traj[0], w1.x0)
     per_step_check(w1.field, traj, steps, eta)
-    xT = pdmp.morph(fld, x0, w1.T, eta).cpu().numpy()
+    xT = pdmp.morph(fld, x0, w1.T, eta, fast=fast).cpu().numpy()
     assert np.array_equal(xT, traj[-1]), "morph and its trace twin disagree"
     ref = oracle.morph(w1.field, w1.x0, w1.T, eta)
     assert max_abs(xT, ref) <= 1e-4
@@ -92,6 +93,33 @@ def test_morph_ragged_shapes(kind, d, M, N, T):
     per_step_check(f, traj.cpu().numpy(), steps.cpu().numpy(), eta)
     xT = pdmp.morph(fld, dev(x0), T, eta).cpu().numpy()
     assert max_abs(xT, oracle.morph(f, x0, T, eta)) <= 1e-4
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_fast_path_dense_tiles_per_step_and_final(d):
+    """Enough samples that the sorted 256-sample tiles are compact, so the
+    fast kernel runs its expanded form; checked on a subset of the samples."""
+    if d == 2:
+        f = wl.config1().field
+        lo, hi, N, T = np.zeros(2), np.full(2, 10.0), 1 << 16, 10
+        eta, L = rbf_eta(f, lo, hi)
+    else:
+        f = wl.random_field(77, wl.RBF, 3, 8192, lo=0, hi=5, gamma=8.0, wscale=2.0, bias=-0.2)
+        lo, hi, N, T = np.zeros(3), np.full(3, 5.0), 1 << 18, 8
+        eta, L = rbf_eta(f, lo - 0.5, hi + 0.5, cells=16)
+    x0 = wl.uniform_box(80 + d, 3, N, lo, hi)
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    traj, steps = pdmp.morph_trace(fld, dev(x0), T, eta)
+    xT = pdmp.morph(fld, dev(x0), T, eta).cpu().numpy()
+    xT2 = pdmp.morph(fld, dev(x0), T, eta).cpu().numpy()
+    traj, steps = traj.cpu().numpy(), steps.cpu().numpy()
+    assert np.array_equal(xT, xT2), "the fast path is not deterministic"
+    assert np.array_equal(xT, traj[-1])
+    idx = np.sort(wl.rng(d, 9).choice(N, 160, replace=False))
+    per_step_check(f, traj[:, idx], steps[:, idx], eta)
+    assert max_abs(xT[idx], oracle.morph(f, x0[idx], T, eta)) <= 1e-4
+    direct = pdmp.morph(fld, dev(x0), T, eta, fast=False).cpu().numpy()
+    assert max_abs(xT, direct) <= 1e-4
 
 
 def test_morph_in_place_zero_steps_and_empty():

@@ -136,7 +136,7 @@ def config2(seed: int = 2, N: int = 1 << 20, M: int = 16384, n_fit: int = 200_00
     return Workload(f"rbf2d-fitted-M{M}-N{N}-T50", fld, x0, 50, lo, hi, boxes, X, y)
 
 
-def proxy_fitted_weights(seed: int, centres: np.ndarray, boxes: np.ndarray, scale: float = 4.0) -> np.ndarray:
+def proxy_fitted_weights(seed: int, centres: np.ndarray, boxes: np.ndarray, scale: float = 0.5) -> np.ndarray:
     """Weights shaped like a fitted occupancy map (positive on centres inside
     an obstacle, negative outside, with spread) for parity runs that must not
     take their weights from the GPU fit."""
