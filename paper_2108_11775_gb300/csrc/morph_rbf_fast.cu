@@ -56,13 +56,32 @@ __device__ __forceinline__ u64 ex2x2(u64 a) {
   return pk(ex2_approx(lo), ex2_approx(hi));
 }
 
-constexpr int kFastWarps = 4;
+// Tile shape (compile-time; the defaults are the tuned configuration).
+#ifndef PDMP_FAST_WARPS
+#define PDMP_FAST_WARPS 4      // warps per block, each summing over its share of M
+#endif
+#ifndef PDMP_FAST_K
+#define PDMP_FAST_K 8          // samples per lane (even)
+#endif
+#ifndef PDMP_FAST_MINB
+#define PDMP_FAST_MINB 4       // blocks per SM the register budget is sized for
+#endif
+#ifndef PDMP_FAST_UNROLL
+#define PDMP_FAST_UNROLL 2     // centres per unrolled inner iteration
+#endif
+#ifndef PDMP_FAST_STAGE
+#define PDMP_FAST_STAGE 256    // centres per shared-memory stage
+#endif
+constexpr int kFastWarps = PDMP_FAST_WARPS;
 constexpr int kFastThreads = 32 * kFastWarps;
-constexpr int kFastK = 8;                      // samples per lane
+constexpr int kFastK = PDMP_FAST_K;
 constexpr int kFastPairs = kFastK / 2;
 constexpr int kFastTile = 32 * kFastK;         // samples per block
-constexpr int kFastStage = 256;                // centres per shared-memory stage
+constexpr int kFastStage = PDMP_FAST_STAGE;
 constexpr int kFastSlice = kFastStage / kFastWarps;
+constexpr int kFastUnroll = PDMP_FAST_UNROLL;
+static_assert(kFastK % 2 == 0, "samples per lane must be even (f32x2 pairs)");
+static_assert(kFastStage % kFastWarps == 0, "stage must split evenly across warps");
 
 template <int D>
 struct FastRec {
@@ -151,7 +170,7 @@ __device__ __forceinline__ void fast_stage(const float4* __restrict__ tab, int64
 }
 
 template <int D, bool TRACE>
-__global__ void __launch_bounds__(kFastThreads, 4)
+__global__ void __launch_bounds__(kFastThreads, PDMP_FAST_MINB)
 k_morph_rbf_fast(const float4* __restrict__ tab, int64_t M, float gamma, float bias, const float* x0,
                  const int32_t* __restrict__ perm, int64_t N, int T, float eta, float* xT, float* __restrict__ ckpt,
                  int kck, float* __restrict__ traj, float* __restrict__ steps) {
@@ -219,7 +238,7 @@ k_morph_rbf_fast(const float4* __restrict__ tab, int64_t M, float gamma, float b
     for (int st = 0; st < nstage; ++st) {
       const u64* rec = bufs + (size_t)(st & 1) * kFastStage * RP + (size_t)warp * kFastSlice * RP;
       if (expanded) {
-#pragma unroll 2
+#pragma unroll kFastUnroll
         for (int c = 0; c < kFastSlice; ++c) {
           const ulonglong2* q = reinterpret_cast<const ulonglong2*>(rec + (size_t)c * RP);
           u64 r[RP];
