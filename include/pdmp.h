@@ -116,6 +116,19 @@ pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t 
 pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* traj,
                              float* steps, void* ws, size_t ws_bytes, void* stream);
 
+/* The fast RBF morph for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Same arguments and results as pdmp_morph with
+ * ws = NULL replaced by scratch built into the library: a 12 MiB device array
+ * that every GPU loading the library holds until the process exits.  Limits:
+ * RBF fields with d = 2 or 3 (others give PDMP_ERR_UNSUPPORTED), N <= 2^20
+ * and M <= 16384 (larger requests give PDMP_ERR_WORKSPACE_TOO_SMALL before
+ * anything is launched).  No checkpoints.  The first call on a device looks up
+ * the scratch's device address; make it before any stream capture.  All calls
+ * share the scratch: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Calls no cudaMalloc / cudaFree. */
+pdmp_status pdmp_morph_noalloc(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* xT,
+                               void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Chain rule through Eq. (1): vector-Jacobian product of the T-step map.   */
 /* ---------------------------------------------------------------------- */

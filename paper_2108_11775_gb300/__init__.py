@@ -230,6 +230,25 @@ def morph_trace(field: DeviceField, x0: torch.Tensor, T: int, eta: float, fast: 
     return traj, steps[:T]
 
 
+def morph_noalloc(field: DeviceField, x0: torch.Tensor, T: int, eta: float,
+                  out: torch.Tensor | None = None) -> torch.Tensor:
+    """pdmp_morph_noalloc: the fast RBF morph on the library's built-in
+    scratch, for callers that cannot allocate device memory (RBF, d = 2 or 3,
+    N <= 2^20, M <= 16384; calls must not overlap on the GPU)."""
+    L = lib()
+    fn = L.pdmp_morph_noalloc
+    fn.argtypes = [_FP, _P, _i64, _i32, _f32, _P, _P]
+    fn.restype = _i32
+    N, d = x0.shape[0], field.d
+    if out is None:
+        out = torch.empty_like(x0)
+    f = field.struct()
+    st = fn(ctypes.byref(f), _ptr(x0, shape=(N, d), name="x0"), N, int(T), float(eta),
+            _ptr(out, shape=(N, d), name="out"), _stream())
+    _check(st, "pdmp_morph_noalloc")
+    return out
+
+
 def morph_vjp_workspace(field: DeviceField, N: int, T: int, k: int, want_param_grad: bool) -> int:
     f = field.struct()
     return int(lib().pdmp_morph_vjp_workspace(ctypes.byref(f), int(N), int(T), int(k), int(bool(want_param_grad))))
