@@ -60,10 +60,15 @@ def peaks():
 
 
 def alu_peak(n_sms: int, sm_mhz: float) -> float:
-    """Feature evaluations per second the FP32 pipe and the MUFU allow: an RBF
+    """Feature evaluations per second the SM's issue slots allow.  An RBF
     feature in d dimensions needs at least 2d + 1 FP32 operations (d for the
-    exponent's linear form, 1 for s, d for the gradient moments) and one ex2."""
-    per_sm_clk = min(FP32_LANES_PER_SM / (2 * D + 1), MUFU_EX2_PER_SM / 1.0)
+    exponent's linear form, 1 for s, d for the gradient moments) and one ex2.
+    A scheduler issues one warp instruction per clock; a packed f32x2 FMA
+    (64 FP32 operations) takes two issue clocks, so the FP32 work of 32
+    features costs 2d + 1 issue clocks and their ex2 one more: 128 / (2d + 2)
+    features per SM per clock.  The ex2 unit itself (32 per SM per clock) is
+    not the limit."""
+    per_sm_clk = min(FP32_LANES_PER_SM / (2 * D + 2), MUFU_EX2_PER_SM / 1.0)
     return n_sms * sm_mhz * 1e6 * per_sm_clk
 
 
@@ -243,7 +248,7 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "feature-evals/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": f"{n_sms} SMs x {pk.get('sm_max_mhz', 2070.0)} MHz ({pk_kind} max clock) x "
-                                   f"min(128/(2d+1) FP32, 32 ex2) per SM-clock"},
+                                   f"128/(2d+2) features per SM-clock (FP32 issue + ex2 issue)"},
         "clocks": clk.summary(),
         # per step: centre table, 7 kernels of the spatial sort, the morph kernel
         "gpu_launches": args.steps * LAUNCHES_PER_MORPH,
@@ -251,11 +256,133 @@ def run_ours(args, world, rank, local):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wk, fld, eta, target_s=args.cpu_seconds)
+    if not args.no_extras and args.workload == "full":
+        del x0, xT, ws, flush
+        torch.cuda.empty_cache()
+        line["extras"] = {
+            "batched_256_envs": extra_batched(pdmp, torch, n_sms, pk),
+            "rff7d_differentiation": extra_rff(pdmp, torch, n_sms, pk),
+            "surrogate_3d": extra_surrogate(pdmp, torch, args),
+        }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _time(torch, fn, reps=3):
+    """Best of reps CUDA-event timings of fn() on the current stream (seconds)."""
+    stream = torch.cuda.current_stream()
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        best = t if best is None else min(best, t)
+    return best
+
+
+def extra_batched(pdmp, torch, n_sms, pk):
+    """256 environments (d in {2,3}, M ~ U[256,8192], N ~ U[1k,64k], T = 30)
+    in one persistent launch, autotuned, replayed from a CUDA graph."""
+    hosts = wl.config4()
+    envs = []
+    for w in hosts:
+        f = pdmp.DeviceField.from_host(w.field)
+        L, _ = pdmp.lipschitz_bound(f, w.lo - 0.5, w.hi + 0.5, cells=64 if w.field.d == 2 else 16)
+        f.lipschitz = L
+        envs.append((f, torch.from_numpy(w.x0).cuda(), float(np.float32(0.5 / L)), w.T))
+    b = pdmp.Batch(envs)
+    best, times = b.autotune(reps=1, use_cache=False)
+    b.capture()
+    torch.cuda.current_stream().wait_stream(b.graph_stream)
+    b.replay()
+    torch.cuda.synchronize()
+    t = _time(torch, b.replay, reps=3)
+    work = b.work()
+    # issue-bound peak per environment's d, weighted by its work
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    t_peak = sum(w.x0.shape[0] * w.field.M * w.T / (n_sms * mhz * 1e6 * 128.0 / (2 * w.field.d + 2)) for w in hosts)
+    return {"value": work / t, "unit": "feature-evals/s", "ms_per_launch": 1e3 * t, "work": work,
+            "roofline_frac": (work / t) / (work / t_peak), "variant": best,
+            "variant_ms": [round(v, 3) for v in times], "launch": "CUDA graph of one pdmp_morph_batched",
+            "gpu_launches_per_run": 11}
+
+
+def extra_rff(pdmp, torch, n_sms, pk):
+    """7-D random Fourier field (M = 4096, N = 2^20, T = 20, k = 5): forward
+    with checkpoints, VJP from them, and the log-det pass."""
+    wk = wl.config3()
+    f = pdmp.DeviceField.from_host(wk.field)
+    L, _ = pdmp.lipschitz_bound(f)
+    eta = float(np.float32(0.5 / L))
+    x0 = torch.from_numpy(wk.x0).cuda()
+    gT = torch.from_numpy(wk.extra["gT"]).cuda()
+    N, T, k, M = x0.shape[0], wk.T, wk.extra["k"], wk.field.M
+    ck = torch.empty(T // k, N, 7, device="cuda")
+    out = torch.empty_like(x0)
+    t_fwd = _time(torch, lambda: pdmp.morph(f, x0, T, eta, out=out, ckpt=ck, k=k), reps=2)
+    g0 = torch.empty_like(x0)
+    t_vjp = _time(torch, lambda: pdmp.morph_vjp(f, x0, T, eta, k, gT, ckpt=ck, g0=g0), reps=2)
+    t_ld = _time(torch, lambda: pdmp.logdet(f, x0, T, eta), reps=1)
+    work = float(N) * T * M
+    return {"forward": work / t_fwd, "vjp_per_pass": 2 * work / t_vjp, "logdet": work / t_ld, "unit": "feature-evals/s",
+            "ms": {"forward": 1e3 * t_fwd, "vjp": 1e3 * t_vjp, "logdet": 1e3 * t_ld},
+            "note": "VJP counts its recompute pass and its Hessian-vector pass (2 N T M)"}
+
+
+def extra_surrogate(pdmp, torch, args):
+    """3-D fitted field (M = 8192, gamma = 8, 48 boxes, T = 40): MLP trained on
+    2^20 pairs from the plain morph, then inference on N = 2^24 with the plain
+    morph as fallback, against the plain morph alone."""
+    wk = wl.config5()
+    f0 = pdmp.DeviceField.from_host(wk.field)
+    w, bias, fit_loss, _ = pdmp.fit_occupancy(f0, torch.from_numpy(wk.fit_X).cuda(), torch.from_numpy(wk.fit_y).cuda(),
+                                              1e-4, 20, 200)
+    f = f0.with_weights(w, bias=bias)
+    L, _ = pdmp.lipschitz_bound(f, wk.lo - 0.5, wk.hi + 0.5, cells=32)
+    f.lipschitz = L
+    eta = float(np.float32(0.5 / L))
+    T = wk.T
+    xtr = torch.from_numpy(wk.extra["x_train"]).cuda()
+    x_prev = pdmp.morph(f, xtr, T - 1, eta)
+    xTtr = pdmp.morph(f, x_prev, 1, eta)
+    last = (xTtr - x_prev).norm(dim=1).cpu().numpy()
+    tau_r = float(np.quantile(last, 0.99))
+    scale = pdmp.displacement_rms(xtr, xTtr).cpu().numpy()
+    net = pdmp.Surrogate(wk.lo, wk.hi, scale, seed=5)
+    B, steps = 4096, args.surrogate_steps
+    loss = torch.zeros(1, device="cuda")
+    t0 = time.perf_counter()
+    for s in range(steps):
+        lr = 2e-3 * 0.5 * (1.0 + np.cos(np.pi * s / steps)) + 1e-5
+        i = (s * B) % (xtr.shape[0] - B)
+        net.train_step(xtr[i:i + B], xTtr[i:i + B], lr=lr, loss=loss if s == steps - 1 else None)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    x0 = torch.from_numpy(wk.x0).cuda()
+    boxes = torch.from_numpy(wk.boxes).cuda()
+    plain = torch.empty_like(x0)
+    ws = torch.empty(pdmp.morph_workspace(f, x0.shape[0]), dtype=torch.uint8, device="cuda")
+    t_plain = _time(torch, lambda: pdmp.morph(f, x0, T, eta, out=plain, ws=ws), reps=2)
+    sur = torch.empty_like(x0)
+    res = {}
+
+    def run_sur():
+        res["nf"] = net.infer(f, x0, T, eta, tau_r, out=sur)[1]
+    run_sur()
+    t_sur = _time(torch, run_sur, reps=2)
+    col = lambda x: float(pdmp.box_labels(boxes, x).float().mean().item())
+    c_prior, c_plain, c_sur = col(x0), col(plain), col(sur)
+    return {"speedup_vs_plain_morph": t_plain / t_sur, "ms_plain": 1e3 * t_plain, "ms_surrogate": 1e3 * t_sur,
+            "fallback_fraction": res["nf"] / x0.shape[0], "collision_rate": {"prior": c_prior, "plain_morph": c_plain,
+                                                                             "surrogate": c_sur},
+            "equal_collision_rate": c_sur <= c_plain + 1e-3, "tau_r": tau_r, "train_steps": steps,
+            "train_s": train_s, "final_train_loss": float(loss.item()), "N": int(x0.shape[0]), "T": T}
 
 
 def cpu_baseline(wk, fld, eta, target_s=12.0):
@@ -313,6 +440,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched / RFF / surrogate measurements")
+    ap.add_argument("--surrogate-steps", type=int, default=1500)
     ap.add_argument("--workload", choices=["full", "small"], default="full",
                     help="small: 65,536 samples and 5 steps of the same workload (for ncu captures)")
     args = ap.parse_args()
@@ -321,6 +450,7 @@ def main():
         N, T = SMALL["N"], SMALL["T"]
         WORKLOAD = f"rbf2d-fitted-M{M}-N{N}-T{T}"
         args.no_cpu_baseline = True
+        args.no_extras = True
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank, local)

@@ -130,6 +130,132 @@ pdmp_status pdmp_morph_noalloc(const pdmp_field* f, const float* x0, int64_t N, 
                                void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Many environments in one persistent launch (no counterpart in the paper: */
+/* the paper morphs one scene's samples).                                   */
+/* ---------------------------------------------------------------------- */
+/* One environment: an RBF field with d = 2 or 3, its own N samples (x0, N x d,
+ * device), output xT (N x d, device; may alias x0), step size and step count.
+ * Environments may differ in d, M, N, eta and T. */
+typedef struct {
+  pdmp_field field;
+  const float* x0;
+  float* xT;
+  int64_t N;
+  float eta;
+  int32_t T;
+} pdmp_env;
+
+/* What pdmp_batch_prepare planned (host struct, filled by the library). */
+typedef struct {
+  int32_t n_envs;
+  int32_t variant;        /* tile shape, 0 .. pdmp_batch_variants() - 1 */
+  int32_t grid, block;    /* persistent blocks and threads per block */
+  size_t smem_bytes;
+  int64_t n_units;        /* (environment, 256-or-128-sample tile) work units */
+  int64_t total_N, total_M, total_cells, nchunks;
+  size_t ws_bytes;        /* workspace bytes the plan uses */
+  double work;            /* sum over environments of N * M * T feature evaluations */
+  size_t off[12];         /* byte offsets of the workspace regions */
+} pdmp_batch_plan;
+
+/* Number of tile shapes the batched kernel is built with. */
+int32_t pdmp_batch_variants(void);
+
+/* Workspace bytes for these environments (host array) and tile shape. */
+size_t pdmp_batch_workspace(const pdmp_env* envs, int32_t n_envs, int32_t variant);
+
+/* Validates the environments (host array of n_envs >= 1), writes the device
+ * environment table and the work list -- (environment, tile) units ordered
+ * by decreasing M * T -- into ws, and fills *plan.  Copies host to device and
+ * synchronises `stream`: call it outside stream capture, once per set of
+ * environments (their buffers' addresses are baked into the plan). */
+pdmp_status pdmp_batch_prepare(const pdmp_env* envs, int32_t n_envs, int32_t variant, void* ws, size_t ws_bytes,
+                               pdmp_batch_plan* plan, void* stream);
+
+/* Runs a prepared batch: every environment's centre table, one spatial sort
+ * over all samples, and one persistent morph kernel whose blocks claim work
+ * units from an atomic counter.  Launches and memsets only (no host copies,
+ * no allocation), so it can be captured into a CUDA graph; calls sharing a
+ * workspace must not overlap on the GPU. */
+pdmp_status pdmp_morph_batched(const pdmp_batch_plan* plan, void* ws, void* stream);
+
+/* Autotuner: prepares and times every tile shape on these environments
+ * (one warm-up and `reps` timed runs each, CUDA events on `stream`), leaves
+ * ws prepared for the fastest, and returns it in *best and its plan in *plan.
+ * times_ms (host, may be NULL) receives pdmp_batch_variants() best times.
+ * ws must hold the largest pdmp_batch_workspace over the variants.
+ * Synchronises `stream`. */
+pdmp_status pdmp_batch_autotune(const pdmp_env* envs, int32_t n_envs, int32_t reps, void* ws, size_t ws_bytes,
+                                int32_t* best, float* times_ms, pdmp_batch_plan* plan, void* stream);
+
+/* Captures pdmp_morph_batched(plan, ws) into a CUDA graph and instantiates
+ * it; *graph_exec receives an opaque cudaGraphExec_t.  `stream` must not be
+ * the legacy default stream (capture needs a created stream). */
+pdmp_status pdmp_batch_graph_create(const pdmp_batch_plan* plan, void* ws, void* stream, void** graph_exec);
+pdmp_status pdmp_graph_launch(void* graph_exec, void* stream);
+pdmp_status pdmp_graph_destroy(void* graph_exec);
+
+/* ---------------------------------------------------------------------- */
+/* Learned surrogate of the T-step map (no counterpart in the paper): an MLP */
+/* predicts x_T - x_0; the plain morph checks it and replaces it when it    */
+/* fails.                                                                   */
+/* ---------------------------------------------------------------------- */
+/* Network 3 -> 128 -> 128 -> 128 -> 3, SiLU between the linear layers, on
+ * normalised coordinates: input u = (x_0 - lo) * in_scale - 1, output
+ * f(u) = (x_T - x_0) / out_scale.  Device buffers, caller-owned:
+ *   W        FP32 master weights, PDMP_MLP_NW floats: W1 (128 x 3), W2 (128 x
+ *            128), W3 (128 x 128), W4 (3 x 128), each [out][in] row-major;
+ *   b        FP32 biases, PDMP_MLP_NB floats: b1, b2, b3 (128 each), b4 (3);
+ *   W_bf16   BF16 copy of W (same layout), the weights the kernels use;
+ *   Wt_bf16  BF16 transposes of W2 and W3 (2 x 128 x 128), for the backward;
+ *   adam     Adam moments: m_W, v_W (PDMP_MLP_NW each), m_b, v_b (PDMP_MLP_NB
+ *            each); zero before the first step.
+ * Matrix products run on the tensor cores in BF16 with FP32 accumulation. */
+#define PDMP_MLP_NW 33536
+#define PDMP_MLP_NB 387
+typedef struct {
+  float* W;
+  float* b;
+  uint16_t* W_bf16;
+  uint16_t* Wt_bf16;
+  float* adam;
+  float lo[3], in_scale[3], out_scale[3];
+} pdmp_mlp;
+
+/* rms (device, d floats) = root mean square over the N rows of xT - x0, per
+ * coordinate: the output scale of the network, from training pairs. */
+pdmp_status pdmp_displacement_rms(const float* x0, const float* xT, int64_t N, int32_t d, float* rms, void* stream);
+
+/* Rewrites W_bf16 and Wt_bf16 from W (after initialising or loading W). */
+pdmp_status pdmp_mlp_refresh(const pdmp_mlp* net, void* stream);
+
+/* xT_hat (N x 3) = x0 + out_scale * f(u(x0)). */
+pdmp_status pdmp_mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* xT_hat, void* stream);
+
+/* One Adam step (step = 1, 2, ...) on the mean squared error between f(u(x0))
+ * and (xT - x0) / out_scale over a batch of B pairs (x0, xT: B x 3 device).
+ * loss (device, one float, may be NULL) receives the batch loss before the
+ * update.  ws: pdmp_mlp_train_workspace(B) bytes. */
+size_t pdmp_mlp_train_workspace(int32_t B);
+pdmp_status pdmp_mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int32_t B, float lr,
+                                float beta1, float beta2, float eps, int32_t step, float* loss, void* ws,
+                                size_t ws_bytes, void* stream);
+
+/* Surrogate morph with the plain morph as fallback and judge: xT (N x 3)
+ * first receives the network's prediction; then one plain Euler step is
+ * evaluated at every prediction, and a sample fails the residual check when
+ * the prediction lies in predicted-occupied space (s >= 0, i.e. c >= 1/2),
+ * when that step's length exceeds tau_r, or when it is not finite.  Failed
+ * samples are morphed by the plain T-step kernel from their x0 and written
+ * back.  *n_fallback (host) receives the number of failed samples (this call
+ * synchronises `stream` once, to learn it).  xT must not alias x0.  f: RBF with d = 3 (the network's
+ * input and output size).  ws: pdmp_surrogate_workspace(f, N) bytes. */
+size_t pdmp_surrogate_workspace(const pdmp_field* f, int64_t N);
+pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const float* x0, int64_t N, int32_t T,
+                                 float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, size_t ws_bytes,
+                                 void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Chain rule through Eq. (1): vector-Jacobian product of the T-step map.   */
 /* ---------------------------------------------------------------------- */
 /* g0[n] = (d x_T / d x_0)^T gT[n] for every sample, computed backwards as

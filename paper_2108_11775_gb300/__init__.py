@@ -23,7 +23,8 @@ from . import build as _build
 
 __all__ = [
     "PdmpError", "DeviceField", "lib", "morph", "morph_trace", "morph_workspace", "morph_vjp", "morph_vjp_workspace", "logdet",
-    "occupancy_query", "box_labels", "lipschitz_bound", "fit_occupancy", "fit_workspace", "stream_status",
+    "occupancy_query", "box_labels", "lipschitz_bound", "fit_occupancy", "fit_workspace", "stream_status", "Batch",
+    "Surrogate", "displacement_rms", "morph_autograd",
     "RBF", "RFF",
 ]
 
@@ -345,3 +346,356 @@ def fit_occupancy(field: DeviceField, X: torch.Tensor, y: torch.Tensor, l2: floa
                                   ctypes.byref(alpha), _ptr(ws, dtype=torch.uint8, name="ws"), nbytes, _stream())
     _check(st, "pdmp_fit_occupancy")
     return w, float(b.value), float(loss.value), float(alpha.value)
+
+
+# ---------------------------------------------------------------------------
+# many environments in one persistent launch
+class _Env(ctypes.Structure):
+    _fields_ = [("field", _Field), ("x0", ctypes.c_void_p), ("xT", ctypes.c_void_p), ("N", ctypes.c_int64),
+                ("eta", ctypes.c_float), ("T", ctypes.c_int32)]
+
+
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("n_envs", ctypes.c_int32), ("variant", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("smem_bytes", ctypes.c_size_t), ("n_units", ctypes.c_int64),
+                ("total_N", ctypes.c_int64), ("total_M", ctypes.c_int64), ("total_cells", ctypes.c_int64),
+                ("nchunks", ctypes.c_int64), ("ws_bytes", ctypes.c_size_t), ("work", ctypes.c_double),
+                ("off", ctypes.c_size_t * 12)]
+
+
+def _batch_sigs():
+    L = lib()
+    if getattr(L, "_batch_ready", False):
+        return L
+    EP = ctypes.POINTER(_Env)
+    PP = ctypes.POINTER(BatchPlan)
+    L.pdmp_batch_variants.restype = _i32
+    L.pdmp_batch_workspace.argtypes = [EP, _i32, _i32]
+    L.pdmp_batch_workspace.restype = _sz
+    for name, argt in {
+        "pdmp_batch_prepare": [EP, _i32, _i32, _P, _sz, PP, _P],
+        "pdmp_morph_batched": [PP, _P, _P],
+        "pdmp_batch_autotune": [EP, _i32, _i32, _P, _sz, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float), PP,
+                                _P],
+        "pdmp_batch_graph_create": [PP, _P, _P, ctypes.POINTER(ctypes.c_void_p)],
+        "pdmp_graph_launch": [_P, _P],
+        "pdmp_graph_destroy": [_P],
+    }.items():
+        fn = getattr(L, name)
+        fn.argtypes = argt
+        fn.restype = _i32
+    L._batch_ready = True
+    return L
+
+
+class Batch:
+    """Several environments (RBF fields in 2-D or 3-D, each with its own
+    samples, step size and step count) morphed by one persistent launch.
+
+    envs: list of (DeviceField, x0 (N x d CUDA tensor), eta, T).  Outputs are
+    written to ``self.outputs`` (one tensor per environment).  ``prepare`` picks
+    a tile shape (``autotune`` times all of them; results are cached in a JSON
+    file keyed by the environments' shapes), ``run`` launches, ``capture``
+    builds a CUDA graph of ``run`` on a side stream and ``replay`` launches it.
+    """
+
+    def __init__(self, envs, cache_path: str | None = None):
+        self.fields = [e[0] for e in envs]
+        self.inputs = [e[1] for e in envs]
+        self.outputs = [torch.empty_like(e[1]) for e in envs]
+        self.etas = [float(e[2]) for e in envs]
+        self.Ts = [int(e[3]) for e in envs]
+        n = len(envs)
+        self._structs = [f.struct() for f in self.fields]
+        self._envs = (_Env * n)()
+        for i in range(n):
+            self._envs[i].field = self._structs[i]
+            self._envs[i].x0 = self.inputs[i].data_ptr() if self.inputs[i].numel() else None
+            self._envs[i].xT = self.outputs[i].data_ptr() if self.outputs[i].numel() else None
+            self._envs[i].N = int(self.inputs[i].shape[0])
+            self._envs[i].eta = self.etas[i]
+            self._envs[i].T = self.Ts[i]
+        self.n = n
+        self.plan = BatchPlan()
+        self.ws = None
+        self.graph = None
+        self.cache_path = cache_path or os.environ.get(
+            "PDMP_AUTOTUNE_CACHE", os.path.join(os.path.dirname(_build.LIB), "autotune.json"))
+        L = _batch_sigs()
+        self.n_variants = int(L.pdmp_batch_variants())
+        need = max(int(L.pdmp_batch_workspace(self._envs, n, v)) for v in range(self.n_variants))
+        if need == 0:
+            raise PdmpError(1, "pdmp_batch_workspace")
+        self.ws = torch.empty(need, dtype=torch.uint8, device=self.inputs[0].device)
+
+    def signature(self) -> str:
+        import hashlib
+        h = hashlib.sha256()
+        for f, x, T in zip(self.fields, self.inputs, self.Ts):
+            h.update(f"{f.d},{f.M},{x.shape[0]},{T};".encode())
+        return f"{torch.cuda.get_device_name()}|{self.n}|{h.hexdigest()[:20]}"
+
+    def prepare(self, variant: int = 0):
+        L = _batch_sigs()
+        st = L.pdmp_batch_prepare(self._envs, self.n, int(variant), ctypes.c_void_p(self.ws.data_ptr()),
+                                  self.ws.numel(), ctypes.byref(self.plan), _stream())
+        _check(st, "pdmp_batch_prepare")
+        return self.plan
+
+    def autotune(self, reps: int = 2, use_cache: bool = True):
+        """(best variant, times in ms per variant or None when read from the cache)."""
+        import json
+        key = self.signature()
+        cache = {}
+        if use_cache and os.path.exists(self.cache_path):
+            try:
+                with open(self.cache_path) as f:
+                    cache = json.load(f)
+            except (OSError, ValueError):
+                cache = {}
+        if use_cache and key in cache:
+            best = int(cache[key]["variant"])
+            self.prepare(best)
+            return best, None
+        L = _batch_sigs()
+        best = _i32(-1)
+        times = (ctypes.c_float * self.n_variants)()
+        st = L.pdmp_batch_autotune(self._envs, self.n, int(reps), ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                   ctypes.byref(best), times, ctypes.byref(self.plan), _stream())
+        _check(st, "pdmp_batch_autotune")
+        tl = [float(t) for t in times]
+        cache[key] = {"variant": int(best.value), "times_ms": tl}
+        try:
+            os.makedirs(os.path.dirname(self.cache_path), exist_ok=True)
+            tmp = self.cache_path + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, self.cache_path)
+        except OSError:
+            pass
+        return int(best.value), tl
+
+    def run(self):
+        L = _batch_sigs()
+        _check(L.pdmp_morph_batched(ctypes.byref(self.plan), ctypes.c_void_p(self.ws.data_ptr()), _stream()),
+               "pdmp_morph_batched")
+        return self.outputs
+
+    def capture(self, stream: torch.cuda.Stream | None = None):
+        """Captures run() into a CUDA graph on a side stream."""
+        L = _batch_sigs()
+        self.graph_stream = stream or torch.cuda.Stream()
+        self.graph_stream.wait_stream(torch.cuda.current_stream())
+        ex = ctypes.c_void_p()
+        st = L.pdmp_batch_graph_create(ctypes.byref(self.plan), ctypes.c_void_p(self.ws.data_ptr()),
+                                       ctypes.c_void_p(self.graph_stream.cuda_stream), ctypes.byref(ex))
+        _check(st, "pdmp_batch_graph_create")
+        self.graph = ex
+        return ex
+
+    def replay(self):
+        L = _batch_sigs()
+        _check(L.pdmp_graph_launch(self.graph, _stream()), "pdmp_graph_launch")
+        return self.outputs
+
+    def work(self) -> float:
+        return float(self.plan.work)
+
+    def __del__(self):
+        try:
+            if self.graph is not None and _lib is not None:
+                _lib.pdmp_graph_destroy(self.graph)
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate (MLP 3 -> 128 -> 128 -> 128 -> 3, BF16 tensor cores)
+MLP_NW, MLP_NB, MLP_H = 33536, 387, 128
+
+
+class _Mlp(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_void_p), ("b", ctypes.c_void_p), ("W_bf16", ctypes.c_void_p),
+                ("Wt_bf16", ctypes.c_void_p), ("adam", ctypes.c_void_p), ("lo", ctypes.c_float * 3),
+                ("in_scale", ctypes.c_float * 3), ("out_scale", ctypes.c_float * 3)]
+
+
+def _mlp_sigs():
+    L = lib()
+    if getattr(L, "_mlp_ready", False):
+        return L
+    MP = ctypes.POINTER(_Mlp)
+    for name, argt in {
+        "pdmp_mlp_refresh": [MP, _P],
+        "pdmp_mlp_forward": [MP, _P, _i64, _P, _P],
+        "pdmp_mlp_train_step": [MP, _P, _P, _i32, _f32, _f32, _f32, _f32, _i32, _P, _P, _sz, _P],
+        "pdmp_surrogate_infer": [MP, _FP, _P, _i64, _i32, _f32, _f32, _P, ctypes.POINTER(_i64), _P, _sz, _P],
+        "pdmp_displacement_rms": [_P, _P, _i64, _i32, _P, _P],
+    }.items():
+        fn = getattr(L, name)
+        fn.argtypes = argt
+        fn.restype = _i32
+    L.pdmp_mlp_train_workspace.argtypes = [_i32]
+    L.pdmp_mlp_train_workspace.restype = _sz
+    L.pdmp_surrogate_workspace.argtypes = [_FP, _i64]
+    L.pdmp_surrogate_workspace.restype = _sz
+    L._mlp_ready = True
+    return L
+
+
+def displacement_rms(x0: torch.Tensor, xT: torch.Tensor) -> torch.Tensor:
+    L = _mlp_sigs()
+    out = torch.empty(x0.shape[1], device=x0.device, dtype=torch.float32)
+    _check(L.pdmp_displacement_rms(_ptr(x0), _ptr(xT, shape=x0.shape), x0.shape[0], x0.shape[1], _ptr(out), _stream()),
+           "pdmp_displacement_rms")
+    return out
+
+
+class Surrogate:
+    """The surrogate network: FP32 master weights, BF16 copies and Adam state
+    on the GPU; normalisation from the workspace box [lo, hi] and the output
+    scale (root mean square displacement of the training pairs)."""
+
+    def __init__(self, lo, hi, out_scale, seed: int = 0, device="cuda"):
+        import numpy as np
+        g = np.random.Generator(np.random.Philox(key=np.array([seed, 0x5eed], dtype=np.uint64)))
+        H = MLP_H
+        shapes = [(H, 3), (H, H), (H, H), (3, H)]
+        Ws = [g.uniform(-1.0, 1.0, s) * np.sqrt(3.0 / s[1]) for s in shapes]   # unit-variance outputs
+        Ws[-1] *= 0.1
+        self.W = torch.tensor(np.concatenate([w.ravel() for w in Ws]), dtype=torch.float32, device=device)
+        self.b = torch.zeros(MLP_NB, dtype=torch.float32, device=device)
+        self.W_bf16 = torch.empty(MLP_NW, dtype=torch.int16, device=device)
+        self.Wt_bf16 = torch.empty(2 * H * H, dtype=torch.int16, device=device)
+        self.adam = torch.zeros(2 * MLP_NW + 2 * MLP_NB, dtype=torch.float32, device=device)
+        lo = [float(v) for v in lo]
+        hi = [float(v) for v in hi]
+        self.lo = lo
+        self.in_scale = [2.0 / (h - l) for l, h in zip(lo, hi)]
+        self.out_scale = [float(v) for v in out_scale]
+        self.step = 0
+        self._ws = None
+        self.refresh()
+
+    def struct(self) -> _Mlp:
+        m = _Mlp()
+        m.W, m.b = self.W.data_ptr(), self.b.data_ptr()
+        m.W_bf16, m.Wt_bf16, m.adam = self.W_bf16.data_ptr(), self.Wt_bf16.data_ptr(), self.adam.data_ptr()
+        for i in range(3):
+            m.lo[i], m.in_scale[i], m.out_scale[i] = self.lo[i], self.in_scale[i], self.out_scale[i]
+        return m
+
+    def refresh(self):
+        m = self.struct()
+        _check(_mlp_sigs().pdmp_mlp_refresh(ctypes.byref(m), _stream()), "pdmp_mlp_refresh")
+
+    def weights(self):
+        """FP32 master weights and biases as numpy arrays, per layer."""
+        H = MLP_H
+        W = self.W.cpu().numpy()
+        b = self.b.cpu().numpy()
+        sizes = [(H, 3), (H, H), (H, H), (3, H)]
+        out_w, out_b, o = [], [], 0
+        for s in sizes:
+            out_w.append(W[o:o + s[0] * s[1]].reshape(s))
+            o += s[0] * s[1]
+        out_b = [b[0:H], b[H:2 * H], b[2 * H:3 * H], b[3 * H:3 * H + 3]]
+        return out_w, out_b
+
+    def bf16_weights(self):
+        """The BF16 weights the kernels use, upcast to float64 numpy arrays."""
+        import numpy as np
+        H = MLP_H
+        bits = self.W_bf16.cpu().numpy().astype(np.uint16).astype(np.uint32) << 16
+        W = bits.view(np.float32).astype(np.float64)
+        sizes = [(H, 3), (H, H), (H, H), (3, H)]
+        out, o = [], 0
+        for s in sizes:
+            out.append(W[o:o + s[0] * s[1]].reshape(s))
+            o += s[0] * s[1]
+        return out
+
+    def forward(self, x0: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty_like(x0)
+        m = self.struct()
+        _check(_mlp_sigs().pdmp_mlp_forward(ctypes.byref(m), _ptr(x0, name="x0"), x0.shape[0],
+                                            _ptr(out, shape=x0.shape, name="out"), _stream()), "pdmp_mlp_forward")
+        return out
+
+    def train_step(self, x0: torch.Tensor, xT: torch.Tensor, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                   loss: torch.Tensor | None = None):
+        L = _mlp_sigs()
+        B = x0.shape[0]
+        need = int(L.pdmp_mlp_train_workspace(B))
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=x0.device)
+        self.step += 1
+        m = self.struct()
+        _check(L.pdmp_mlp_train_step(ctypes.byref(m), _ptr(x0, name="x0"), _ptr(xT, shape=x0.shape, name="xT"), B,
+                                     float(lr), float(beta1), float(beta2), float(eps), self.step,
+                                     _ptr(loss, name="loss"), ctypes.c_void_p(self._ws.data_ptr()), self._ws.numel(),
+                                     _stream()), "pdmp_mlp_train_step")
+        return loss
+
+    def infer(self, field: DeviceField, x0: torch.Tensor, T: int, eta: float, tau_r: float,
+              out: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+        """(x_T, number of samples that fell back to the plain morph)."""
+        L = _mlp_sigs()
+        N = x0.shape[0]
+        if out is None:
+            out = torch.empty_like(x0)
+        f = field.struct()
+        need = int(L.pdmp_surrogate_workspace(ctypes.byref(f), N))
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 16), dtype=torch.uint8, device=x0.device)
+        nf = _i64(0)
+        m = self.struct()
+        _check(L.pdmp_surrogate_infer(ctypes.byref(m), ctypes.byref(f), _ptr(x0, name="x0"), N, int(T), float(eta),
+                                      float(tau_r), _ptr(out, shape=x0.shape, name="out"), ctypes.byref(nf),
+                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()), "pdmp_surrogate_infer")
+        return out, int(nf.value)
+
+
+# ---------------------------------------------------------------------------
+# autograd through the Euler chain
+class _MorphFn(torch.autograd.Function):
+    """x_T = morph(x_0; w, bias): forward by pdmp_morph with checkpoints every
+    k steps, backward by pdmp_morph_vjp from them (and d/dw, d/dbias when the
+    weights require gradients).  No PyTorch arithmetic on the path."""
+
+    @staticmethod
+    def forward(ctx, x0, w, bias, field, T, eta, k):
+        fld = field.with_weights(w.detach(), bias=float(bias.detach()) if bias is not None else field.bias)
+        ck = torch.empty(T // k, x0.shape[0], field.d, device=x0.device, dtype=torch.float32) if T else None
+        xT = morph(fld, x0.detach().contiguous(), T, eta, ckpt=ck, k=k if T else 0)
+        ctx.fld, ctx.T, ctx.eta, ctx.k = fld, T, eta, k
+        ctx.save_for_backward(x0.detach(), ck if ck is not None else torch.empty(0, device=x0.device))
+        return xT
+
+    @staticmethod
+    def backward(ctx, gT):
+        x0, ck = ctx.saved_tensors
+        want_w = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+        if ctx.T == 0:
+            gw = torch.zeros(ctx.fld.M, device=x0.device) if ctx.needs_input_grad[1] else None
+            gb = torch.zeros((), device=x0.device) if ctx.needs_input_grad[2] else None
+            return gT, gw, gb, None, None, None, None
+        res = morph_vjp(ctx.fld, x0, ctx.T, ctx.eta, ctx.k, gT.contiguous(), ckpt=ck, want_param_grad=want_w)
+        if want_w:
+            g0, gw, gb = res
+            return (g0, gw if ctx.needs_input_grad[1] else None, gb.reshape(()) if ctx.needs_input_grad[2] else None,
+                    None, None, None, None)
+        return res, None, None, None, None, None, None
+
+
+def morph_autograd(field: DeviceField, x0: torch.Tensor, T: int, eta: float, k: int = 1,
+                   w: torch.Tensor | None = None, bias: torch.Tensor | None = None) -> torch.Tensor:
+    """Differentiable morph: gradients flow to x0 and, when given as tensors
+    that require grad, to the weights w (M) and the bias (a 0-d tensor)."""
+    if T % max(k, 1) != 0:
+        raise ValueError("k must divide T")
+    w = field.w if w is None else w
+    if bias is None:
+        bias = torch.tensor(field.bias, device=x0.device, dtype=torch.float32)
+    return _MorphFn.apply(x0, w, bias, field, int(T), float(eta), int(k))

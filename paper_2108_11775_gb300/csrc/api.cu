@@ -223,6 +223,194 @@ pdmp_status pdmp_lipschitz_bound(const pdmp_field* f, const double* lo, const do
   return cuda_status(pdmp::lipschitz_bound(f->kind, f->d, field_args(f), lo, hi, cells, L, G, as_stream(stream)));
 }
 
+int32_t pdmp_batch_variants(void) { return pdmp::batch_variants(); }
+
+static pdmp_status check_envs(const pdmp_env* envs, int32_t n) {
+  if (envs == nullptr || n < 1) return PDMP_ERR_INVALID_ARG;
+  int64_t total = 0;
+  for (int32_t e = 0; e < n; ++e) {
+    const pdmp_env& E = envs[e];
+    pdmp_status s = check_field(&E.field);
+    if (s != PDMP_OK) return s;
+    if (E.field.kind != PDMP_KIND_RBF || (E.field.d != 2 && E.field.d != 3)) return PDMP_ERR_UNSUPPORTED;
+    if ((s = check_step(&E.field, E.eta)) != PDMP_OK) return s;
+    if (E.N < 0 || E.T < 0) return PDMP_ERR_INVALID_ARG;
+    if (E.N > 0 && (!ok_ptr(E.x0, true) || !ok_ptr(E.xT, true))) return PDMP_ERR_INVALID_ARG;
+    total += E.N;
+  }
+  if (total >= ((int64_t)1 << 31)) return PDMP_ERR_INVALID_ARG;
+  return PDMP_OK;
+}
+
+size_t pdmp_batch_workspace(const pdmp_env* envs, int32_t n_envs, int32_t variant) {
+  if (check_envs(envs, n_envs) != PDMP_OK || variant < 0 || variant >= pdmp::batch_variants()) return 0;
+  return pdmp::batch_workspace(envs, n_envs, variant);
+}
+
+pdmp_status pdmp_batch_prepare(const pdmp_env* envs, int32_t n_envs, int32_t variant, void* ws, size_t ws_bytes,
+                               pdmp_batch_plan* plan, void* stream) {
+  pdmp_status s = check_envs(envs, n_envs);
+  if (s != PDMP_OK) return s;
+  if (variant < 0 || variant >= pdmp::batch_variants() || plan == nullptr) return PDMP_ERR_INVALID_ARG;
+  if (ws == nullptr || !aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::batch_workspace(envs, n_envs, variant)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  if (pdmp::batch_workspace(envs, n_envs, variant) == 0) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::batch_prepare(envs, n_envs, variant, ws, plan, as_stream(stream)));
+}
+
+pdmp_status pdmp_morph_batched(const pdmp_batch_plan* plan, void* ws, void* stream) {
+  if (plan == nullptr || ws == nullptr || !aligned16(ws) || plan->n_envs < 1) return PDMP_ERR_INVALID_ARG;
+  if (plan->variant < 0 || plan->variant >= pdmp::batch_variants()) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::batch_run(plan, ws, as_stream(stream)));
+}
+
+pdmp_status pdmp_batch_autotune(const pdmp_env* envs, int32_t n_envs, int32_t reps, void* ws, size_t ws_bytes,
+                                int32_t* best, float* times_ms, pdmp_batch_plan* plan, void* stream) {
+  pdmp_status s = check_envs(envs, n_envs);
+  if (s != PDMP_OK) return s;
+  if (best == nullptr || plan == nullptr || reps < 1 || ws == nullptr || !aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+  const int nv = pdmp::batch_variants();
+  for (int v = 0; v < nv; ++v)
+    if (ws_bytes < pdmp::batch_workspace(envs, n_envs, v)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = as_stream(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PDMP_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PDMP_ERR_CUDA;
+  }
+  int bestv = -1;
+  float bestt = 0.0f;
+  pdmp_status out = PDMP_OK;
+  for (int v = 0; v < nv && out == PDMP_OK; ++v) {
+    pdmp_batch_plan p;
+    if (pdmp::batch_prepare(envs, n_envs, v, ws, &p, st) != cudaSuccess) { out = PDMP_ERR_CUDA; break; }
+    if (pdmp::batch_run(&p, ws, st) != cudaSuccess) { out = PDMP_ERR_CUDA; break; }
+    float tmin = 0.0f;
+    for (int r = 0; r < reps; ++r) {
+      float ms = 0.0f;
+      if (cudaEventRecord(e0, st) != cudaSuccess || pdmp::batch_run(&p, ws, st) != cudaSuccess ||
+          cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        out = PDMP_ERR_CUDA;
+        break;
+      }
+      if (r == 0 || ms < tmin) tmin = ms;
+    }
+    if (times_ms) times_ms[v] = tmin;
+    if (bestv < 0 || tmin < bestt) {
+      bestv = v;
+      bestt = tmin;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out != PDMP_OK) return out;
+  *best = bestv;
+  return cuda_status(pdmp::batch_prepare(envs, n_envs, bestv, ws, plan, st));
+}
+
+pdmp_status pdmp_batch_graph_create(const pdmp_batch_plan* plan, void* ws, void* stream, void** graph_exec) {
+  if (plan == nullptr || ws == nullptr || graph_exec == nullptr || stream == nullptr) return PDMP_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PDMP_ERR_CUDA;
+  cudaError_t run = pdmp::batch_run(plan, ws, st);
+  cudaGraph_t g = nullptr;
+  cudaError_t end = cudaStreamEndCapture(st, &g);
+  if (run != cudaSuccess || end != cudaSuccess || g == nullptr) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return PDMP_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t inst = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (inst != cudaSuccess) return PDMP_ERR_CUDA;
+  *graph_exec = (void*)ex;
+  return PDMP_OK;
+}
+
+pdmp_status pdmp_graph_launch(void* graph_exec, void* stream) {
+  if (graph_exec == nullptr) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(cudaGraphLaunch((cudaGraphExec_t)graph_exec, as_stream(stream)));
+}
+
+pdmp_status pdmp_graph_destroy(void* graph_exec) {
+  if (graph_exec == nullptr) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(cudaGraphExecDestroy((cudaGraphExec_t)graph_exec));
+}
+
+static pdmp_status check_mlp(const pdmp_mlp* net, bool training) {
+  if (net == nullptr) return PDMP_ERR_INVALID_ARG;
+  if (!ok_ptr(net->W_bf16, true) || !ok_ptr(net->b, true) || !ok_ptr(net->Wt_bf16, training)) return PDMP_ERR_INVALID_ARG;
+  if (training && (!ok_ptr(net->W, true) || !ok_ptr(net->adam, true))) return PDMP_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(net->lo[i]) || !std::isfinite(net->in_scale[i]) || !(net->out_scale[i] != 0.0f) ||
+        !std::isfinite(net->out_scale[i]))
+      return PDMP_ERR_INVALID_ARG;
+  return PDMP_OK;
+}
+
+pdmp_status pdmp_mlp_refresh(const pdmp_mlp* net, void* stream) {
+  if (net == nullptr || !ok_ptr(net->W, true) || !ok_ptr(net->W_bf16, true) || !ok_ptr(net->Wt_bf16, true))
+    return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::mlp_refresh(net, as_stream(stream)));
+}
+
+pdmp_status pdmp_mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* xT_hat, void* stream) {
+  pdmp_status s = check_mlp(net, false);
+  if (s != PDMP_OK) return s;
+  if (N < 0) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT_hat, true)) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::mlp_forward(net, x0, N, xT_hat, as_stream(stream)));
+}
+
+size_t pdmp_mlp_train_workspace(int32_t B) { return B < 1 ? 0 : pdmp::mlp_train_workspace(B); }
+
+pdmp_status pdmp_mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int32_t B, float lr,
+                                float beta1, float beta2, float eps, int32_t step, float* loss, void* ws,
+                                size_t ws_bytes, void* stream) {
+  pdmp_status s = check_mlp(net, true);
+  if (s != PDMP_OK) return s;
+  if (B < 1 || step < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+      !(eps > 0.0f))
+    return PDMP_ERR_INVALID_ARG;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || !ok_ptr(loss, false) || ws == nullptr || !aligned16(ws))
+    return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::mlp_train_workspace(B)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  return cuda_status(pdmp::mlp_train_step(net, x0, xT, B, lr, beta1, beta2, eps, step, loss, ws, as_stream(stream)));
+}
+
+pdmp_status pdmp_displacement_rms(const float* x0, const float* xT, int64_t N, int32_t d, float* rms, void* stream) {
+  if (N < 1 || d < 1 || d > 8 || !ok_ptr(x0, true) || !ok_ptr(xT, true) || rms == nullptr) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::displacement_rms(x0, xT, N, d, rms, as_stream(stream)));
+}
+
+size_t pdmp_surrogate_workspace(const pdmp_field* f, int64_t N) {
+  if (check_field(f) != PDMP_OK || f->kind != PDMP_KIND_RBF || f->d != 3 || N < 1) return 0;
+  return pdmp::surrogate_workspace(f->d, f->M, N);
+}
+
+pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const float* x0, int64_t N, int32_t T,
+                                 float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  pdmp_status s = check_mlp(net, false);
+  if (s != PDMP_OK) return s;
+  if ((s = check_field(f)) != PDMP_OK) return s;
+  if (f->kind != PDMP_KIND_RBF || f->d != 3) return PDMP_ERR_UNSUPPORTED;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0 || n_fallback == nullptr || !(tau_r >= 0.0f)) return PDMP_ERR_INVALID_ARG;
+  if (N >= ((int64_t)1 << 31)) return PDMP_ERR_INVALID_ARG;
+  *n_fallback = 0;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || ws == nullptr || !aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+  if (xT == x0) return PDMP_ERR_INVALID_ARG;   // the fallback re-reads x0 after xT is written
+  if (ws_bytes < pdmp::surrogate_workspace(f->d, f->M, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  return cuda_status(pdmp::surrogate_infer(net, f->d, field_args(f), x0, N, T, eta, tau_r, xT, n_fallback, ws,
+                                           as_stream(stream)));
+}
+
 size_t pdmp_fit_workspace(int64_t M, int64_t n) {
   if (M < 1 || n < 1) return 0;
   return pdmp::fit_workspace(M, n);

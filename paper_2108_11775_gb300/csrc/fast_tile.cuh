@@ -1,0 +1,404 @@
+// Per-tile device code of the fast RBF morph (d = 2, 3), shared by the
+// single-field launch (morph_rbf_fast.cu) and the batched launch (batch.cu).
+//
+#pragma once
+#include "field.cuh"
+
+namespace pdmp {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk(u64 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 ex2x2(u64 a) {
+  float lo, hi;
+  upk(a, lo, hi);
+  return pk(ex2_approx(lo), ex2_approx(hi));
+}
+
+// Tile shape: W warps per block (each summing over its share of M) and K
+// samples per lane (even: f32x2 pairs).  The single-field launch uses
+// W = 4, K = 8; the batched launch picks among a few shapes (autotuned).
+constexpr int kFastStage = 256;                // centres per shared-memory stage
+constexpr int kFastUnroll = 2;                 // centres per unrolled inner iteration
+
+template <int W, int K>
+struct Shape {
+  static_assert(K % 2 == 0, "samples per lane must be even (f32x2 pairs)");
+  static_assert(kFastStage % W == 0, "a stage must split evenly across the warps");
+  static constexpr int kWarps = W, kThreads = 32 * W, kK = K, kPairs = K / 2, kTile = 32 * K;
+  static constexpr int kSlice = kFastStage / W;
+  static constexpr int kMinBlocks = 16 / W;    // 16 warps per SM
+};
+
+template <int D>
+struct FastRec {
+  static constexpr int kPairs = 2 * D + 2;     // u64 pairs per staged centre
+  static constexpr int kTab = D == 2 ? 1 : 2;  // float4s per centre in the table
+};
+
+// Shared memory of one tile: two stages of transformed records, aliased
+// after the last stage of a step by the cross-warp reduction buffer, then the
+// raw table entries of the stage being prefetched.
+template <int D>
+__host__ __device__ constexpr size_t fast_bufs_bytes() {
+  return 2 * (size_t)kFastStage * FastRec<D>::kPairs * sizeof(u64);
+}
+template <int W, int K>
+__host__ __device__ constexpr size_t fast_red_bytes() {
+  return (size_t)W * (32 * K) * sizeof(float4);
+}
+template <int D, int W, int K>
+__host__ __device__ constexpr size_t fast_region0_bytes() {
+  return fast_bufs_bytes<D>() > fast_red_bytes<W, K>() ? fast_bufs_bytes<D>() : fast_red_bytes<W, K>();
+}
+template <int D, int W, int K>
+__host__ __device__ constexpr size_t fast_smem_bytes() {
+  return fast_region0_bytes<D, W, K>() + (size_t)kFastStage * FastRec<D>::kTab * sizeof(float4);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// table: RBF centre records {mu_0 .. mu_{d-1}, lw = log2|w|, sg = sign(w)}
+template <int D>
+__global__ void k_rbf_table(const float* __restrict__ centres, const float* __restrict__ w, int64_t M,
+                            float4* __restrict__ tab) {
+  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  float wm = w[m];
+  float lw = wm != 0.0f ? log2f(fabsf(wm)) : -INFINITY;
+  float sg = wm > 0.0f ? 1.0f : (wm < 0.0f ? -1.0f : 0.0f);
+  if (D == 2) {
+    tab[m] = make_float4(centres[m * 2], centres[m * 2 + 1], lw, sg);
+  } else {
+    tab[2 * m] = make_float4(centres[m * 3], centres[m * 3 + 1], centres[m * 3 + 2], lw);
+    tab[2 * m + 1] = make_float4(sg, 0.0f, 0.0f, 0.0f);
+  }
+}
+
+// Copies the table entries of centres [m0, m0 + kFastStage) into raw
+// (asynchronously; each thread copies the entries it later transforms).
+template <int D, int NT>
+__device__ __forceinline__ void stage_prefetch(const float4* __restrict__ tab, int64_t M, int64_t m0, float4* raw) {
+  constexpr int KT = FastRec<D>::kTab;
+  for (int i = threadIdx.x; i < kFastStage; i += NT) {
+    const int64_t m = m0 + i;
+    if (m < M)
+#pragma unroll
+      for (int q = 0; q < KT; ++q) cp_async16(raw + i * KT + q, tab + KT * m + q);
+  }
+  cp_async_commit();
+}
+
+// Waits for this thread's prefetched entries and writes the records of
+// centres [m0, m0 + kFastStage) into rec (kFastStage x kPairs u64).
+//   expanded: [a a][b_0 b_0]..[b_{d-1} ..][sg sg][c~_0 c~_0]..  (c~ = sg (mu - o))
+//   direct:   [-mu_0 -mu_0]..[-mu_{d-1} ..][lw lw][sg sg]
+template <int D, int NT>
+__device__ __forceinline__ void stage_build(int64_t M, int64_t m0, bool expanded, const float* o, float gl2e,
+                                            const float4* raw, u64* rec) {
+  constexpr int RP = FastRec<D>::kPairs;
+  constexpr int KT = FastRec<D>::kTab;
+  cp_async_wait_all();
+  for (int i = threadIdx.x; i < kFastStage; i += NT) {
+    const int64_t m = m0 + i;
+    float mu[D], lw = -INFINITY, sg = 0.0f;
+    if (m < M) {
+      const float4 t0 = raw[i * KT];
+      mu[0] = t0.x;
+      mu[1] = t0.y;
+      if (D == 2) {
+        lw = t0.z;
+        sg = t0.w;
+      } else {
+        mu[2] = t0.z;
+        lw = t0.w;
+        sg = raw[i * KT + 1].x;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) mu[j] = 0.0f;
+    }
+    u64 r[RP];
+    if (expanded) {
+      float c[D], r2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        c[j] = mu[j] - o[j];
+        r2 = fmaf(c[j], c[j], r2);
+      }
+      float a = fmaf(-gl2e, r2, lw);
+      r[0] = pk(a, a);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float b = 2.0f * gl2e * c[j];
+        r[1 + j] = pk(b, b);
+        float ct = sg * c[j];
+        r[D + 2 + j] = pk(ct, ct);
+      }
+      r[D + 1] = pk(sg, sg);
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) r[j] = pk(-mu[j], -mu[j]);
+      r[D] = pk(lw, lw);
+      r[D + 1] = pk(sg, sg);
+#pragma unroll
+      for (int j = D + 2; j < RP; ++j) r[j] = 0ull;
+    }
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(rec + (size_t)i * RP);
+#pragma unroll
+    for (int j = 0; j < RP / 2; ++j) dst[j] = make_ulonglong2(r[2 * j], r[2 * j + 1]);
+  }
+}
+
+// Arguments of one tile: a run of 256 (32 K) consecutive sorted positions
+// [p0, min(p0 + tile, p_end)) of one field's samples.  perm maps a sorted
+// position to a sample index; the sample's index in x0 / xT / ckpt / traj /
+// steps is perm[p] - perm_base, and those arrays hold N samples.
+struct TileArgs {
+  const float4* tab;
+  int64_t M;
+  float gamma, bias, eta;
+  int T;
+  const float* x0;
+  const int32_t* perm;
+  int64_t perm_base;
+  int64_t N;
+  float* xT;
+  float* ckpt;
+  int kck;
+  float* traj;
+  float* steps;
+  float* s_out;   // optional: the logit s(x_{T-1}) of the last step, per sample
+};
+
+template <int D, int W, int K, bool TRACE>
+__device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t p_end, unsigned char* smem) {
+  using S_ = Shape<W, K>;
+  constexpr int RP = FastRec<D>::kPairs;
+  constexpr int P = S_::kPairs;
+  constexpr int kTile = S_::kTile, kSlice = S_::kSlice;
+  u64* bufs = reinterpret_cast<u64*>(smem);
+  float4* red = reinterpret_cast<float4*>(smem);   // aliases bufs after a step's last stage
+  float4* raw = reinterpret_cast<float4*>(smem + fast_region0_bytes<D, W, K>());
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float4* __restrict__ tab = a.tab;
+  const int64_t M = a.M, N = a.N;
+  const float gamma = a.gamma, bias = a.bias, eta = a.eta;
+  const int T = a.T;
+  const float gl2e = gamma * kLog2e;
+  const int nstage = (int)((M + kFastStage - 1) / kFastStage);
+
+  float x[K][D];
+  bool act[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int64_t p = p0 + k * 32 + lane;
+    act[k] = p < p_end;
+    const int64_t n = act[k] ? (int64_t)a.perm[p] - a.perm_base : 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) x[k][j] = act[k] ? a.x0[n * D + j] : 0.0f;
+  }
+
+  for (int t = 0; t < T; ++t) {
+    // tile origin and half-diagonal (identical in every warp)
+    float lo[D], hi[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) { lo[j] = INFINITY; hi[j] = -INFINITY; }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (act[k])
+#pragma unroll
+        for (int j = 0; j < D; ++j) { lo[j] = fminf(lo[j], x[k][j]); hi[j] = fmaxf(hi[j], x[k][j]); }
+    float o[D], R2 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], s));
+        hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], s));
+      }
+      o[j] = 0.5f * (lo[j] + hi[j]);
+      float h = 0.5f * (hi[j] - lo[j]);
+      R2 = fmaf(h, h, R2);
+    }
+    const bool expanded = (gl2e * R2 <= 4.0f) && (o[0] == o[0]);
+    if (!expanded)
+#pragma unroll
+      for (int j = 0; j < D; ++j) o[j] = 0.0f;
+
+    u64 U[P][D], S[P], G[P][D];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        U[i][j] = pk(x[2 * i][j] - o[j], x[2 * i + 1][j] - o[j]);
+        G[i][j] = 0ull;
+      }
+      S[i] = 0ull;
+    }
+
+    stage_prefetch<D, S_::kThreads>(tab, M, 0, raw);
+    stage_build<D, S_::kThreads>(M, 0, expanded, o, gl2e, raw, bufs);
+    __syncthreads();
+    for (int st = 0; st < nstage; ++st) {
+      if (st + 1 < nstage) stage_prefetch<D, S_::kThreads>(tab, M, (int64_t)(st + 1) * kFastStage, raw);
+      const u64* rec = bufs + (size_t)(st & 1) * kFastStage * RP + (size_t)warp * kSlice * RP;
+      if (expanded) {
+#pragma unroll kFastUnroll
+        for (int c = 0; c < kSlice; ++c) {
+          const ulonglong2* q = reinterpret_cast<const ulonglong2*>(rec + (size_t)c * RP);
+          u64 r[RP];
+#pragma unroll
+          for (int j = 0; j < RP / 2; ++j) {
+            ulonglong2 v = q[j];
+            r[2 * j] = v.x;
+            r[2 * j + 1] = v.y;
+          }
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            u64 arg = fma2(r[1], U[i][0], r[0]);
+#pragma unroll
+            for (int j = 1; j < D; ++j) arg = fma2(r[1 + j], U[i][j], arg);
+            const u64 e = ex2x2(arg);
+            S[i] = fma2(r[D + 1], e, S[i]);
+#pragma unroll
+            for (int j = 0; j < D; ++j) G[i][j] = fma2(e, r[D + 2 + j], G[i][j]);
+          }
+        }
+      } else {
+        const u64 ng = pk(-gl2e, -gl2e);
+        for (int c = 0; c < kSlice; ++c) {
+          const u64* r = rec + (size_t)c * RP;
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            u64 dx[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) dx[j] = add2(U[i][j], r[j]);
+            u64 r2 = mul2(dx[0], dx[0]);
+#pragma unroll
+            for (int j = 1; j < D; ++j) r2 = fma2(dx[j], dx[j], r2);
+            const u64 we = mul2(r[D + 1], ex2x2(fma2(r2, ng, r[D])));
+            S[i] = add2(S[i], we);
+#pragma unroll
+            for (int j = 0; j < D; ++j) G[i][j] = fma2(we, dx[j], G[i][j]);
+          }
+        }
+      }
+      if (st + 1 < nstage)
+        stage_build<D, S_::kThreads>(M, (int64_t)(st + 1) * kFastStage, expanded, o, gl2e, raw,
+                                     bufs + (size_t)((st + 1) & 1) * kFastStage * RP);
+      __syncthreads();
+    }
+
+    // partial sums -> shared memory, then the same fixed-order total in every warp
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      float s0, s1, g0[D], g1[D];
+      upk(S[i], s0, s1);
+#pragma unroll
+      for (int j = 0; j < D; ++j) upk(G[i][j], g0[j], g1[j]);
+      red[warp * kTile + (2 * i) * 32 + lane] = make_float4(s0, g0[0], g0[1], D == 3 ? g0[D - 1] : 0.0f);
+      red[warp * kTile + (2 * i + 1) * 32 + lane] = make_float4(s1, g1[0], g1[1], D == 3 ? g1[D - 1] : 0.0f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float4 acc = red[k * 32 + lane];
+#pragma unroll
+      for (int w = 1; w < W; ++w) {
+        float4 b = red[w * kTile + k * 32 + lane];
+        acc.x += b.x;
+        acc.y += b.y;
+        acc.z += b.z;
+        acc.w += b.w;
+      }
+      const float Ssum = acc.x, Gs[3] = {acc.y, acc.z, acc.w};
+      float shat, ghat[D];
+      if (expanded) {
+        float u[D], u2 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          u[j] = x[k][j] - o[j];
+          u2 = fmaf(u[j], u[j], u2);
+        }
+        const float f = ex2_approx(-gl2e * u2);
+        shat = f * Ssum;
+#pragma unroll
+        for (int j = 0; j < D; ++j) ghat[j] = f * fmaf(u[j], Ssum, -Gs[j]);
+      } else {
+        shat = Ssum;
+#pragma unroll
+        for (int j = 0; j < D; ++j) ghat[j] = Gs[j];
+      }
+      float d1, d2;
+      sigmoid_d12(shat + bias, d1, d2);
+      const float c = -eta * d1;
+      const int64_t p = p0 + k * 32 + lane;
+      const bool own = act[k] && warp == 0;
+      const int64_t n = (own && (TRACE || a.s_out != nullptr)) ? (int64_t)a.perm[p] - a.perm_base : 0;
+      if (own && a.s_out != nullptr && t == T - 1) a.s_out[n] = shat + bias;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const float inc = __fmul_rn(c, -2.0f * gamma * ghat[j]);
+        if (TRACE && act[k] && warp == 0) {
+          a.traj[((int64_t)t * N + n) * D + j] = x[k][j];
+          a.steps[((int64_t)t * N + n) * D + j] = inc;
+        }
+        x[k][j] = __fadd_rn(x[k][j], inc);
+      }
+    }
+    __syncthreads();   // every warp has read the reduction buffer before the next step rebuilds the stages
+    if (a.ckpt != nullptr && (t + 1) % a.kck == 0 && warp == 0) {
+      float* dst = a.ckpt + (int64_t)((t + 1) / a.kck - 1) * N * D;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (act[k]) {
+          const int64_t n = (int64_t)a.perm[p0 + k * 32 + lane] - a.perm_base;
+#pragma unroll
+          for (int j = 0; j < D; ++j) dst[n * D + j] = x[k][j];
+        }
+    }
+  }
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (act[k]) {
+        const int64_t n = (int64_t)a.perm[p0 + k * 32 + lane] - a.perm_base;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          if (a.xT) a.xT[n * D + j] = x[k][j];
+          if (TRACE) a.traj[((int64_t)T * N + n) * D + j] = x[k][j];
+        }
+      }
+  }
+  __syncthreads();   // the next tile of this block reuses the shared memory
+}
+
+}  // namespace pdmp

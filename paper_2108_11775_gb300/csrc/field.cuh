@@ -13,8 +13,25 @@ namespace pdmp {
 // whose contributions are exactly zero.
 template <int D>
 struct RecLayout {
-  static constexpr int kFloats = D + 2;
+  static constexpr int kUsed = D + 2;                    // floats that carry data
+  static constexpr int kFloats = (kUsed + 3) / 4 * 4;    // padded to whole float4s
 };
+
+// Copies staged record i (kFloats floats, 16-byte aligned) into registers
+// with 128-bit shared-memory loads.
+template <int D>
+__device__ __forceinline__ void load_rec(const float* sm, int i, float* rec) {
+  constexpr int R = RecLayout<D>::kFloats;
+  const float4* q = reinterpret_cast<const float4*>(sm + i * R);
+#pragma unroll
+  for (int v = 0; v < R / 4; ++v) {
+    const float4 t = q[v];
+    rec[4 * v] = t.x;
+    rec[4 * v + 1] = t.y;
+    rec[4 * v + 2] = t.z;
+    rec[4 * v + 3] = t.w;
+  }
+}
 
 struct FieldArgs {
   const float* centres;
@@ -50,6 +67,8 @@ __device__ __forceinline__ void stage_tile(const FieldArgs& fa, int64_t m0, int 
       r[D] = KIND == PDMP_KIND_RBF ? -INFINITY : 0.0f;
       r[D + 1] = 0.0f;
     }
+#pragma unroll
+    for (int j = D + 2; j < R; ++j) r[j] = 0.0f;
   }
 }
 

@@ -12,8 +12,10 @@ cudaError_t morph_direct(int kind, int d, const FieldArgs& fa, const float* x0, 
                          float* xT, float* ckpt, int k, float* traj, float* steps, cudaStream_t st);
 // fast RBF path (d = 2, 3): spatially sorted tiles, expanded exponent, f32x2
 size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N);
+// s_out (optional): the logit at the last step's state, per sample
 cudaError_t morph_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
-                           float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
+                           float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st,
+                           float* s_out = nullptr);
 // workspace the dispatcher's fast path needs (0: the request takes the direct path)
 size_t morph_workspace(int kind, int d, int64_t M, int64_t N);
 // ws == nullptr selects the direct path
@@ -34,6 +36,25 @@ cudaError_t box_labels(int d, const float* boxes, int64_t nb, const float* x, in
 
 cudaError_t lipschitz_bound(int kind, int d, const FieldArgs& fa, const double* lo, const double* hi, int cells,
                             double* L, double* G, cudaStream_t st);
+
+int batch_variants();
+size_t batch_workspace(const pdmp_env* envs, int n, int variant);
+cudaError_t batch_prepare(const pdmp_env* envs, int n, int variant, void* ws, pdmp_batch_plan* plan,
+                          cudaStream_t st);
+cudaError_t batch_run(const pdmp_batch_plan* plan, void* ws, cudaStream_t st);
+
+// surrogate MLP (mlp.cu, surrogate.cu)
+constexpr int64_t kMlpNW = 3 * 128 + 2 * 128 * 128 + 3 * 128;   // weights W1, W2, W3, W4
+constexpr int64_t kMlpNB = 3 * 128 + 3;                         // biases b1, b2, b3, b4
+cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, cudaStream_t st);
+size_t mlp_train_workspace(int B);
+cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int B, float lr, float beta1,
+                           float beta2, float eps, int step, float* loss, void* ws, cudaStream_t st);
+cudaError_t mlp_refresh(const pdmp_mlp* net, cudaStream_t st);
+size_t surrogate_workspace(int d, int64_t M, int64_t N);
+cudaError_t displacement_rms(const float* x0, const float* xT, int64_t N, int d, float* rms, cudaStream_t st);
+cudaError_t surrogate_infer(const pdmp_mlp* net, int d, const FieldArgs& fa, const float* x0, int64_t N, int T,
+                            float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, cudaStream_t st);
 
 size_t fit_workspace(int64_t M, int64_t n);
 cudaError_t fit_occupancy(int kind, int d, const FieldArgs& geom, const float* X, const uint8_t* y, int64_t n,

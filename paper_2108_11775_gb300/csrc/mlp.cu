@@ -1,0 +1,536 @@
+// Learned surrogate of the T-step morph (no counterpart in the paper): an MLP
+// 3 -> 128 -> 128 -> 128 -> 3 with SiLU between the linear layers, predicting
+// the normalised displacement (x_T - x_0) / out_scale from the normalised
+// input u = (x_0 - lo) * in_scale - 1.  BF16 weights, FP32 accumulation.
+//
+// The two 128 x 128 layers and the output layer run on the tensor cores
+// (mma.sync m16n8k16, BF16 x BF16 -> FP32): a warp owns 16 samples, and the
+// accumulator fragments of one layer, after bias + SiLU and rounding to BF16,
+// are exactly the A fragments of the next layer, so activations never leave
+// registers.  The 3 -> 128 input layer is FP32 on the CUDA cores.
+//
+// Training: forward with saved pre-activations, backward through the same
+// fragment layouts (dA = dZ W on the tensor cores with transposed weight
+// copies), weight gradients as fixed-order FP32 sums over the batch, and Adam
+// on FP32 master weights that rewrites the BF16 copies.
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace pdmp {
+
+constexpr int kH = 128;          // hidden width
+constexpr int kRowU32 = 68;      // padded smem row: 136 bf16 = 68 words (conflict-free fragment loads)
+constexpr int kMlpWarps = 4;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad_f(float z) {
+  const float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+// Device copy of the network (all pointers device; bf16 as raw uint16).
+struct MlpArgs {
+  const uint16_t* W1;   // 128 x 3
+  const uint16_t* W2;   // 128 x 128  [out][in]
+  const uint16_t* W3;   // 128 x 128
+  const uint16_t* W4;   // 3 x 128
+  const uint16_t* W2t;  // 128 x 128  [in][out] (backward)
+  const uint16_t* W3t;  // 128 x 128
+  const float *b1, *b2, *b3, *b4;
+  float lo[3], in_scale[3], out_scale[3];
+};
+
+// shared-memory image of the weights
+struct MlpSmem {
+  uint32_t W2[kH * kRowU32];
+  uint32_t W3[kH * kRowU32];
+  uint32_t W4[8 * kRowU32];      // rows 3..7 zero (one n8 tile)
+  float W1[kH * 3];
+  float b1[kH], b2[kH], b3[kH], b4[4];
+};
+
+__device__ void load_weights(const MlpArgs& a, MlpSmem* s, bool transposed) {
+  const uint16_t* w2 = transposed ? a.W2t : a.W2;
+  const uint16_t* w3 = transposed ? a.W3t : a.W3;
+  for (int i = threadIdx.x; i < kH * (kH / 2); i += blockDim.x) {
+    const int r = i / (kH / 2), c = i % (kH / 2);
+    const uint32_t* s2 = reinterpret_cast<const uint32_t*>(w2);
+    const uint32_t* s3 = reinterpret_cast<const uint32_t*>(w3);
+    s->W2[r * kRowU32 + c] = s2[i];
+    s->W3[r * kRowU32 + c] = s3[i];
+  }
+  for (int i = threadIdx.x; i < 8 * (kH / 2); i += blockDim.x) {
+    const int r = i / (kH / 2), c = i % (kH / 2);
+    s->W4[r * kRowU32 + c] = r < 3 ? reinterpret_cast<const uint32_t*>(a.W4)[r * (kH / 2) + c] : 0u;
+  }
+  for (int i = threadIdx.x; i < kH * 3; i += blockDim.x) s->W1[i] = __uint_as_float((uint32_t)a.W1[i] << 16);
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    s->b1[i] = a.b1[i];
+    s->b2[i] = a.b2[i];
+    s->b3[i] = a.b3[i];
+  }
+  if (threadIdx.x < 4) s->b4[threadIdx.x] = threadIdx.x < 3 ? a.b4[threadIdx.x] : 0.0f;
+}
+
+// acc[16][4] (C fragments over 128 columns) -> A fragments [8][4] after bias + SiLU;
+// Z (optional, B x 128 rows) receives the pre-activations of rows r0, r1 (< B)
+__device__ __forceinline__ void act_to_afrag(float (&acc)[16][4], const float* bias, int t, uint32_t (&af)[8][4],
+                                             float* Z = nullptr, int64_t r0 = 0, int64_t r1 = 0, int64_t B = 0) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int c = 8 * j + 2 * t;
+    float v0 = acc[j][0] + bias[c], v1 = acc[j][1] + bias[c + 1];
+    float v2 = acc[j][2] + bias[c], v3 = acc[j][3] + bias[c + 1];
+    if (Z) {
+      if (r0 < B) *reinterpret_cast<float2*>(Z + r0 * kH + c) = make_float2(v0, v1);
+      if (r1 < B) *reinterpret_cast<float2*>(Z + r1 * kH + c) = make_float2(v2, v3);
+    }
+    acc[j][0] = silu_f(v0);
+    acc[j][1] = silu_f(v1);
+    acc[j][2] = silu_f(v2);
+    acc[j][3] = silu_f(v3);
+  }
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    af[kk][0] = pack_bf16(acc[2 * kk][0], acc[2 * kk][1]);
+    af[kk][1] = pack_bf16(acc[2 * kk][2], acc[2 * kk][3]);
+    af[kk][2] = pack_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
+    af[kk][3] = pack_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
+  }
+}
+
+// acc = A (16 x 128) * W^T for a 128 x 128 smem weight image W[n][k]
+__device__ __forceinline__ void gemm_128(const uint32_t (&af)[8][4], const uint32_t* W, int g, int t,
+                                         float (&acc)[16][4]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const uint32_t* row = W + (8 * j + g) * kRowU32 + 8 * kk;
+      mma16816(acc[j], af[kk], row[t], row[4 + t]);
+    }
+}
+
+// input layer (FP32): acc[j] = W1 u + b1 for rows g, g + 8 of the warp's tile
+__device__ __forceinline__ void input_layer(const MlpSmem* s, const float* u0, const float* u1, int t,
+                                            float (&acc)[16][4]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int c = 8 * j + 2 * t;
+    const float* wa = s->W1 + c * 3;
+    const float* wb = s->W1 + (c + 1) * 3;
+    acc[j][0] = fmaf(wa[0], u0[0], fmaf(wa[1], u0[1], wa[2] * u0[2]));
+    acc[j][1] = fmaf(wb[0], u0[0], fmaf(wb[1], u0[1], wb[2] * u0[2]));
+    acc[j][2] = fmaf(wa[0], u1[0], fmaf(wa[1], u1[1], wa[2] * u1[2]));
+    acc[j][3] = fmaf(wb[0], u1[0], fmaf(wb[1], u1[1], wb[2] * u1[2]));
+  }
+}
+
+__device__ __forceinline__ void normalise(const MlpArgs& a, const float* x, float* u) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) u[i] = fmaf(x[i] - a.lo[i], a.in_scale[i], -1.0f);
+}
+
+// ---------------------------------------------------------------- inference
+// y[n] = x0[n] + out_scale * f(u(x0[n]))  (the predicted x_T)
+__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpArgs a, const float* __restrict__ x0, int64_t N,
+                                                                 float* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpSmem* s = reinterpret_cast<MlpSmem*>(smem_raw);
+  load_weights(a, s, false);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int64_t tiles = (N + 15) / 16;
+  for (int64_t tile = (int64_t)blockIdx.x * kMlpWarps + warp; tile < tiles; tile += (int64_t)gridDim.x * kMlpWarps) {
+    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+    float x_0[3] = {0, 0, 0}, x_1[3] = {0, 0, 0}, u0[3], u1[3];
+    if (r0 < N)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) x_0[i] = x0[r0 * 3 + i];
+    if (r1 < N)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) x_1[i] = x0[r1 * 3 + i];
+    normalise(a, x_0, u0);
+    normalise(a, x_1, u1);
+    float acc[16][4];
+    uint32_t af[8][4];
+    input_layer(s, u0, u1, t, acc);
+    act_to_afrag(acc, s->b1, t, af);
+    gemm_128(af, s->W2, g, t, acc);
+    act_to_afrag(acc, s->b2, t, af);
+    gemm_128(af, s->W3, g, t, acc);
+    act_to_afrag(acc, s->b3, t, af);
+    float o[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const uint32_t* row = s->W4 + g * kRowU32 + 8 * kk;
+      mma16816(o, af[kk], row[t], row[4 + t]);
+    }
+    // lane (g, t) holds columns 2t, 2t + 1 of rows g and g + 8; outputs are columns 0..2
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int c = 2 * t + q;
+      if (c < 3) {
+        if (r0 < N) y[r0 * 3 + c] = fmaf(o[q] + s->b4[c], a.out_scale[c], x_0[c]);
+        if (r1 < N) y[r1 * 3 + c] = fmaf(o[2 + q] + s->b4[c], a.out_scale[c], x_1[c]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- training
+// Forward over a batch, saving z1..z3 (B x 128 each, FP32), the normalised
+// input u (B x 3) and dY = d loss / d output (B x 3) for the MSE loss against
+// target (x_T - x_0) / out_scale; loss_rows[tile * 16 + r] gets row r's
+// squared error (summed in a fixed order later).
+__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a, const float* __restrict__ x0,
+                                                                       const float* __restrict__ xT, int B,
+                                                                       float* __restrict__ Z,   // 3 x B x 128
+                                                                       float* __restrict__ U,   // B x 3
+                                                                       float* __restrict__ dY,  // B x 3
+                                                                       float* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpSmem* s = reinterpret_cast<MlpSmem*>(smem_raw);
+  load_weights(a, s, false);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int tiles = (B + 15) / 16;
+  const float inv = 2.0f / (3.0f * (float)B);
+  for (int tile = blockIdx.x * kMlpWarps + warp; tile < tiles; tile += gridDim.x * kMlpWarps) {
+    const int r0 = tile * 16 + g, r1 = r0 + 8;
+    float x_0[3] = {0, 0, 0}, x_1[3] = {0, 0, 0}, u0[3], u1[3];
+    if (r0 < B)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) x_0[i] = x0[r0 * 3 + i];
+    if (r1 < B)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) x_1[i] = x0[r1 * 3 + i];
+    normalise(a, x_0, u0);
+    normalise(a, x_1, u1);
+    if (t == 0) {
+      if (r0 < B)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) U[r0 * 3 + i] = u0[i];
+      if (r1 < B)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) U[r1 * 3 + i] = u1[i];
+    }
+    float acc[16][4];
+    uint32_t af[8][4];
+    input_layer(s, u0, u1, t, acc);
+    act_to_afrag(acc, s->b1, t, af, Z, r0, r1, B);
+    gemm_128(af, s->W2, g, t, acc);
+    act_to_afrag(acc, s->b2, t, af, Z + (size_t)B * kH, r0, r1, B);
+    gemm_128(af, s->W3, g, t, acc);
+    act_to_afrag(acc, s->b3, t, af, Z + (size_t)2 * B * kH, r0, r1, B);
+    float o[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const uint32_t* row = s->W4 + g * kRowU32 + 8 * kk;
+      mma16816(o, af[kk], row[t], row[4 + t]);
+    }
+    float e0 = 0.0f, e1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int c = 2 * t + q;
+      if (c < 3) {
+        if (r0 < B) {
+          const float tgt = (xT[r0 * 3 + c] - x_0[c]) / a.out_scale[c];
+          const float r = o[q] + s->b4[c] - tgt;
+          dY[r0 * 3 + c] = inv * r;
+          e0 += r * r;
+        }
+        if (r1 < B) {
+          const float tgt = (xT[r1 * 3 + c] - x_1[c]) / a.out_scale[c];
+          const float r = o[2 + q] + s->b4[c] - tgt;
+          dY[r1 * 3 + c] = inv * r;
+          e1 += r * r;
+        }
+      }
+    }
+    // row sums of the squared errors: lanes t = 0, 1 hold the columns
+    e0 += __shfl_xor_sync(0xffffffffu, e0, 1);
+    e1 += __shfl_xor_sync(0xffffffffu, e1, 1);
+    if (t == 0) {
+      if (r0 < B) err[r0] = e0;
+      if (r1 < B) err[r1] = e1;
+    }
+  }
+}
+
+// Backward through the activations: dZ3 = (dY W4) * silu'(z3), dZ2 = (dZ3 W3) * silu'(z2),
+// dZ1 = (dZ2 W2) * silu'(z1), into dZ (3 x B x 128); Z holds the pre-activations.
+__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_backward(MlpArgs a, int B, const float* __restrict__ dY,
+                                                                        const float* __restrict__ Z,
+                                                                        float* __restrict__ dZ) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpSmem* s = reinterpret_cast<MlpSmem*>(smem_raw);
+  load_weights(a, s, true);   // W2, W3 images hold the transposes
+  __shared__ float W4f[3 * kH];
+  for (int i = threadIdx.x; i < 3 * kH; i += blockDim.x) W4f[i] = __uint_as_float((uint32_t)a.W4[i] << 16);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int tiles = (B + 15) / 16;
+  for (int tile = blockIdx.x * kMlpWarps + warp; tile < tiles; tile += gridDim.x * kMlpWarps) {
+    const int r0 = tile * 16 + g, r1 = r0 + 8;
+    float dy0[3] = {0, 0, 0}, dy1[3] = {0, 0, 0};
+    if (r0 < B)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dy0[i] = dY[r0 * 3 + i];
+    if (r1 < B)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dy1[i] = dY[r1 * 3 + i];
+    float acc[16][4];
+    uint32_t af[8][4];
+    // dA3 = dY W4 (FP32)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int c = 8 * j + 2 * t;
+      acc[j][0] = dy0[0] * W4f[c] + dy0[1] * W4f[kH + c] + dy0[2] * W4f[2 * kH + c];
+      acc[j][1] = dy0[0] * W4f[c + 1] + dy0[1] * W4f[kH + c + 1] + dy0[2] * W4f[2 * kH + c + 1];
+      acc[j][2] = dy1[0] * W4f[c] + dy1[1] * W4f[kH + c] + dy1[2] * W4f[2 * kH + c];
+      acc[j][3] = dy1[0] * W4f[c + 1] + dy1[1] * W4f[kH + c + 1] + dy1[2] * W4f[2 * kH + c + 1];
+    }
+#pragma unroll 1
+    for (int l = 2; l >= 0; --l) {
+      const float* Zl = Z + (size_t)l * B * kH;
+      float* dZl = dZ + (size_t)l * B * kH;
+      // dZ_l = dA_l * silu'(z_l)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = 8 * j + 2 * t;
+        float zz[4] = {0, 0, 0, 0};
+        if (r0 < B) {
+          zz[0] = Zl[(size_t)r0 * kH + c];
+          zz[1] = Zl[(size_t)r0 * kH + c + 1];
+        }
+        if (r1 < B) {
+          zz[2] = Zl[(size_t)r1 * kH + c];
+          zz[3] = Zl[(size_t)r1 * kH + c + 1];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] *= silu_grad_f(zz[q]);
+        if (r0 < B) *reinterpret_cast<float2*>(dZl + (size_t)r0 * kH + c) = make_float2(acc[j][0], acc[j][1]);
+        if (r1 < B) *reinterpret_cast<float2*>(dZl + (size_t)r1 * kH + c) = make_float2(acc[j][2], acc[j][3]);
+      }
+      if (l == 0) break;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        af[kk][0] = pack_bf16(acc[2 * kk][0], acc[2 * kk][1]);
+        af[kk][1] = pack_bf16(acc[2 * kk][2], acc[2 * kk][3]);
+        af[kk][2] = pack_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
+        af[kk][3] = pack_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
+      }
+      // dA_{l-1} = dZ_l W_l: B operand (k = out, n = in) from the transposed image W_l^T[in][out]
+      gemm_128(af, l == 2 ? s->W3 : s->W2, g, t, acc);
+    }
+  }
+}
+
+// Weight and bias gradients as fixed-order sums over the batch:
+//   dW_l[o][i] = sum_b dZ_l[b][o] a_{l-1}[b][i],  db_l[o] = sum_b dZ_l[b][o],
+// with a_0 = u and a_l = silu(z_l) recomputed from the saved pre-activations.
+// grid.x covers the outputs of one layer; blockIdx.y selects the layer.
+__global__ void k_mlp_weight_grads(int B, const float* __restrict__ U, const float* __restrict__ Zf,
+                                   const float* __restrict__ dZ, const float* __restrict__ dY,
+                                   float* __restrict__ gW, float* __restrict__ gb) {
+  // gW layout: W1 (128x3), W2 (128x128), W3 (128x128), W4 (3x128); gb: b1, b2, b3, b4
+  const int layer = blockIdx.y;   // 0..3
+  const int in_dim = layer == 0 ? 3 : kH, out_dim = layer == 3 ? 3 : kH;
+  const int64_t woff = layer == 0 ? 0 : (layer == 1 ? 3 * kH : (layer == 2 ? 3 * kH + kH * kH : 3 * kH + 2 * kH * kH));
+  const int boff = layer * kH;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nw = in_dim * out_dim;
+  if (idx >= nw + out_dim) return;
+  const bool is_bias = idx >= nw;
+  const int o = is_bias ? idx - nw : idx / in_dim, i = is_bias ? 0 : idx % in_dim;
+  double acc = 0.0;
+  for (int b = 0; b < B; ++b) {
+    const float dz = layer == 3 ? dY[(size_t)b * 3 + o] : dZ[((size_t)layer * B + b) * kH + o];
+    float av = 1.0f;
+    if (!is_bias) {
+      if (layer == 0) av = U[(size_t)b * 3 + i];
+      else av = silu_f(Zf[((size_t)(layer - 1) * B + b) * kH + i]);
+    }
+    acc += (double)dz * (double)av;
+  }
+  if (is_bias) gb[boff + o] = (float)acc;
+  else gW[woff + idx] = (float)acc;
+}
+
+// Adam on FP32 masters; rewrites the BF16 copies (and the transposed copies of W2, W3)
+__global__ void k_mlp_adam(int64_t nW, int64_t nb, float* __restrict__ W, float* __restrict__ b,
+                           const float* __restrict__ gW, const float* __restrict__ gb, float* __restrict__ mW,
+                           float* __restrict__ vW, float* __restrict__ mb, float* __restrict__ vb, float lr, float beta1,
+                           float beta2, float eps, float c1, float c2, uint16_t* __restrict__ Wbf,
+                           uint16_t* __restrict__ W2t, uint16_t* __restrict__ W3t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nW) {
+    const float gr = gW[i];
+    const float m = beta1 * mW[i] + (1.0f - beta1) * gr;
+    const float v = beta2 * vW[i] + (1.0f - beta2) * gr * gr;
+    mW[i] = m;
+    vW[i] = v;
+    const float w = W[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    W[i] = w;
+    __nv_bfloat16 wb = __float2bfloat16_rn(w);
+    const uint16_t bits = *reinterpret_cast<uint16_t*>(&wb);
+    Wbf[i] = bits;
+    const int64_t o2 = 3 * kH, o3 = 3 * kH + kH * kH;
+    if (i >= o2 && i < o3) {
+      const int64_t r = (i - o2) / kH, c = (i - o2) % kH;
+      W2t[c * kH + r] = bits;
+    } else if (i >= o3 && i < o3 + kH * kH) {
+      const int64_t r = (i - o3) / kH, c = (i - o3) % kH;
+      W3t[c * kH + r] = bits;
+    }
+  } else if (i < nW + nb) {
+    const int64_t k = i - nW;
+    const float gr = gb[k];
+    const float m = beta1 * mb[k] + (1.0f - beta1) * gr;
+    const float v = beta2 * vb[k] + (1.0f - beta2) * gr * gr;
+    mb[k] = m;
+    vb[k] = v;
+    b[k] = b[k] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+  }
+}
+
+// fixed-order sum of the per-row squared errors -> mean loss
+__global__ void __launch_bounds__(1024) k_mlp_loss(const float* __restrict__ err, int B, float* __restrict__ loss) {
+  __shared__ double sh[1024];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) a += err[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = (float)(sh[0] / (3.0 * B));
+}
+
+// BF16 copies of the FP32 masters (and the transposes of W2, W3)
+__global__ void k_mlp_refresh(const float* __restrict__ W, uint16_t* __restrict__ Wbf, uint16_t* __restrict__ W2t,
+                              uint16_t* __restrict__ W3t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kMlpNW) return;
+  __nv_bfloat16 wb = __float2bfloat16_rn(W[i]);
+  const uint16_t bits = *reinterpret_cast<uint16_t*>(&wb);
+  Wbf[i] = bits;
+  const int64_t o2 = 3 * kH, o3 = 3 * kH + kH * kH;
+  if (i >= o2 && i < o3) W2t[((i - o2) % kH) * kH + (i - o2) / kH] = bits;
+  else if (i >= o3 && i < o3 + kH * kH) W3t[((i - o3) % kH) * kH + (i - o3) / kH] = bits;
+}
+
+// ------------------------------------------------------------------ host
+static MlpArgs mlp_args(const pdmp_mlp* net) {
+  MlpArgs a;
+  const uint16_t* w = net->W_bf16;
+  a.W1 = w;
+  a.W2 = w + 3 * kH;
+  a.W3 = w + 3 * kH + kH * kH;
+  a.W4 = w + 3 * kH + 2 * kH * kH;
+  a.W2t = net->Wt_bf16;
+  a.W3t = net->Wt_bf16 + kH * kH;
+  a.b1 = net->b;
+  a.b2 = net->b + kH;
+  a.b3 = net->b + 2 * kH;
+  a.b4 = net->b + 3 * kH;
+  for (int i = 0; i < 3; ++i) {
+    a.lo[i] = net->lo[i];
+    a.in_scale[i] = net->in_scale[i];
+    a.out_scale[i] = net->out_scale[i];
+  }
+  return a;
+}
+
+static int mlp_grid(int64_t tiles, const void* kernel) {
+  int dev = 0, sms = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 32 * kMlpWarps, sizeof(MlpSmem));
+  if (per < 1) per = 1;
+  int64_t want = (tiles + kMlpWarps - 1) / kMlpWarps;
+  int64_t cap = (int64_t)sms * per;
+  return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+cudaError_t mlp_refresh(const pdmp_mlp* net, cudaStream_t st) {
+  k_mlp_refresh<<<(unsigned)((kMlpNW + 255) / 256), 256, 0, st>>>(net->W, net->W_bf16, net->Wt_bf16,
+                                                                  net->Wt_bf16 + kH * kH);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  const size_t smem = sizeof(MlpSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = mlp_grid((N + 15) / 16, (const void*)k_mlp_forward);
+  k_mlp_forward<<<grid, 32 * kMlpWarps, smem, st>>>(mlp_args(net), x0, N, y);
+  return cudaGetLastError();
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t mlp_train_workspace(int B) {
+  return 2 * al256(sizeof(float) * 3 * (size_t)B * kH) + 3 * al256(sizeof(float) * 3 * (size_t)B) +
+         al256(sizeof(float) * kMlpNW) + al256(sizeof(float) * kMlpNB);
+}
+
+cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int B, float lr, float beta1,
+                           float beta2, float eps, int step, float* loss, void* ws, cudaStream_t st) {
+  char* p = (char*)ws;
+  auto take = [&](size_t b) { char* q = p; p += al256(b); return q; };
+  float* Z = (float*)take(sizeof(float) * 3 * (size_t)B * kH);
+  float* dZ = (float*)take(sizeof(float) * 3 * (size_t)B * kH);
+  float* U = (float*)take(sizeof(float) * 3 * (size_t)B);
+  float* dY = (float*)take(sizeof(float) * 3 * (size_t)B);
+  float* err = (float*)take(sizeof(float) * 3 * (size_t)B);
+  float* gW = (float*)take(sizeof(float) * kMlpNW);
+  float* gb = (float*)take(sizeof(float) * kMlpNB);
+  const MlpArgs a = mlp_args(net);
+  const size_t smem = sizeof(MlpSmem);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_mlp_train_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_mlp_train_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return e;
+  const int64_t tiles = (B + 15) / 16;
+  const int gf = mlp_grid(tiles, (const void*)k_mlp_train_forward);
+  k_mlp_train_forward<<<gf, 32 * kMlpWarps, smem, st>>>(a, x0, xT, B, Z, U, dY, err);
+  if (loss) k_mlp_loss<<<1, 1024, 0, st>>>(err, B, loss);
+  const int gbk = mlp_grid(tiles, (const void*)k_mlp_train_backward);
+  k_mlp_train_backward<<<gbk, 32 * kMlpWarps, smem, st>>>(a, B, dY, Z, dZ);
+  const dim3 gg((unsigned)((kH * kH + kH + 127) / 128), 4);
+  k_mlp_weight_grads<<<gg, 128, 0, st>>>(B, U, Z, dZ, dY, gW, gb);
+  float* mW = net->adam;
+  float* vW = net->adam + kMlpNW;
+  float* mb = net->adam + 2 * kMlpNW;
+  float* vb = net->adam + 2 * kMlpNW + kMlpNB;
+  const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+  k_mlp_adam<<<(unsigned)((kMlpNW + kMlpNB + 255) / 256), 256, 0, st>>>(
+      kMlpNW, kMlpNB, net->W, net->b, gW, gb, mW, vW, mb, vb, lr, beta1, beta2, eps, c1, c2, net->W_bf16,
+      net->Wt_bf16, net->Wt_bf16 + kH * kH);
+  return cudaGetLastError();
+}
+
+}  // namespace pdmp

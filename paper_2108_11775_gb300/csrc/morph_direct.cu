@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kDirectThreads)
 k_morph_direct(FieldArgs fa, const float* x0, int64_t N, int T, float eta,
                float* xT, float* __restrict__ ckpt, int kck, float* __restrict__ traj, float* __restrict__ steps) {
   constexpr int R = RecLayout<D>::kFloats;
-  __shared__ float sm[kDirectTile * R];
+  __shared__ __align__(16) float sm[kDirectTile * R];
   const float ngl2e = -fa.gamma * kLog2e;
   const int64_t base = (int64_t)blockIdx.x * (kDirectThreads * K) + threadIdx.x;
 
@@ -58,8 +58,7 @@ k_morph_direct(FieldArgs fa, const float* x0, int64_t N, int T, float eta,
       const int cnt = (int)min64(kDirectTile, fa.M - m0);
       for (int i = 0; i < cnt; ++i) {
         float rec[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) rec[j] = sm[i * R + j];
+        load_rec<D>(sm, i, rec);
 #pragma unroll
         for (int k = 0; k < K; ++k) accum_grad<KIND, D>(rec, x[k], ngl2e, s[k], gs[k]);
       }
@@ -106,7 +105,7 @@ k_morph_direct(FieldArgs fa, const float* x0, int64_t N, int T, float eta,
 template <int KIND, int D>
 static cudaError_t launch_direct(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
                                  float* ckpt, int k, float* traj, float* steps, cudaStream_t st) {
-  constexpr int K = D <= 3 ? 4 : 2;
+  constexpr int K = 4;
   int64_t per_block = (int64_t)kDirectThreads * K;
   int64_t blocks = (N + per_block - 1) / per_block;
   if (blocks == 0) return cudaSuccess;

@@ -13,7 +13,7 @@ __global__ void __launch_bounds__(kQueryThreads)
 k_query(FieldArgs fa, const float* __restrict__ x, int64_t N, float* __restrict__ c, float* __restrict__ s_out,
         float* __restrict__ grad) {
   constexpr int R = RecLayout<D>::kFloats;
-  __shared__ float sm[kQueryTile * R];
+  __shared__ __align__(16) float sm[kQueryTile * R];
   const float ngl2e = -fa.gamma * kLog2e;
   const int64_t n = (int64_t)blockIdx.x * kQueryThreads + threadIdx.x;
   float xv[D];
@@ -27,7 +27,11 @@ k_query(FieldArgs fa, const float* __restrict__ x, int64_t N, float* __restrict_
     stage_tile<KIND, D>(fa, m0, kQueryTile, sm);
     __syncthreads();
     const int cnt = (int)min64(kQueryTile, fa.M - m0);
-    for (int i = 0; i < cnt; ++i) accum_grad<KIND, D>(sm + i * R, xv, ngl2e, s, gs);
+    for (int i = 0; i < cnt; ++i) {
+      float rec[RecLayout<D>::kFloats];
+      load_rec<D>(sm, i, rec);
+      accum_grad<KIND, D>(rec, xv, ngl2e, s, gs);
+    }
   }
   if (n >= N) return;
   s += fa.bias;

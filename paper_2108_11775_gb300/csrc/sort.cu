@@ -8,33 +8,6 @@
 
 namespace pdmp {
 
-// monotone map float -> uint32 (for atomicMin / atomicMax on floats)
-__device__ __forceinline__ uint32_t ordered_bits(float f) {
-  uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float from_ordered(uint32_t u) {
-  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
-
-// spreads the low 10 bits of v so that bit i lands at bit i * 2 (d = 2) or i * 3 (d = 3)
-__device__ __forceinline__ uint32_t spread2(uint32_t v) {
-  v &= 0x3ffu;
-  v = (v | (v << 8)) & 0x00ff00ffu;
-  v = (v | (v << 4)) & 0x0f0f0f0fu;
-  v = (v | (v << 2)) & 0x33333333u;
-  v = (v | (v << 1)) & 0x55555555u;
-  return v;
-}
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {
-  v &= 0x3ffu;
-  v = (v | (v << 16)) & 0x030000ffu;
-  v = (v | (v << 8)) & 0x0300f00fu;
-  v = (v | (v << 4)) & 0x030c30c3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-
 template <int D>
 __global__ void k_bbox(const float* __restrict__ x, int64_t N, uint32_t* __restrict__ box) {
   float lo[D], hi[D];
@@ -67,23 +40,19 @@ __global__ void k_cell_keys(const float* __restrict__ x, int64_t N, const uint32
   int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const float cells = (float)(1u << bits);
-  uint32_t key = 0;
+  uint32_t c[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    float lo = from_ordered(box[j]), hi = from_ordered(box[D + j]);
-    float span = hi - lo;
-    float v = x[n * D + j];
-    float q = span > 0.0f ? (v - lo) * (cells / span) : 0.0f;
-    uint32_t c = (q >= 0.0f) ? (uint32_t)fminf(q, cells - 1.0f) : 0u;  // NaN and negatives -> 0
-    key |= (D == 2 ? spread2(c) : spread3(c)) << j;
-  }
+  for (int j = 0; j < D; ++j) c[j] = cell_coord(x[n * D + j], from_ordered(box[j]), from_ordered(box[D + j]), cells);
+  uint32_t key;
+  if (D == 2)
+    key = spread2(c[0]) | (spread2(c[1]) << 1);
+  else
+    key = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[D - 1]) << 2);
   keys[n] = key;
   atomicAdd(&counts[key], 1u);
 }
 
 // exclusive scan of counts[0..C) into offs, in chunks of kScanChunk
-constexpr int kScanThreads = 1024;
-constexpr int kScanChunk = 2 * kScanThreads;
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* sh, uint32_t& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -145,7 +114,7 @@ __global__ void k_add_chunk_offsets(uint32_t* __restrict__ offs, int64_t C, cons
   if (i >= C) return;
   uint32_t v = offs[i] + tot[i / kScanChunk];
   offs[i] = v;
-  cursor[i] = v;
+  if (cursor) cursor[i] = v;
 }
 
 __global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t N, uint32_t* __restrict__ cursor,
@@ -219,11 +188,26 @@ cudaError_t spatial_sort(int d, const float* x, int64_t N, const SortWs& s, cuda
     k_bbox<3><<<bb, 256, 0, st>>>(x, N, s.box);
     k_cell_keys<3><<<nb, 256, 0, st>>>(x, N, s.box, s.bits, s.keys, s.counts);
   }
-  k_scan_chunks<<<(unsigned)s.nchunks, kScanThreads, 0, st>>>(s.counts, s.cells, s.offs, s.chunk_tot);
-  k_scan_totals<<<1, kScanThreads, 0, st>>>(s.chunk_tot, s.nchunks);
-  k_add_chunk_offsets<<<(unsigned)((s.cells + 255) / 256), 256, 0, st>>>(s.offs, s.cells, s.chunk_tot, s.cursor);
-  k_scatter<<<nb, 256, 0, st>>>(s.keys, N, s.cursor, s.perm);
-  k_order_cells<<<(unsigned)((s.cells + 255) / 256), 256, 0, st>>>(s.offs, s.counts, s.cells, s.perm);
+  return sort_by_keys(s.keys, N, s.counts, s.offs, s.cursor, s.chunk_tot, s.cells, s.perm, st);
+}
+
+cudaError_t exclusive_scan_u32(const uint32_t* in, int64_t n, uint32_t* out, uint32_t* chunk_tot, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nchunks = (n + kScanChunk - 1) / kScanChunk;
+  k_scan_chunks<<<(unsigned)nchunks, kScanThreads, 0, st>>>(in, n, out, chunk_tot);
+  k_scan_totals<<<1, kScanThreads, 0, st>>>(chunk_tot, nchunks);
+  k_add_chunk_offsets<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, chunk_tot, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t sort_by_keys(const uint32_t* keys, int64_t N, const uint32_t* counts, uint32_t* offs, uint32_t* cursor,
+                         uint32_t* chunk_tot, int64_t cells, int32_t* perm, cudaStream_t st) {
+  const int64_t nchunks = (cells + kScanChunk - 1) / kScanChunk;
+  k_scan_chunks<<<(unsigned)nchunks, kScanThreads, 0, st>>>(counts, cells, offs, chunk_tot);
+  k_scan_totals<<<1, kScanThreads, 0, st>>>(chunk_tot, nchunks);
+  k_add_chunk_offsets<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(offs, cells, chunk_tot, cursor);
+  if (N > 0) k_scatter<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(keys, N, cursor, perm);
+  k_order_cells<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(offs, counts, cells, perm);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,44 @@
 
 namespace pdmp {
 
+constexpr int kScanThreads = 1024;
+constexpr int kScanChunk = 2 * kScanThreads;
+
+// monotone map float -> uint32 (for atomicMin / atomicMax on floats)
+__device__ __forceinline__ uint32_t ordered_bits(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// spreads the low 10 bits of v so that bit i lands at bit i * 2 (d = 2) or i * 3 (d = 3)
+__device__ __forceinline__ uint32_t spread2(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// cell index in [0, cells) of v along one axis of the box [lo, hi]; NaN and
+// values below lo give 0, values at or above hi give cells - 1
+__device__ __forceinline__ uint32_t cell_coord(float v, float lo, float hi, float cells) {
+  const float span = hi - lo;
+  const float q = span > 0.0f ? (v - lo) * (cells / span) : 0.0f;
+  return (q >= 0.0f) ? (uint32_t)fminf(q, cells - 1.0f) : 0u;
+}
+
 struct SortWs {
   int bits;           // grid cells per axis = 2^bits
   int64_t cells;      // 2^(d * bits)
@@ -23,5 +61,12 @@ int sort_bits(int d, int64_t N);
 SortWs sort_layout(void* ws, int d, int64_t N);
 size_t sort_workspace(int d, int64_t N);
 cudaError_t spatial_sort(int d, const float* x, int64_t N, const SortWs& s, cudaStream_t st);
+// exclusive prefix sum of n uint32 values (chunk_tot: ceil(n / kScanChunk) scratch words)
+cudaError_t exclusive_scan_u32(const uint32_t* in, int64_t n, uint32_t* out, uint32_t* chunk_tot, cudaStream_t st);
+// counting sort of N items by keys[] < cells, given counts[] (item counts per
+// key): perm receives the items in key order, each key's items by index when
+// a key holds at most 64 items
+cudaError_t sort_by_keys(const uint32_t* keys, int64_t N, const uint32_t* counts, uint32_t* offs, uint32_t* cursor,
+                         uint32_t* chunk_tot, int64_t cells, int32_t* perm, cudaStream_t st);
 
 }  // namespace pdmp

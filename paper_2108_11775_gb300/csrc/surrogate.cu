@@ -1,0 +1,137 @@
+// Surrogate inference with the plain morph as fallback and judge (no
+// counterpart in the paper; the fallback mirrors the paper's non-blocking
+// fall-back to the prior when the morphed samples are not available).
+//   1. the MLP predicts x_T for every sample;
+//   2. one plain Euler step is evaluated at every prediction (the fast RBF
+//      kernel with T = 1, which also reports the logit s);
+//   3. a sample fails when s >= 0 (c >= 1/2: the prediction is in
+//      predicted-occupied space), when that step is longer than tau_r, or when
+//      either is not finite;
+//   4. failed samples are compacted (prefix sum, so in index order), morphed
+//      by the plain T-step kernel from their x0, and scattered back.
+#include "kernels.cuh"
+#include "sort.cuh"
+
+namespace pdmp {
+
+__global__ void k_residual_flags(const float* __restrict__ s, const float* __restrict__ steps, int64_t N, int d,
+                                 float tau_r2, uint32_t* __restrict__ flags) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float r2 = 0.0f;
+  for (int j = 0; j < d; ++j) {
+    const float v = steps[n * d + j];
+    r2 = fmaf(v, v, r2);
+  }
+  const float sv = s[n];
+  const bool ok = (sv < 0.0f) && (r2 <= tau_r2);     // false for NaN
+  flags[n] = ok ? 0u : 1u;
+}
+
+__global__ void k_compact(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ offs, int64_t N,
+                          int32_t* __restrict__ idx, int64_t* __restrict__ count) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  if (flags[n]) idx[offs[n]] = (int32_t)n;
+  if (n == N - 1) *count = (int64_t)offs[n] + flags[n];
+}
+
+__global__ void k_gather(const float* __restrict__ x, const int32_t* __restrict__ idx, int64_t n, int d,
+                         float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * d) return;
+  out[i] = x[(int64_t)idx[i / d] * d + i % d];
+}
+
+__global__ void k_scatter_rows(const float* __restrict__ v, const int32_t* __restrict__ idx, int64_t n, int d,
+                               float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * d) return;
+  out[(int64_t)idx[i / d] * d + i % d] = v[i];
+}
+
+struct SurWs {
+  float *traj, *steps, *s, *xs, *ys;
+  uint32_t *flags, *offs, *chunks;
+  int32_t* idx;
+  int64_t* count;
+  void* fast;
+  size_t bytes;
+};
+
+static size_t al(size_t b) { return (b + 255) & ~size_t(255); }
+
+static SurWs sur_layout(void* ws, int d, int64_t M, int64_t N) {
+  SurWs w;
+  char* p = (char*)ws;
+  auto take = [&](size_t b) { char* q = p; p += al(b); return q; };
+  w.traj = (float*)take(sizeof(float) * 2 * N * d);
+  w.steps = (float*)take(sizeof(float) * N * d);
+  w.s = (float*)take(sizeof(float) * N);
+  w.xs = (float*)take(sizeof(float) * N * d);
+  w.ys = (float*)take(sizeof(float) * N * d);
+  w.flags = (uint32_t*)take(sizeof(uint32_t) * N);
+  w.offs = (uint32_t*)take(sizeof(uint32_t) * N);
+  w.chunks = (uint32_t*)take(sizeof(uint32_t) * ((N + kScanChunk - 1) / kScanChunk + 1));
+  w.idx = (int32_t*)take(sizeof(int32_t) * N);
+  w.count = (int64_t*)take(sizeof(int64_t));
+  w.fast = take(morph_rbf_fast_workspace(d, M, N));
+  w.bytes = (size_t)(p - (char*)ws);
+  return w;
+}
+
+size_t surrogate_workspace(int d, int64_t M, int64_t N) { return sur_layout(nullptr, d, M, N).bytes; }
+
+// rms[j] = sqrt(mean_n (xT[n][j] - x0[n][j])^2), single block, fixed order
+__global__ void __launch_bounds__(1024) k_displacement_rms(const float* __restrict__ x0, const float* __restrict__ xT,
+                                                            int64_t N, int d, float* __restrict__ rms) {
+  __shared__ double sh[1024];
+  for (int j = 0; j < d; ++j) {
+    double a = 0.0;
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+      const double v = (double)xT[n * d + j] - (double)x0[n * d + j];
+      a += v * v;
+    }
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) rms[j] = (float)sqrt(sh[0] / (double)N);
+    __syncthreads();
+  }
+}
+
+cudaError_t displacement_rms(const float* x0, const float* xT, int64_t N, int d, float* rms, cudaStream_t st) {
+  k_displacement_rms<<<1, 1024, 0, st>>>(x0, xT, N, d, rms);
+  return cudaGetLastError();
+}
+
+cudaError_t surrogate_infer(const pdmp_mlp* net, int d, const FieldArgs& fa, const float* x0, int64_t N, int T,
+                            float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, cudaStream_t st) {
+  *n_fallback = 0;
+  if (N == 0) return cudaSuccess;
+  SurWs w = sur_layout(ws, d, fa.M, N);
+  cudaError_t e;
+  if ((e = mlp_forward(net, x0, N, xT, st))) return e;
+  if (T == 0) return cudaSuccess;
+  // one plain step at every prediction: traj[0] = prediction, steps[0] = its increment, s = its logit
+  if ((e = morph_rbf_fast(d, fa, xT, N, 1, eta, nullptr, nullptr, 0, w.traj, w.steps, w.fast, st, w.s))) return e;
+  const unsigned nb = (unsigned)((N + 255) / 256);
+  k_residual_flags<<<nb, 256, 0, st>>>(w.s, w.steps, N, d, tau_r * tau_r, w.flags);
+  if ((e = exclusive_scan_u32(w.flags, N, w.offs, w.chunks, st))) return e;
+  k_compact<<<nb, 256, 0, st>>>(w.flags, w.offs, N, w.idx, w.count);
+  int64_t cnt = 0;
+  if ((e = cudaMemcpyAsync(&cnt, w.count, sizeof(int64_t), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
+  *n_fallback = cnt;
+  if (cnt == 0) return cudaGetLastError();
+  const unsigned gb = (unsigned)((cnt * d + 255) / 256);
+  k_gather<<<gb, 256, 0, st>>>(x0, w.idx, cnt, d, w.xs);
+  if ((e = morph_rbf_fast(d, fa, w.xs, cnt, T, eta, w.ys, nullptr, 0, nullptr, nullptr, w.fast, st))) return e;
+  k_scatter_rows<<<gb, 256, 0, st>>>(w.ys, w.idx, cnt, d, xT);
+  return cudaGetLastError();
+}
+
+}  // namespace pdmp

@@ -26,7 +26,11 @@ __device__ void grad_pass(const FieldArgs& fa, float ngl2e, const float* x, floa
     stage_tile<KIND, D>(fa, m0, kVjpTile, sm);
     __syncthreads();
     const int cnt = (int)min64(kVjpTile, fa.M - m0);
-    for (int i = 0; i < cnt; ++i) accum_grad<KIND, D>(sm + i * R, x, ngl2e, s, gs);
+    for (int i = 0; i < cnt; ++i) {
+      float rec[R];
+      load_rec<D>(sm, i, rec);
+      accum_grad<KIND, D>(rec, x, ngl2e, s, gs);
+    }
   }
   s_out = s + fa.bias;
   finish_grad_s<KIND, D>(gs, fa.gamma, grad_s);
@@ -60,7 +64,8 @@ __device__ void hvp_pass(const FieldArgs& fa, float ngl2e, const float* x, const
     __syncthreads();
     const int cnt = (int)min64(kVjpTile, fa.M - m0);
     for (int i = 0; i < cnt; ++i) {
-      const float* rec = sm + i * R;
+      float rec[R];
+      load_rec<D>(sm, i, rec);
       if (KIND == PDMP_KIND_RBF) {
         float dx[D], r2 = 0.0f, rv = 0.0f;
 #pragma unroll
@@ -128,7 +133,8 @@ __device__ void weight_grad_pass(const FieldArgs& fa, float ngl2e, const float* 
     __syncthreads();
     const int cnt = (int)min64(kVjpTile, fa.M - m0);
     for (int i = 0; i < cnt; ++i) {
-      const float* rec = sm + i * R;
+      float rec[R];
+      load_rec<D>(sm, i, rec);
       float contrib = 0.0f;
       if (active) {
         float phi, dphig;
@@ -176,7 +182,7 @@ k_morph_vjp(FieldArgs fa, const float* __restrict__ x0, int64_t N, int T, float 
             const float* __restrict__ ckpt, const float* __restrict__ gT, float* __restrict__ g0,
             float* __restrict__ ws_rows /* nullptr or gridDim.x x (M + 1) */) {
   constexpr int R = RecLayout<D>::kFloats;
-  __shared__ float sm[kVjpTile * R];
+  __shared__ __align__(16) float sm[kVjpTile * R];
   __shared__ float red[(kVjpThreads / 32) * kVjpTile];
   const float ngl2e = -fa.gamma * kLog2e;
   const int64_t n = (int64_t)blockIdx.x * kVjpThreads + threadIdx.x;
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kVjpThreads)
 k_logdet(FieldArgs fa, const float* __restrict__ x0, int64_t N, int T, float eta, float* __restrict__ logdet,
          float* __restrict__ xT) {
   constexpr int R = RecLayout<D>::kFloats;
-  __shared__ float sm[kVjpTile * R];
+  __shared__ __align__(16) float sm[kVjpTile * R];
   const float ngl2e = -fa.gamma * kLog2e;
   const int64_t n = (int64_t)blockIdx.x * kVjpThreads + threadIdx.x;
   const bool active = n < N;
@@ -311,7 +317,8 @@ k_logdet(FieldArgs fa, const float* __restrict__ x0, int64_t N, int T, float eta
       __syncthreads();
       const int cnt = (int)min64(kVjpTile, fa.M - m0);
       for (int i = 0; i < cnt; ++i) {
-        const float* rec = sm + i * R;
+        float rec[R];
+        load_rec<D>(sm, i, rec);
         if (KIND == PDMP_KIND_RBF) {
           float dx[D], r2 = 0.0f;
 #pragma unroll

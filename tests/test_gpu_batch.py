@@ -1,0 +1,97 @@
+"""Batched environments in one persistent launch: every environment's result
+against the single-field morph and, on samples, against the FP64 oracle;
+CUDA-graph replay; the autotuner."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2108_11775_gb300 as pdmp
+import workloads as wl
+from gpu_util import rbf_eta, setup_oracle_threads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available()
+    setup_oracle_threads()
+    yield
+    assert pdmp.stream_status()[0] == 0
+
+
+def small_envs(seed=7, n=12):
+    g = wl.rng(seed, wl.S_ENV)
+    envs, host = [], []
+    for e in range(n):
+        d = int(g.integers(2, 4))
+        M = int(g.integers(1, 700)) if e else 1
+        N = [0, 1, 255, 256, 257][e] if e < 5 else int(g.integers(100, 3000))
+        T = int(g.integers(2, 6))
+        f = wl.random_field(seed * 1000 + e, wl.RBF, d, M, lo=0, hi=4, gamma=3.0, wscale=1.5, bias=0.1)
+        eta, _ = rbf_eta(f, np.full(d, -0.5), np.full(d, 4.5), cells=24 if d == 2 else 10)
+        x0 = wl.uniform_box(seed * 1000 + e, 3, N, np.zeros(d), np.full(d, 4.0))
+        host.append((f, x0, eta, T))
+        envs.append((pdmp.DeviceField.from_host(f), torch.from_numpy(x0).cuda().reshape(N, d), eta, T))
+    return envs, host
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_batched_matches_single_field_and_oracle(variant):
+    envs, host = small_envs()
+    b = pdmp.Batch(envs)
+    b.prepare(variant)
+    outs = [o.cpu().numpy() for o in b.run()]
+    assert pdmp.stream_status()[0] == 0
+    for (fld, x0, eta, T), (f, xh, _, _), out in zip(envs, host, outs):
+        if x0.shape[0] == 0:
+            continue
+        single = pdmp.morph(fld, x0, T, eta).cpu().numpy()
+        if variant == 0:                       # same tile shape as the single-field launch
+            assert np.array_equal(out, single)
+        else:
+            assert np.abs(out - single).max() <= 1e-4
+        idx = np.arange(0, x0.shape[0], max(1, x0.shape[0] // 8))
+        ref = oracle.morph(f, xh[idx], T, eta)
+        assert np.abs(out[idx] - ref).max() <= 1e-4
+
+
+def test_batched_graph_replay_and_autotune(tmp_path):
+    envs, _ = small_envs(seed=9, n=20)
+    b = pdmp.Batch(envs, cache_path=str(tmp_path / "tune.json"))
+    best, times = b.autotune(reps=1)
+    assert 0 <= best < b.n_variants and len(times) == b.n_variants and all(t > 0 for t in times)
+    assert b.plan.variant == best
+    direct = [o.clone() for o in b.run()]
+    for o in b.outputs:
+        o.fill_(float("nan"))
+    b.capture()
+    torch.cuda.current_stream().wait_stream(b.graph_stream)
+    b.replay()
+    b.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(b.outputs, direct):
+        assert torch.equal(o, r)
+    again = pdmp.Batch(envs, cache_path=str(tmp_path / "tune.json"))
+    best2, times2 = again.autotune()
+    assert best2 == best and times2 is None               # from the cache
+
+
+def test_batched_config4_shape_sampled():
+    """The 256-environment shape, scaled down in N, checked per environment on samples."""
+    hosts = wl.config4(n_envs=256, N_range=(64, 512))
+    envs = []
+    for w in hosts:
+        eta, _ = rbf_eta(w.field, w.lo - 0.5, w.hi + 0.5, cells=16 if w.field.d == 2 else 6)
+        envs.append((pdmp.DeviceField.from_host(w.field), torch.from_numpy(w.x0).cuda(), eta, w.T))
+    b = pdmp.Batch(envs)
+    b.prepare(0)
+    outs = b.run()
+    torch.cuda.synchronize()
+    assert pdmp.stream_status()[0] == 0
+    for i in range(0, 256, 37):
+        w, (fld, x0, eta, T) = hosts[i], envs[i]
+        idx = np.arange(0, w.x0.shape[0], 97)
+        ref = oracle.morph(w.field, w.x0[idx], T, eta)
+        assert np.abs(outs[i].cpu().numpy()[idx] - ref).max() <= 1e-4
