@@ -142,13 +142,27 @@ def barrier(world):
 
 
 def max_over_ranks(world, value: float) -> float:
+    """The largest value over the ranks (timing only: the morph itself needs
+    no collective).  Works on the NCCL (CUDA tensors) and gloo (CPU) backends."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_sample_seed(rank: int) -> int:
+    """Each rank morphs its own batch of samples (weak scaling): same field,
+    different base samples."""
+    return 2 + 1000 * rank
+
+
+def whole_job_rate(world: int, work_per_rank_step: float, steps: int, max_seconds: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * work_per_rank_step * steps / max_seconds
 
 
 # ---------------------------------------------------------------------------
@@ -174,6 +188,8 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wk, fld, eta, info = build_workload(pdmp, torch)
+    if rank:
+        wk.x0 = wl.uniform_box(rank_sample_seed(rank), wl.S_SAMPLES, N, wk.lo, wk.hi)
     x0 = torch.from_numpy(wk.x0).cuda()
     xT = torch.empty_like(x0)
     ws = torch.empty(pdmp.morph_workspace(fld, N), dtype=torch.uint8, device="cuda")
@@ -224,7 +240,7 @@ def run_ours(args, world, rank, local):
     assert np.isfinite(out_host.numpy()).all()
 
     work = float(N) * T * M
-    value = world * work * args.steps / total
+    value = whole_job_rate(world, work, args.steps, total)
     achieved = work / (sum(per) / len(per))
     pk, pk_kind = peaks()
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -243,7 +259,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD, "N": N, "M": M, "T": T, "d": D, "gamma": 8.0, "eta": eta,
                    "L": info["L"], "fit_loss": info["fit_loss"], "l2_flush": "256 MiB write between timed launches",
                    "parallelism": f"replicas{world}"},
-        "e2e": {"value": world * work * args.steps / e2e_total, "unit": "feature-evals/s",
+        "e2e": {"value": whole_job_rate(world, work, args.steps, e2e_total), "unit": "feature-evals/s",
                 "h2d_bytes_per_step": int(x_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "feature-evals/s",
                      "frac": achieved / peak, "traffic": traffic,

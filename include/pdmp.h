@@ -200,10 +200,12 @@ pdmp_status pdmp_graph_destroy(void* graph_exec);
 /* predicts x_T - x_0; the plain morph checks it and replaces it when it    */
 /* fails.                                                                   */
 /* ---------------------------------------------------------------------- */
-/* Network 3 -> 128 -> 128 -> 128 -> 3, SiLU between the linear layers, on
- * normalised coordinates: input u = (x_0 - lo) * in_scale - 1, output
- * f(u) = (x_T - x_0) / out_scale.  Device buffers, caller-owned:
- *   W        FP32 master weights, PDMP_MLP_NW floats: W1 (128 x 3), W2 (128 x
+/* Network 39 -> 128 -> 128 -> 128 -> 3, SiLU between the linear layers, on
+ * normalised coordinates: u = (x_0 - lo) * in_scale - 1 is encoded as
+ * enc(u) = [u_0..u_2, then for k = 0..5: sin(2^k pi u_0..u_2),
+ * cos(2^k pi u_0..u_2)] (39 values), output f = (x_T - x_0) / out_scale.
+ * Device buffers, caller-owned:
+ *   W        FP32 master weights, PDMP_MLP_NW floats: W1 (128 x 39), W2 (128 x
  *            128), W3 (128 x 128), W4 (3 x 128), each [out][in] row-major;
  *   b        FP32 biases, PDMP_MLP_NB floats: b1, b2, b3 (128 each), b4 (3);
  *   W_bf16   BF16 copy of W (same layout), the weights the kernels use;
@@ -211,7 +213,7 @@ pdmp_status pdmp_graph_destroy(void* graph_exec);
  *   adam     Adam moments: m_W, v_W (PDMP_MLP_NW each), m_b, v_b (PDMP_MLP_NB
  *            each); zero before the first step.
  * Matrix products run on the tensor cores in BF16 with FP32 accumulation. */
-#define PDMP_MLP_NW 33536
+#define PDMP_MLP_NW 38144
 #define PDMP_MLP_NB 387
 typedef struct {
   float* W;

@@ -87,9 +87,10 @@ def lib():
             L.orc_box_labels.argtypes = [_I, _fp, _L, _fp, _L, _u8p]
             L.orc_mlp_forward.argtypes = [_I, _ip, _dp, _dp, _dp, _L, _dp, _dp]
             L.orc_mlp_loss_backward.argtypes = [_I, _ip, _dp, _dp, _dp, _dp, _L, _dp, _dp, _dp]
+            L.orc_mlp_encode.argtypes = [_dp, _L, _I, _dp]
             for name in ("orc_eval", "orc_morph", "orc_morph_inverse", "orc_morph_vjp", "orc_logdet",
                          "orc_lipschitz_rbf", "orc_lipschitz_rff", "orc_fit", "orc_fit_objective",
-                         "orc_box_labels", "orc_mlp_forward", "orc_mlp_loss_backward"):
+                         "orc_box_labels", "orc_mlp_forward", "orc_mlp_loss_backward", "orc_mlp_encode"):
                 getattr(L, name).restype = _I
             L.orc_set_threads(os.cpu_count() or 1)
             _lib = L
@@ -276,6 +277,14 @@ def _mlp_pack(weights, biases):
     wflat = np.concatenate([_d(w).ravel() for w in weights])
     bflat = np.concatenate([_d(b).ravel() for b in biases])
     return np.asarray(widths, dtype=np.int32), wflat, bflat
+
+
+def mlp_encode(u, n_freq: int = 6):
+    """Fourier encoding of normalised inputs u (n x 3) -> n x (3 + 6 n_freq)."""
+    u = _d(u).reshape(-1, 3)
+    out = np.zeros((u.shape[0], 3 + 6 * n_freq))
+    _check(lib().orc_mlp_encode(_ptr(u), u.shape[0], int(n_freq), _ptr(out)), "mlp_encode")
+    return out
 
 
 def mlp_forward(weights, biases, X):

@@ -829,3 +829,24 @@ int orc_mlp_loss_backward(int nl, const int* widths, const double* W, const doub
   free_layers(z, nl); free_layers(a, nl); free_layers(dz, nl); free(offw); free(offb);
   return 0;
 }
+
+/* Fourier encoding of the surrogate's normalised input u (n x 3):
+ * out (n x (3 + 6 nf)) = [u_0..u_2, then for k = 0..nf-1:
+ * sin(2^k pi u_0..u_2), cos(2^k pi u_0..u_2)]. */
+int orc_mlp_encode(const double* u, long n, int nf, double* out) {
+  if (n < 0 || nf < 0) return 1;
+  const int w = 3 + 6 * nf;
+  const double pi = 3.14159265358979323846;
+  for (long s = 0; s < n; ++s) {
+    for (int j = 0; j < 3; ++j) out[s * w + j] = u[s * 3 + j];
+    double f = pi;
+    for (int k = 0; k < nf; ++k) {
+      for (int j = 0; j < 3; ++j) {
+        out[s * w + 3 + 6 * k + j] = sin(f * u[s * 3 + j]);
+        out[s * w + 3 + 6 * k + 3 + j] = cos(f * u[s * 3 + j]);
+      }
+      f *= 2.0;
+    }
+  }
+  return 0;
+}

@@ -510,8 +510,8 @@ class Batch:
 
 
 # ---------------------------------------------------------------------------
-# learned surrogate (MLP 3 -> 128 -> 128 -> 128 -> 3, BF16 tensor cores)
-MLP_NW, MLP_NB, MLP_H = 33536, 387, 128
+# learned surrogate (MLP over a 39-wide Fourier encoding -> 128 -> 128 -> 128 -> 3)
+MLP_NW, MLP_NB, MLP_H, MLP_ENC = 38144, 387, 128, 39
 
 
 class _Mlp(ctypes.Structure):
@@ -560,7 +560,7 @@ class Surrogate:
         import numpy as np
         g = np.random.Generator(np.random.Philox(key=np.array([seed, 0x5eed], dtype=np.uint64)))
         H = MLP_H
-        shapes = [(H, 3), (H, H), (H, H), (3, H)]
+        shapes = [(H, MLP_ENC), (H, H), (H, H), (3, H)]
         Ws = [g.uniform(-1.0, 1.0, s) * np.sqrt(3.0 / s[1]) for s in shapes]   # unit-variance outputs
         Ws[-1] *= 0.1
         self.W = torch.tensor(np.concatenate([w.ravel() for w in Ws]), dtype=torch.float32, device=device)
@@ -594,7 +594,7 @@ class Surrogate:
         H = MLP_H
         W = self.W.cpu().numpy()
         b = self.b.cpu().numpy()
-        sizes = [(H, 3), (H, H), (H, H), (3, H)]
+        sizes = [(H, MLP_ENC), (H, H), (H, H), (3, H)]
         out_w, out_b, o = [], [], 0
         for s in sizes:
             out_w.append(W[o:o + s[0] * s[1]].reshape(s))
@@ -608,7 +608,7 @@ class Surrogate:
         H = MLP_H
         bits = self.W_bf16.cpu().numpy().astype(np.uint16).astype(np.uint32) << 16
         W = bits.view(np.float32).astype(np.float64)
-        sizes = [(H, 3), (H, H), (H, H), (3, H)]
+        sizes = [(H, MLP_ENC), (H, H), (H, H), (3, H)]
         out, o = [], 0
         for s in sizes:
             out.append(W[o:o + s[0] * s[1]].reshape(s))

@@ -44,7 +44,7 @@ cudaError_t batch_prepare(const pdmp_env* envs, int n, int variant, void* ws, pd
 cudaError_t batch_run(const pdmp_batch_plan* plan, void* ws, cudaStream_t st);
 
 // surrogate MLP (mlp.cu, surrogate.cu)
-constexpr int64_t kMlpNW = 3 * 128 + 2 * 128 * 128 + 3 * 128;   // weights W1, W2, W3, W4
+constexpr int64_t kMlpNW = 39 * 128 + 2 * 128 * 128 + 3 * 128;  // weights W1 (over the 39-wide encoding), W2, W3, W4
 constexpr int64_t kMlpNB = 3 * 128 + 3;                         // biases b1, b2, b3, b4
 cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, cudaStream_t st);
 size_t mlp_train_workspace(int B);

@@ -1,7 +1,10 @@
 // Learned surrogate of the T-step morph (no counterpart in the paper): an MLP
-// 3 -> 128 -> 128 -> 128 -> 3 with SiLU between the linear layers, predicting
-// the normalised displacement (x_T - x_0) / out_scale from the normalised
-// input u = (x_0 - lo) * in_scale - 1.  BF16 weights, FP32 accumulation.
+// 39 -> 128 -> 128 -> 128 -> 3 with SiLU between the linear layers, predicting
+// the normalised displacement (x_T - x_0) / out_scale from a Fourier encoding
+// of the normalised input u = (x_0 - lo) * in_scale - 1:
+//   enc(u) = [u_0..u_2, sin(2^k pi u_0..u_2), cos(2^k pi u_0..u_2) for k = 0..5]
+// (without it the displacement field, sharp near obstacle boundaries, is out
+// of reach of a small SiLU network).  BF16 weights, FP32 accumulation.
 //
 // The two 128 x 128 layers and the output layer run on the tensor cores
 // (mma.sync m16n8k16, BF16 x BF16 -> FP32): a warp owns 16 samples, and the
@@ -20,6 +23,8 @@
 namespace pdmp {
 
 constexpr int kH = 128;          // hidden width
+constexpr int kFreq = 6;         // octaves of the input encoding
+constexpr int kEnc = 3 + 6 * kFreq;   // encoded input width (39)
 constexpr int kRowU32 = 68;      // padded smem row: 136 bf16 = 68 words (conflict-free fragment loads)
 constexpr int kMlpWarps = 4;
 
@@ -46,7 +51,7 @@ __device__ __forceinline__ float silu_grad_f(float z) {
 
 // Device copy of the network (all pointers device; bf16 as raw uint16).
 struct MlpArgs {
-  const uint16_t* W1;   // 128 x 3
+  const uint16_t* W1;   // 128 x 39
   const uint16_t* W2;   // 128 x 128  [out][in]
   const uint16_t* W3;   // 128 x 128
   const uint16_t* W4;   // 3 x 128
@@ -61,7 +66,7 @@ struct MlpSmem {
   uint32_t W2[kH * kRowU32];
   uint32_t W3[kH * kRowU32];
   uint32_t W4[8 * kRowU32];      // rows 3..7 zero (one n8 tile)
-  float W1[kH * 3];
+  float W1[kH * kEnc];
   float b1[kH], b2[kH], b3[kH], b4[4];
 };
 
@@ -79,7 +84,7 @@ __device__ void load_weights(const MlpArgs& a, MlpSmem* s, bool transposed) {
     const int r = i / (kH / 2), c = i % (kH / 2);
     s->W4[r * kRowU32 + c] = r < 3 ? reinterpret_cast<const uint32_t*>(a.W4)[r * (kH / 2) + c] : 0u;
   }
-  for (int i = threadIdx.x; i < kH * 3; i += blockDim.x) s->W1[i] = __uint_as_float((uint32_t)a.W1[i] << 16);
+  for (int i = threadIdx.x; i < kH * kEnc; i += blockDim.x) s->W1[i] = __uint_as_float((uint32_t)a.W1[i] << 16);
   for (int i = threadIdx.x; i < kH; i += blockDim.x) {
     s->b1[i] = a.b1[i];
     s->b2[i] = a.b2[i];
@@ -129,18 +134,43 @@ __device__ __forceinline__ void gemm_128(const uint32_t (&af)[8][4], const uint3
     }
 }
 
-// input layer (FP32): acc[j] = W1 u + b1 for rows g, g + 8 of the warp's tile
-__device__ __forceinline__ void input_layer(const MlpSmem* s, const float* u0, const float* u1, int t,
+// Fourier encoding of a normalised input (FP32; sin / cos after reduction to [-pi, pi])
+__device__ __forceinline__ void encode(const float* u, float* e) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) e[j] = u[j];
+  float f = 3.14159265358979f;
+#pragma unroll
+  for (int k = 0; k < kFreq; ++k) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float th = reduce_2pi(f * u[j]);
+      e[3 + 6 * k + j] = sin_approx(th);
+      e[3 + 6 * k + 3 + j] = cos_approx(th);
+    }
+    f *= 2.0f;
+  }
+}
+
+// input layer (FP32): acc[j] = W1 enc for rows g, g + 8 of the warp's tile
+__device__ __forceinline__ void input_layer(const MlpSmem* s, const float* e0, const float* e1, int t,
                                             float (&acc)[16][4]) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const int c = 8 * j + 2 * t;
-    const float* wa = s->W1 + c * 3;
-    const float* wb = s->W1 + (c + 1) * 3;
-    acc[j][0] = fmaf(wa[0], u0[0], fmaf(wa[1], u0[1], wa[2] * u0[2]));
-    acc[j][1] = fmaf(wb[0], u0[0], fmaf(wb[1], u0[1], wb[2] * u0[2]));
-    acc[j][2] = fmaf(wa[0], u1[0], fmaf(wa[1], u1[1], wa[2] * u1[2]));
-    acc[j][3] = fmaf(wb[0], u1[0], fmaf(wb[1], u1[1], wb[2] * u1[2]));
+    const float* wa = s->W1 + c * kEnc;
+    const float* wb = s->W1 + (c + 1) * kEnc;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kEnc; ++i) {
+      a0 = fmaf(wa[i], e0[i], a0);
+      a1 = fmaf(wb[i], e0[i], a1);
+      a2 = fmaf(wa[i], e1[i], a2);
+      a3 = fmaf(wb[i], e1[i], a3);
+    }
+    acc[j][0] = a0;
+    acc[j][1] = a1;
+    acc[j][2] = a2;
+    acc[j][3] = a3;
   }
 }
 
@@ -170,9 +200,12 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpArgs a, const
       for (int i = 0; i < 3; ++i) x_1[i] = x0[r1 * 3 + i];
     normalise(a, x_0, u0);
     normalise(a, x_1, u1);
+    float e0[kEnc], e1[kEnc];
+    encode(u0, e0);
+    encode(u1, e1);
     float acc[16][4];
     uint32_t af[8][4];
-    input_layer(s, u0, u1, t, acc);
+    input_layer(s, e0, e1, t, acc);
     act_to_afrag(acc, s->b1, t, af);
     gemm_128(af, s->W2, g, t, acc);
     act_to_afrag(acc, s->b2, t, af);
@@ -204,7 +237,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpArgs a, const
 __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a, const float* __restrict__ x0,
                                                                        const float* __restrict__ xT, int B,
                                                                        float* __restrict__ Z,   // 3 x B x 128
-                                                                       float* __restrict__ U,   // B x 3
+                                                                       float* __restrict__ U,   // B x kEnc
                                                                        float* __restrict__ dY,  // B x 3
                                                                        float* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -225,17 +258,20 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a,
       for (int i = 0; i < 3; ++i) x_1[i] = x0[r1 * 3 + i];
     normalise(a, x_0, u0);
     normalise(a, x_1, u1);
+    float e0[kEnc], e1[kEnc];
+    encode(u0, e0);
+    encode(u1, e1);
     if (t == 0) {
       if (r0 < B)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) U[r0 * 3 + i] = u0[i];
+        for (int i = 0; i < kEnc; ++i) U[(size_t)r0 * kEnc + i] = e0[i];
       if (r1 < B)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) U[r1 * 3 + i] = u1[i];
+        for (int i = 0; i < kEnc; ++i) U[(size_t)r1 * kEnc + i] = e1[i];
     }
     float acc[16][4];
     uint32_t af[8][4];
-    input_layer(s, u0, u1, t, acc);
+    input_layer(s, e0, e1, t, acc);
     act_to_afrag(acc, s->b1, t, af, Z, r0, r1, B);
     gemm_128(af, s->W2, g, t, acc);
     act_to_afrag(acc, s->b2, t, af, Z + (size_t)B * kH, r0, r1, B);
@@ -247,7 +283,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a,
       const uint32_t* row = s->W4 + g * kRowU32 + 8 * kk;
       mma16816(o, af[kk], row[t], row[4 + t]);
     }
-    float e0 = 0.0f, e1 = 0.0f;
+    float q0 = 0.0f, q1 = 0.0f;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int c = 2 * t + q;
@@ -256,22 +292,22 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a,
           const float tgt = (xT[r0 * 3 + c] - x_0[c]) / a.out_scale[c];
           const float r = o[q] + s->b4[c] - tgt;
           dY[r0 * 3 + c] = inv * r;
-          e0 += r * r;
+          q0 += r * r;
         }
         if (r1 < B) {
           const float tgt = (xT[r1 * 3 + c] - x_1[c]) / a.out_scale[c];
           const float r = o[2 + q] + s->b4[c] - tgt;
           dY[r1 * 3 + c] = inv * r;
-          e1 += r * r;
+          q1 += r * r;
         }
       }
     }
     // row sums of the squared errors: lanes t = 0, 1 hold the columns
-    e0 += __shfl_xor_sync(0xffffffffu, e0, 1);
-    e1 += __shfl_xor_sync(0xffffffffu, e1, 1);
+    q0 += __shfl_xor_sync(0xffffffffu, q0, 1);
+    q1 += __shfl_xor_sync(0xffffffffu, q1, 1);
     if (t == 0) {
-      if (r0 < B) err[r0] = e0;
-      if (r1 < B) err[r1] = e1;
+      if (r0 < B) err[r0] = q0;
+      if (r1 < B) err[r1] = q1;
     }
   }
 }
@@ -352,10 +388,11 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_backward(MlpArgs a
 __global__ void k_mlp_weight_grads(int B, const float* __restrict__ U, const float* __restrict__ Zf,
                                    const float* __restrict__ dZ, const float* __restrict__ dY,
                                    float* __restrict__ gW, float* __restrict__ gb) {
-  // gW layout: W1 (128x3), W2 (128x128), W3 (128x128), W4 (3x128); gb: b1, b2, b3, b4
+  // gW layout: W1 (128 x kEnc), W2 (128x128), W3 (128x128), W4 (3x128); gb: b1, b2, b3, b4
   const int layer = blockIdx.y;   // 0..3
-  const int in_dim = layer == 0 ? 3 : kH, out_dim = layer == 3 ? 3 : kH;
-  const int64_t woff = layer == 0 ? 0 : (layer == 1 ? 3 * kH : (layer == 2 ? 3 * kH + kH * kH : 3 * kH + 2 * kH * kH));
+  const int in_dim = layer == 0 ? kEnc : kH, out_dim = layer == 3 ? 3 : kH;
+  const int64_t w1 = (int64_t)kEnc * kH;
+  const int64_t woff = layer == 0 ? 0 : (layer == 1 ? w1 : (layer == 2 ? w1 + kH * kH : w1 + 2 * kH * kH));
   const int boff = layer * kH;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int nw = in_dim * out_dim;
@@ -367,7 +404,7 @@ __global__ void k_mlp_weight_grads(int B, const float* __restrict__ U, const flo
     const float dz = layer == 3 ? dY[(size_t)b * 3 + o] : dZ[((size_t)layer * B + b) * kH + o];
     float av = 1.0f;
     if (!is_bias) {
-      if (layer == 0) av = U[(size_t)b * 3 + i];
+      if (layer == 0) av = U[(size_t)b * kEnc + i];
       else av = silu_f(Zf[((size_t)(layer - 1) * B + b) * kH + i]);
     }
     acc += (double)dz * (double)av;
@@ -394,7 +431,7 @@ __global__ void k_mlp_adam(int64_t nW, int64_t nb, float* __restrict__ W, float*
     __nv_bfloat16 wb = __float2bfloat16_rn(w);
     const uint16_t bits = *reinterpret_cast<uint16_t*>(&wb);
     Wbf[i] = bits;
-    const int64_t o2 = 3 * kH, o3 = 3 * kH + kH * kH;
+    const int64_t o2 = (int64_t)kEnc * kH, o3 = o2 + kH * kH;
     if (i >= o2 && i < o3) {
       const int64_t r = (i - o2) / kH, c = (i - o2) % kH;
       W2t[c * kH + r] = bits;
@@ -435,7 +472,7 @@ __global__ void k_mlp_refresh(const float* __restrict__ W, uint16_t* __restrict_
   __nv_bfloat16 wb = __float2bfloat16_rn(W[i]);
   const uint16_t bits = *reinterpret_cast<uint16_t*>(&wb);
   Wbf[i] = bits;
-  const int64_t o2 = 3 * kH, o3 = 3 * kH + kH * kH;
+  const int64_t o2 = (int64_t)kEnc * kH, o3 = o2 + kH * kH;
   if (i >= o2 && i < o3) W2t[((i - o2) % kH) * kH + (i - o2) / kH] = bits;
   else if (i >= o3 && i < o3 + kH * kH) W3t[((i - o3) % kH) * kH + (i - o3) / kH] = bits;
 }
@@ -445,9 +482,9 @@ static MlpArgs mlp_args(const pdmp_mlp* net) {
   MlpArgs a;
   const uint16_t* w = net->W_bf16;
   a.W1 = w;
-  a.W2 = w + 3 * kH;
-  a.W3 = w + 3 * kH + kH * kH;
-  a.W4 = w + 3 * kH + 2 * kH * kH;
+  a.W2 = w + kEnc * kH;
+  a.W3 = w + kEnc * kH + kH * kH;
+  a.W4 = w + kEnc * kH + 2 * kH * kH;
   a.W2t = net->Wt_bf16;
   a.W3t = net->Wt_bf16 + kH * kH;
   a.b1 = net->b;
@@ -492,8 +529,8 @@ cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* 
 static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 size_t mlp_train_workspace(int B) {
-  return 2 * al256(sizeof(float) * 3 * (size_t)B * kH) + 3 * al256(sizeof(float) * 3 * (size_t)B) +
-         al256(sizeof(float) * kMlpNW) + al256(sizeof(float) * kMlpNB);
+  return 2 * al256(sizeof(float) * 3 * (size_t)B * kH) + al256(sizeof(float) * kEnc * (size_t)B) +
+         2 * al256(sizeof(float) * 3 * (size_t)B) + al256(sizeof(float) * kMlpNW) + al256(sizeof(float) * kMlpNB);
 }
 
 cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int B, float lr, float beta1,
@@ -502,7 +539,7 @@ cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT
   auto take = [&](size_t b) { char* q = p; p += al256(b); return q; };
   float* Z = (float*)take(sizeof(float) * 3 * (size_t)B * kH);
   float* dZ = (float*)take(sizeof(float) * 3 * (size_t)B * kH);
-  float* U = (float*)take(sizeof(float) * 3 * (size_t)B);
+  float* U = (float*)take(sizeof(float) * kEnc * (size_t)B);
   float* dY = (float*)take(sizeof(float) * 3 * (size_t)B);
   float* err = (float*)take(sizeof(float) * 3 * (size_t)B);
   float* gW = (float*)take(sizeof(float) * kMlpNW);
@@ -520,7 +557,7 @@ cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT
   if (loss) k_mlp_loss<<<1, 1024, 0, st>>>(err, B, loss);
   const int gbk = mlp_grid(tiles, (const void*)k_mlp_train_backward);
   k_mlp_train_backward<<<gbk, 32 * kMlpWarps, smem, st>>>(a, B, dY, Z, dZ);
-  const dim3 gg((unsigned)((kH * kH + kH + 127) / 128), 4);
+  const dim3 gg((unsigned)((kH * kH + kH + 127) / 128), 4);   // covers the largest layer (128 x 128 + 128)
   k_mlp_weight_grads<<<gg, 128, 0, st>>>(B, U, Z, dZ, dY, gW, gb);
   float* mW = net->adam;
   float* vW = net->adam + kMlpNW;

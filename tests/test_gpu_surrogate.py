@@ -25,7 +25,9 @@ LO, HI = np.zeros(3), np.full(3, 5.0)
 
 
 def normalised(net, x):
-    return (np.asarray(x, np.float64) - np.asarray(net.lo)) * np.asarray(net.in_scale) - 1.0
+    """The network's input: the oracle's Fourier encoding of the normalised coordinates."""
+    u = (np.asarray(x, np.float64) - np.asarray(net.lo)) * np.asarray(net.in_scale) - 1.0
+    return oracle.mlp_encode(u, 6)
 
 
 def test_mlp_forward_matches_oracle():
@@ -83,7 +85,7 @@ def test_surrogate_learns_the_displacement_and_beats_the_identity():
     loss = torch.zeros(1, device="cuda")
     B = 4096
     first = None
-    for step in range(300):
+    for step in range(600):
         i = (step * B) % (x0.shape[0] - B)
         net.train_step(x0[i:i + B].contiguous(), xT[i:i + B].contiguous(), lr=2e-3, loss=loss)
         if first is None:

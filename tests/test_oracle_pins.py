@@ -400,3 +400,18 @@ def test_mlp_gradient_matches_fd():
         Wm[layer][i, j] -= h
         fd = (oracle.mlp_loss_backward(Wp, Bs, X, Y)[0] - oracle.mlp_loss_backward(Wm, Bs, X, Y)[0]) / (2 * h)
         assert abs(dW[layer][i, j] - fd) < 1e-8
+
+
+def test_mlp_encoding_identities():
+    u = wl.rng(42, 1).uniform(-1, 1, (50, 3))
+    e = oracle.mlp_encode(u, 6)
+    assert e.shape == (50, 39)
+    np.testing.assert_array_equal(e[:, :3], u)
+    for k in range(6):
+        s_, c_ = e[:, 3 + 6 * k:6 + 6 * k], e[:, 6 + 6 * k:9 + 6 * k]
+        np.testing.assert_allclose(s_ ** 2 + c_ ** 2, 1.0, atol=1e-14)
+        if k:
+            ps, pc = e[:, 3 + 6 * (k - 1):6 + 6 * (k - 1)], e[:, 6 + 6 * (k - 1):9 + 6 * (k - 1)]
+            np.testing.assert_allclose(s_, 2 * ps * pc, atol=1e-13)      # octaves double the angle
+            np.testing.assert_allclose(c_, pc ** 2 - ps ** 2, atol=1e-13)
+    np.testing.assert_allclose(e[:, 3:6], np.sin(np.pi * u), atol=1e-15)   # first octave is pi u
