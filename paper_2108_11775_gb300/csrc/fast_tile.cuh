@@ -40,15 +40,13 @@ __device__ __forceinline__ u64 ex2x2(u64 a) {
 // Tile shape: W warps per block (each summing over its share of M) and K
 // samples per lane (even: f32x2 pairs).  The single-field launch uses
 // W = 4, K = 8; the batched launch picks among a few shapes (autotuned).
-constexpr int kFastStage = 256;                // centres per shared-memory stage
+constexpr int kWarpStage = 64;                 // centres per warp per shared-memory stage
 constexpr int kFastUnroll = 2;                 // centres per unrolled inner iteration
 
 template <int W, int K>
 struct Shape {
   static_assert(K % 2 == 0, "samples per lane must be even (f32x2 pairs)");
-  static_assert(kFastStage % W == 0, "a stage must split evenly across the warps");
   static constexpr int kWarps = W, kThreads = 32 * W, kK = K, kPairs = K / 2, kTile = 32 * K;
-  static constexpr int kSlice = kFastStage / W;
   static constexpr int kMinBlocks = 16 / W;    // 16 warps per SM
 };
 
@@ -58,12 +56,12 @@ struct FastRec {
   static constexpr int kTab = D == 2 ? 1 : 2;  // float4s per centre in the table
 };
 
-// Shared memory of one tile: two stages of transformed records, aliased
-// after the last stage of a step by the cross-warp reduction buffer, then the
-// raw table entries of the stage being prefetched.
-template <int D>
+// Shared memory of one tile: per warp, two stages of transformed records
+// (aliased, after a step's last stage, by the cross-warp reduction buffer),
+// then per warp the raw table entries of the stage being prefetched.
+template <int D, int W>
 __host__ __device__ constexpr size_t fast_bufs_bytes() {
-  return 2 * (size_t)kFastStage * FastRec<D>::kPairs * sizeof(u64);
+  return (size_t)W * 2 * kWarpStage * FastRec<D>::kPairs * sizeof(u64);
 }
 template <int W, int K>
 __host__ __device__ constexpr size_t fast_red_bytes() {
@@ -71,11 +69,11 @@ __host__ __device__ constexpr size_t fast_red_bytes() {
 }
 template <int D, int W, int K>
 __host__ __device__ constexpr size_t fast_region0_bytes() {
-  return fast_bufs_bytes<D>() > fast_red_bytes<W, K>() ? fast_bufs_bytes<D>() : fast_red_bytes<W, K>();
+  return fast_bufs_bytes<D, W>() > fast_red_bytes<W, K>() ? fast_bufs_bytes<D, W>() : fast_red_bytes<W, K>();
 }
 template <int D, int W, int K>
 __host__ __device__ constexpr size_t fast_smem_bytes() {
-  return fast_region0_bytes<D, W, K>() + (size_t)kFastStage * FastRec<D>::kTab * sizeof(float4);
+  return fast_region0_bytes<D, W, K>() + (size_t)W * kWarpStage * FastRec<D>::kTab * sizeof(float4);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -102,12 +100,14 @@ __global__ void k_rbf_table(const float* __restrict__ centres, const float* __re
   }
 }
 
-// Copies the table entries of centres [m0, m0 + kFastStage) into raw
-// (asynchronously; each thread copies the entries it later transforms).
-template <int D, int NT>
-__device__ __forceinline__ void stage_prefetch(const float4* __restrict__ tab, int64_t M, int64_t m0, float4* raw) {
+// One warp copies the table entries of centres [m0, m0 + kWarpStage) into
+// its raw buffer (asynchronously; each lane copies the entries it later
+// transforms).
+template <int D>
+__device__ __forceinline__ void stage_prefetch(const float4* __restrict__ tab, int64_t M, int64_t m0, float4* raw,
+                                               int lane) {
   constexpr int KT = FastRec<D>::kTab;
-  for (int i = threadIdx.x; i < kFastStage; i += NT) {
+  for (int i = lane; i < kWarpStage; i += 32) {
     const int64_t m = m0 + i;
     if (m < M)
 #pragma unroll
@@ -116,17 +116,18 @@ __device__ __forceinline__ void stage_prefetch(const float4* __restrict__ tab, i
   cp_async_commit();
 }
 
-// Waits for this thread's prefetched entries and writes the records of
-// centres [m0, m0 + kFastStage) into rec (kFastStage x kPairs u64).
+// Waits for this lane's prefetched entries and writes the records of
+// centres [m0, m0 + kWarpStage) into the warp's rec (kWarpStage x kPairs u64);
+// the caller synchronises the warp before reading them.
 //   expanded: [a a][b_0 b_0]..[b_{d-1} ..][sg sg][c~_0 c~_0]..  (c~ = sg (mu - o))
 //   direct:   [-mu_0 -mu_0]..[-mu_{d-1} ..][lw lw][sg sg]
-template <int D, int NT>
+template <int D>
 __device__ __forceinline__ void stage_build(int64_t M, int64_t m0, bool expanded, const float* o, float gl2e,
-                                            const float4* raw, u64* rec) {
+                                            const float4* raw, u64* rec, int lane) {
   constexpr int RP = FastRec<D>::kPairs;
   constexpr int KT = FastRec<D>::kTab;
   cp_async_wait_all();
-  for (int i = threadIdx.x; i < kFastStage; i += NT) {
+  for (int i = lane; i < kWarpStage; i += 32) {
     const int64_t m = m0 + i;
     float mu[D], lw = -INFINITY, sg = 0.0f;
     if (m < M) {
@@ -203,17 +204,21 @@ __device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t
   using S_ = Shape<W, K>;
   constexpr int RP = FastRec<D>::kPairs;
   constexpr int P = S_::kPairs;
-  constexpr int kTile = S_::kTile, kSlice = S_::kSlice;
-  u64* bufs = reinterpret_cast<u64*>(smem);
-  float4* red = reinterpret_cast<float4*>(smem);   // aliases bufs after a step's last stage
-  float4* raw = reinterpret_cast<float4*>(smem + fast_region0_bytes<D, W, K>());
+  constexpr int kTile = S_::kTile;
+  constexpr int KT = FastRec<D>::kTab;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // each warp owns a contiguous slice of the centres and its own stage buffers
+  u64* wbuf = reinterpret_cast<u64*>(smem) + (size_t)warp * 2 * kWarpStage * RP;
+  float4* red = reinterpret_cast<float4*>(smem);   // aliases the stage buffers after a step's last stage
+  float4* wraw = reinterpret_cast<float4*>(smem + fast_region0_bytes<D, W, K>()) + (size_t)warp * kWarpStage * KT;
   const float4* __restrict__ tab = a.tab;
   const int64_t M = a.M, N = a.N;
   const float gamma = a.gamma, bias = a.bias, eta = a.eta;
   const int T = a.T;
   const float gl2e = gamma * kLog2e;
-  const int nstage = (int)((M + kFastStage - 1) / kFastStage);
+  const int64_t Mw = ((M + W - 1) / W + kWarpStage - 1) / kWarpStage * kWarpStage;   // slice length
+  const int64_t mbase = (int64_t)warp * Mw;
+  const int nstage = (int)(Mw / kWarpStage);
 
   float x[K][D];
   bool act[K];
@@ -264,15 +269,15 @@ __device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t
       S[i] = 0ull;
     }
 
-    stage_prefetch<D, S_::kThreads>(tab, M, 0, raw);
-    stage_build<D, S_::kThreads>(M, 0, expanded, o, gl2e, raw, bufs);
-    __syncthreads();
+    stage_prefetch<D>(tab, M, mbase, wraw, lane);
+    stage_build<D>(M, mbase, expanded, o, gl2e, wraw, wbuf, lane);
+    __syncwarp();
     for (int st = 0; st < nstage; ++st) {
-      if (st + 1 < nstage) stage_prefetch<D, S_::kThreads>(tab, M, (int64_t)(st + 1) * kFastStage, raw);
-      const u64* rec = bufs + (size_t)(st & 1) * kFastStage * RP + (size_t)warp * kSlice * RP;
+      if (st + 1 < nstage) stage_prefetch<D>(tab, M, mbase + (int64_t)(st + 1) * kWarpStage, wraw, lane);
+      const u64* rec = wbuf + (size_t)(st & 1) * kWarpStage * RP;
       if (expanded) {
 #pragma unroll kFastUnroll
-        for (int c = 0; c < kSlice; ++c) {
+        for (int c = 0; c < kWarpStage; ++c) {
           const ulonglong2* q = reinterpret_cast<const ulonglong2*>(rec + (size_t)c * RP);
           u64 r[RP];
 #pragma unroll
@@ -294,7 +299,7 @@ __device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t
         }
       } else {
         const u64 ng = pk(-gl2e, -gl2e);
-        for (int c = 0; c < kSlice; ++c) {
+        for (int c = 0; c < kWarpStage; ++c) {
           const u64* r = rec + (size_t)c * RP;
 #pragma unroll
           for (int i = 0; i < P; ++i) {
@@ -312,10 +317,11 @@ __device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t
         }
       }
       if (st + 1 < nstage)
-        stage_build<D, S_::kThreads>(M, (int64_t)(st + 1) * kFastStage, expanded, o, gl2e, raw,
-                                     bufs + (size_t)((st + 1) & 1) * kFastStage * RP);
-      __syncthreads();
+        stage_build<D>(M, mbase + (int64_t)(st + 1) * kWarpStage, expanded, o, gl2e, wraw,
+                       wbuf + (size_t)((st + 1) & 1) * kWarpStage * RP, lane);
+      __syncwarp();
     }
+    __syncthreads();   // every warp has finished its slice before the reduction buffer overwrites the stages
 
     // partial sums -> shared memory, then the same fixed-order total in every warp
 #pragma unroll
