@@ -39,8 +39,8 @@ L2_FLUSH_BYTES = 256 << 20
 LAUNCHES_PER_MORPH = 9
 FP32_LANES_PER_SM = 128           # FP32 pipe width per SM per clock
 MUFU_EX2_PER_SM = 32              # measured ex2 throughput per SM per clock on GB300
-KERNEL_SOURCES = ["paper_2108_11775_gb300/csrc/morph_rbf_fast.cu", "paper_2108_11775_gb300/csrc/sort.cu",
-                  "paper_2108_11775_gb300/csrc/common.cuh"]
+KERNEL_SOURCES = ["paper_2108_11775_gb300/csrc/morph_rbf_fast.cu", "paper_2108_11775_gb300/csrc/fast_tile.cuh",
+                  "paper_2108_11775_gb300/csrc/sort.cu", "paper_2108_11775_gb300/csrc/common.cuh"]
 
 
 def kernel_hash() -> str:
@@ -60,16 +60,22 @@ def peaks():
 
 
 def alu_peak(n_sms: int, sm_mhz: float) -> float:
-    """Feature evaluations per second the SM's issue slots allow.  An RBF
-    feature in d dimensions needs at least 2d + 1 FP32 operations (d for the
-    exponent's linear form, 1 for s, d for the gradient moments) and one ex2.
-    A scheduler issues one warp instruction per clock; a packed f32x2 FMA
-    (64 FP32 operations) takes two issue clocks, so the FP32 work of 32
-    features costs 2d + 1 issue clocks and their ex2 one more: 128 / (2d + 2)
-    features per SM per clock.  The ex2 unit itself (32 per SM per clock) is
-    not the limit."""
+    """Feature evaluations per second at the FP32/ex2 roofline with the
+    algorithmic count of an RBF feature in d dimensions: 2d + 2 FP32
+    operations (d for the exponent's linear form, one for the weight, one for
+    s, d for the gradient moments) and one ex2.  128 FP32 lanes per SM per
+    clock give 128 / (2d + 2) features per SM per clock; the ex2 unit (32 per
+    SM per clock) is not the limit."""
     per_sm_clk = min(FP32_LANES_PER_SM / (2 * D + 2), MUFU_EX2_PER_SM / 1.0)
     return n_sms * sm_mhz * 1e6 * per_sm_clk
+
+
+def kernel_pipe_peak(n_sms: int, sm_mhz: float) -> float:
+    """The fast kernel's own FP32-pipe ceiling: it folds the weight into the
+    exponent and issues 2d + 1 FP32 operations per feature, as packed f32x2
+    FMAs that occupy the FMA pipe for two clocks each (one issue slot), so
+    128 / (2d + 1) features per SM per clock."""
+    return n_sms * sm_mhz * 1e6 * FP32_LANES_PER_SM / (2 * D + 1)
 
 
 class ClockSampler:
@@ -245,6 +251,7 @@ def run_ours(args, world, rank, local):
     pk, pk_kind = peaks()
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = alu_peak(n_sms, float(pk.get("sm_max_mhz", 2070.0)))
+    pipe_peak = kernel_pipe_peak(n_sms, float(pk.get("sm_max_mhz", 2070.0)))
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -264,7 +271,8 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "feature-evals/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": f"{n_sms} SMs x {pk.get('sm_max_mhz', 2070.0)} MHz ({pk_kind} max clock) x "
-                                   f"128/(2d+2) features per SM-clock (FP32 issue + ex2 issue)"},
+                                   f"128 FP32 lanes / (2d+2) FP32 operations per feature",
+                     "kernel_pipe_peak": pipe_peak, "kernel_pipe_frac": achieved / pipe_peak},
         "clocks": clk.summary(),
         # per step: centre table, 7 kernels of the spatial sort, the morph kernel
         "gpu_launches": args.steps * LAUNCHES_PER_MORPH,
@@ -273,9 +281,12 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wk, fld, eta, target_s=args.cpu_seconds)
     if not args.no_extras and args.workload == "full":
+        culled = extra_culled(pdmp, torch, fld, x0, xT, eta)
+        culled["speedup_vs_dense"] = (float(N) * T * M / achieved) / (culled["ms"] / 1e3)
         del x0, xT, ws, flush
         torch.cuda.empty_cache()
         line["extras"] = {
+            "culled_morph": culled,
             "batched_256_envs": extra_batched(pdmp, torch, n_sms, pk),
             "rff7d_differentiation": extra_rff(pdmp, torch, n_sms, pk),
             "surrogate_3d": extra_surrogate(pdmp, torch, args),
@@ -320,13 +331,35 @@ def extra_batched(pdmp, torch, n_sms, pk):
     torch.cuda.synchronize()
     t = _time(torch, b.replay, reps=3)
     work = b.work()
-    # issue-bound peak per environment's d, weighted by its work
+    # FP32 roofline (2d + 2 operations per feature) per environment's d, weighted by its work
     mhz = float(pk.get("sm_max_mhz", 2070.0))
     t_peak = sum(w.x0.shape[0] * w.field.M * w.T / (n_sms * mhz * 1e6 * 128.0 / (2 * w.field.d + 2)) for w in hosts)
     return {"value": work / t, "unit": "feature-evals/s", "ms_per_launch": 1e3 * t, "work": work,
             "roofline_frac": (work / t) / (work / t_peak), "variant": best,
             "variant_ms": [round(v, 3) for v in times], "launch": "CUDA graph of one pdmp_morph_batched",
             "gpu_launches_per_run": 11}
+
+
+def extra_culled(pdmp, torch, fld, x0, xT_dense, eta, eps=1e-6):
+    """The spatially culled morph on the same workload: its effective rate
+    (dense N T M over its time; not a roofline fraction), the fraction of
+    the dense feature evaluations it performs, and its largest deviation
+    from the dense kernel's x_T."""
+    r, W = pdmp.cull_radius(fld, eps)
+    ws = torch.empty(pdmp.morph_culled_workspace(fld, N), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(x0)
+    run = lambda: pdmp.morph_culled(fld, x0, T, eta, r, out=out, ws=ws)
+    for _ in range(3):
+        run()
+    t = _time(torch, run, reps=5)
+    work = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pdmp.morph_culled(fld, x0, T, eta, r, out=out, ws=ws, work=work)
+    dense = float(N) * T * M
+    dev = float((out - xT_dense).abs().max())
+    return {"effective_value": dense / t, "unit": "feature-evals/s (dense-equivalent)", "ms": 1e3 * t,
+            "speedup_vs_dense": None, "evaluated_fraction": int(work.item()) / dense,
+            "eps": eps, "r_cut": r, "sum_abs_w": W, "max_abs_dev_vs_dense": dev,
+            "note": "features farther than r_cut from a tile dropped; s and |grad s| change by at most eps"}
 
 
 def extra_rff(pdmp, torch, n_sms, pk):
@@ -459,7 +492,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / RFF / surrogate measurements")
     ap.add_argument("--surrogate-steps", type=int, default=1500)
     ap.add_argument("--workload", choices=["full", "small"], default="full",
-                    help="small: 65,536 samples and 5 steps of the same workload (for ncu captures)")
+                    help="small: 262,144 samples and 3 steps of the same workload (for ncu captures)")
     args = ap.parse_args()
     if args.workload == "small":
         global N, T, WORKLOAD

@@ -258,6 +258,53 @@ pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const
                                  void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Spatially culled morph (RBF, d = 2 or 3).                                */
+/* ---------------------------------------------------------------------- */
+/* The T Euler steps of pdmp_morph, but every sample tile sums, at every
+ * step, only over the centres that can lie within r_cut of one of its
+ * samples (the centres are sorted into a uniform grid each call).  Features
+ * farther than r_cut are dropped: with W = sum |w_m| and r_cut >=
+ * 1/sqrt(2 gamma), each gradient evaluation loses at most
+ * W exp(-gamma r_cut^2) of s and W 2 gamma r_cut exp(-gamma r_cut^2) of
+ * |grad s|.  ws: pdmp_morph_culled_workspace bytes, 16-byte aligned, required.
+ * work (device, 8-byte aligned, may be NULL) is incremented by the number of
+ * feature evaluations performed (sum over tiles and steps of the visited
+ * centres times the tile's samples).  x0 may alias xT; checkpoints as in
+ * pdmp_morph.  PDMP_ERR_UNSUPPORTED for RFF fields or d = 1. */
+size_t pdmp_morph_culled_workspace(const pdmp_field* f, int64_t N);
+pdmp_status pdmp_morph_culled(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float r_cut,
+                              float* xT, float* ckpt, int32_t k, void* ws, size_t ws_bytes,
+                              unsigned long long* work, void* stream);
+
+/* The smallest r_cut >= 1/sqrt(2 gamma) for which both dropped parts above
+ * are at most eps (W computed on the device in FP64; synchronises the
+ * stream).  *r_cut receives it (host float, rounded up); *w_abs (may be NULL)
+ * receives W. */
+pdmp_status pdmp_cull_radius(const pdmp_field* f, float eps, float* r_cut, double* w_abs, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Eq. (2): the inverse map.                                                */
+/* ---------------------------------------------------------------------- */
+/* y[n] = phi^{-1}(z[n]): the T Euler steps of pdmp_morph are undone last
+ * first, each by the fixed point y = z + eta grad c(y) (a contraction when
+ * eta L < 1), iterated until every sample of a block of 256 moves by at most
+ * tol * (1 + |y|) per coordinate, or maxit times.  iters (N, may be NULL)
+ * receives, per sample, the largest number of iterations any step of its
+ * block used (maxit means the tolerance was not reached).  y may alias z. */
+pdmp_status pdmp_morph_inverse(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, float tol,
+                               int32_t maxit, float* y, int32_t* iters, void* stream);
+
+/* Density of the morphed samples (Sec. 3.2, "Drawing Samples", by the
+ * change of variables through the T-step map) for a base density uniform on
+ * the box [lo, hi] (host arrays of d doubles):
+ *   log_p[n] = -log vol(box) - log det J(y[n])   if y[n] lies in the box,
+ *            = -inf                                otherwise,
+ * with y = phi^{-1}(z) from pdmp_morph_inverse (tol, maxit as there) written
+ * to y (N x d, must not alias z) and log det J as pdmp_logdet computes it. */
+pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, const double* lo,
+                             const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Chain rule through Eq. (1): vector-Jacobian product of the T-step map.   */
 /* ---------------------------------------------------------------------- */
 /* g0[n] = (d x_T / d x_0)^T gT[n] for every sample, computed backwards as

@@ -22,7 +22,7 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "PdmpError", "DeviceField", "lib", "morph", "morph_trace", "morph_workspace", "morph_vjp", "morph_vjp_workspace", "logdet",
+    "PdmpError", "DeviceField", "lib", "morph", "morph_trace", "morph_workspace", "morph_inverse", "log_density", "morph_culled", "morph_culled_workspace", "cull_radius", "morph_vjp", "morph_vjp_workspace", "logdet",
     "occupancy_query", "box_labels", "lipschitz_bound", "fit_occupancy", "fit_workspace", "stream_status", "Batch",
     "Surrogate", "displacement_rms", "morph_autograd",
     "RBF", "RFF",
@@ -74,6 +74,10 @@ def lib():
                 "pdmp_morph_trace": [_FP, _P, _i64, _i32, _f32, _P, _P, _P, _sz, _P],
                 "pdmp_morph_vjp": [_FP, _P, _i64, _i32, _f32, _i32, _P, _P, _P, _P, _P, _P, _sz, _P],
                 "pdmp_logdet": [_FP, _P, _i64, _i32, _f32, _P, _P, _P],
+                "pdmp_morph_culled": [_FP, _P, _i64, _i32, _f32, _f32, _P, _P, _i32, _P, _sz, _P, _P],
+                "pdmp_cull_radius": [_FP, _f32, ctypes.POINTER(_f32), ctypes.POINTER(_f64), _P],
+                "pdmp_morph_inverse": [_FP, _P, _i64, _i32, _f32, _f32, _i32, _P, _P, _P],
+                "pdmp_log_density": [_FP, _P, _i64, _i32, _f32, _P, _P, _f32, _i32, _P, _P, _P],
                 "pdmp_occupancy_query": [_FP, _P, _i64, _P, _P, _P, _P],
                 "pdmp_box_labels": [_i32, _P, _i64, _P, _i64, _P, _P],
                 "pdmp_lipschitz_bound": [_FP, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _i32,
@@ -87,6 +91,8 @@ def lib():
                 fn.restype = _i32
             L.pdmp_morph_workspace.argtypes = [_FP, _i64]
             L.pdmp_morph_workspace.restype = _sz
+            L.pdmp_morph_culled_workspace.argtypes = [_FP, _i64]
+            L.pdmp_morph_culled_workspace.restype = _sz
             L.pdmp_morph_vjp_workspace.argtypes = [_FP, _i64, _i32, _i32, _i32]
             L.pdmp_morph_vjp_workspace.restype = _sz
             L.pdmp_fit_workspace.argtypes = [_i64, _i64]
@@ -248,6 +254,67 @@ def morph_noalloc(field: DeviceField, x0: torch.Tensor, T: int, eta: float,
             _ptr(out, shape=(N, d), name="out"), _stream())
     _check(st, "pdmp_morph_noalloc")
     return out
+
+
+def cull_radius(field: DeviceField, eps: float):
+    """(r_cut, W): the cut-off radius whose dropped features change s and |grad s| by at most eps."""
+    r = ctypes.c_float(0)
+    W = ctypes.c_double(0)
+    f = field.struct()
+    _check(lib().pdmp_cull_radius(ctypes.byref(f), float(eps), ctypes.byref(r), ctypes.byref(W), _stream()),
+           "pdmp_cull_radius")
+    return float(r.value), float(W.value)
+
+
+def morph_culled_workspace(field: DeviceField, N: int) -> int:
+    """Bytes of device workspace pdmp_morph_culled needs for N samples."""
+    f = field.struct()
+    return int(lib().pdmp_morph_culled_workspace(ctypes.byref(f), int(N)))
+
+
+def morph_culled(field: DeviceField, x0: torch.Tensor, T: int, eta: float, r_cut: float, out: torch.Tensor | None = None,
+                 ckpt: torch.Tensor | None = None, k: int = 0, ws: torch.Tensor | None = None,
+                 work: torch.Tensor | None = None):
+    """The morph of Eq. (1) with features farther than r_cut from a sample tile dropped (RBF, d = 2, 3)."""
+    L = lib()
+    N, d = x0.shape[0], field.d
+    xT = torch.empty_like(x0) if out is None else out
+    f = field.struct()
+    if ws is None:
+        ws = torch.empty(max(morph_culled_workspace(field, N), 16), device=x0.device, dtype=torch.uint8)
+    _check(L.pdmp_morph_culled(ctypes.byref(f), _ptr(x0, shape=(N, d), name="x0"), N, int(T), float(eta),
+                               float(r_cut), _ptr(xT), _ptr(ckpt, name="ckpt"), int(k), _ptr(ws, dtype=torch.uint8),
+                               ws.numel(), _ptr(work, dtype=torch.int64, name="work"), _stream()),
+           "pdmp_morph_culled")
+    return xT
+
+
+def morph_inverse(field: DeviceField, z: torch.Tensor, T: int, eta: float, tol: float = 1e-6, maxit: int = 60,
+                  want_iters: bool = False):
+    """Eq. (2): the inverse of the T-step map by per-step fixed points."""
+    fn = lib().pdmp_morph_inverse
+    N, d = z.shape[0], field.d
+    y = torch.empty_like(z)
+    its = torch.empty(N, device=z.device, dtype=torch.int32) if want_iters else None
+    f = field.struct()
+    _check(fn(ctypes.byref(f), _ptr(z, shape=(N, d), name="z"), N, int(T), float(eta), float(tol), int(maxit),
+              _ptr(y), _ptr(its, dtype=torch.int32, name="iters"), _stream()), "pdmp_morph_inverse")
+    return (y, its) if want_iters else y
+
+
+def log_density(field: DeviceField, z: torch.Tensor, T: int, eta: float, lo, hi, tol: float = 1e-6,
+                maxit: int = 60):
+    """log p_z of morphed samples for a base density uniform on [lo, hi]; returns (log_p, y = phi^{-1}(z))."""
+    fn = lib().pdmp_log_density
+    N, d = z.shape[0], field.d
+    lo_h = (ctypes.c_double * d)(*[float(v) for v in lo])
+    hi_h = (ctypes.c_double * d)(*[float(v) for v in hi])
+    y = torch.empty_like(z)
+    lp = torch.empty(N, device=z.device, dtype=torch.float32)
+    f = field.struct()
+    _check(fn(ctypes.byref(f), _ptr(z, shape=(N, d), name="z"), N, int(T), float(eta), ctypes.addressof(lo_h),
+              ctypes.addressof(hi_h), float(tol), int(maxit), _ptr(y), _ptr(lp), _stream()), "pdmp_log_density")
+    return lp, y
 
 
 def morph_vjp_workspace(field: DeviceField, N: int, T: int, k: int, want_param_grad: bool) -> int:

@@ -7,6 +7,7 @@
 
 namespace pdmp {
 __device__ int32_t g_device_flag = 0;
+__device__ double g_abs_weight_sum = 0.0;
 }
 
 using namespace pdmp_host;
@@ -123,6 +124,66 @@ pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t 
                                           nullptr, ws, st));
 }
 
+static bool cull_field(const pdmp_field* f) { return f->kind == PDMP_KIND_RBF && (f->d == 2 || f->d == 3); }
+
+size_t pdmp_morph_culled_workspace(const pdmp_field* f, int64_t N) {
+  if (f == nullptr || check_field(f) != PDMP_OK || !cull_field(f) || N <= 0) return 0;
+  return pdmp::morph_rbf_cull_workspace(f->d, f->M, N);
+}
+
+pdmp_status pdmp_morph_culled(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float r_cut,
+                              float* xT, float* ckpt, int32_t k, void* ws, size_t ws_bytes,
+                              unsigned long long* work, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if (!cull_field(f)) return PDMP_ERR_UNSUPPORTED;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0 || !(r_cut > 0.0f) || !std::isfinite(r_cut)) return PDMP_ERR_INVALID_ARG;
+  if (ckpt != nullptr && (k < 1 || T % k != 0)) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || !ok_ptr(ckpt, false) || !ok_ptr(ws, true) ||
+      (reinterpret_cast<uintptr_t>(work) & 7u) != 0)
+    return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::morph_rbf_cull_workspace(f->d, f->M, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = as_stream(stream);
+  if (T == 0) {
+    if (xT != x0) return cuda_status(cudaMemcpyAsync(xT, x0, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st));
+    return PDMP_OK;
+  }
+  return cuda_status(pdmp::morph_rbf_cull(f->d, field_args(f), x0, N, T, eta, r_cut, xT, ckpt, k, ws, work, st));
+}
+
+pdmp_status pdmp_cull_radius(const pdmp_field* f, float eps, float* r_cut, double* w_abs, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if (f->kind != PDMP_KIND_RBF) return PDMP_ERR_UNSUPPORTED;
+  if (!(eps > 0.0f) || !std::isfinite(eps) || r_cut == nullptr) return PDMP_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  double* dsum = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&dsum, pdmp::g_abs_weight_sum);
+  if (e == cudaSuccess) e = pdmp::abs_weight_sum(f->w, f->M, dsum, st);
+  double W = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&W, dsum, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (w_abs) *w_abs = W;
+  // smallest r >= 1/sqrt(2 gamma) with W max(1, 2 gamma r) exp(-gamma r^2) <= eps (decreasing there)
+  const double g = f->gamma;
+  auto bound = [&](double r) { return W * std::fmax(1.0, 2.0 * g * r) * std::exp(-g * r * r); };
+  double lo = 1.0 / std::sqrt(2.0 * g), hi = lo;
+  if (bound(lo) > (double)eps) {
+    while (bound(hi) > (double)eps) hi *= 2.0;
+    for (int i = 0; i < 200 && hi - lo > 1e-12 * hi; ++i) {
+      const double mid = 0.5 * (lo + hi);
+      if (bound(mid) > (double)eps) lo = mid; else hi = mid;
+    }
+  }
+  float r = (float)hi;
+  if ((double)r < hi) r = std::nextafter(r, INFINITY);
+  *r_cut = r;
+  return PDMP_OK;
+}
+
 pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* traj,
                              float* steps, void* ws, size_t ws_bytes, void* stream) {
   pdmp_status s = check_field(f);
@@ -136,6 +197,39 @@ pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, in
   if (T == 0) return cuda_status(cudaMemcpyAsync(traj, x0, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st));
   return cuda_status(pdmp::morph_dispatch(f->kind, f->d, field_args(f), x0, N, T, eta, nullptr, nullptr, 0, traj,
                                           steps, ws, st));
+}
+
+pdmp_status pdmp_morph_inverse(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, float tol,
+                               int32_t maxit, float* y, int32_t* iters, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0 || maxit < 1 || !(tol >= 0.0f) || !std::isfinite(tol)) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(z, true) || !ok_ptr(y, true) || !ok_ptr(iters, false)) return PDMP_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  if (T == 0) {
+    if (y != z) return cuda_status(cudaMemcpyAsync(y, z, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st));
+    return PDMP_OK;
+  }
+  return cuda_status(pdmp::morph_inverse(f->kind, f->d, field_args(f), z, N, T, eta, tol, maxit, y, iters, st));
+}
+
+pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, const double* lo,
+                             const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0 || maxit < 1 || !(tol >= 0.0f) || !std::isfinite(tol) || !lo || !hi) return PDMP_ERR_INVALID_ARG;
+  for (int j = 0; j < f->d; ++j)
+    if (!(hi[j] > lo[j]) || !std::isfinite(lo[j]) || !std::isfinite(hi[j])) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(z, true) || !ok_ptr(y, true) || !ok_ptr(log_p, true) || y == z) return PDMP_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  if ((s = pdmp_morph_inverse(f, z, N, T, eta, tol, maxit, y, nullptr, stream)) != PDMP_OK) return s;
+  if ((s = cuda_status(pdmp::logdet(f->kind, f->d, field_args(f), y, N, T, eta, log_p, nullptr, st))) != PDMP_OK)
+    return s;
+  return cuda_status(pdmp::uniform_log_density(y, N, f->d, lo, hi, log_p, st));
 }
 
 size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32_t k, int32_t want_param_grad) {

@@ -40,8 +40,14 @@ __device__ __forceinline__ u64 ex2x2(u64 a) {
 // Tile shape: W warps per block (each summing over its share of M) and K
 // samples per lane (even: f32x2 pairs).  The single-field launch uses
 // W = 4, K = 8; the batched launch picks among a few shapes (autotuned).
-constexpr int kWarpStage = 64;                 // centres per warp per shared-memory stage
-constexpr int kFastUnroll = 2;                 // centres per unrolled inner iteration
+#ifndef PDMP_WARP_STAGE
+#define PDMP_WARP_STAGE 64
+#endif
+#ifndef PDMP_FAST_UNROLL
+#define PDMP_FAST_UNROLL 2
+#endif
+constexpr int kWarpStage = PDMP_WARP_STAGE;    // centres per warp per shared-memory stage
+constexpr int kFastUnroll = PDMP_FAST_UNROLL;  // centres per unrolled inner iteration
 
 template <int W, int K>
 struct Shape {
@@ -199,29 +205,91 @@ struct TileArgs {
   float* s_out;   // optional: the logit s(x_{T-1}) of the last step, per sample
 };
 
-template <int D, int W, int K, bool TRACE>
-__device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t p_end, unsigned char* smem) {
-  using S_ = Shape<W, K>;
-  constexpr int RP = FastRec<D>::kPairs;
-  constexpr int P = S_::kPairs;
-  constexpr int kTile = S_::kTile;
-  constexpr int KT = FastRec<D>::kTab;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // each warp owns a contiguous slice of the centres and its own stage buffers
-  u64* wbuf = reinterpret_cast<u64*>(smem) + (size_t)warp * 2 * kWarpStage * RP;
-  float4* red = reinterpret_cast<float4*>(smem);   // aliases the stage buffers after a step's last stage
-  float4* wraw = reinterpret_cast<float4*>(smem + fast_region0_bytes<D, W, K>()) + (size_t)warp * kWarpStage * KT;
-  const float4* __restrict__ tab = a.tab;
-  const int64_t M = a.M, N = a.N;
-  const float gamma = a.gamma, bias = a.bias, eta = a.eta;
-  const int T = a.T;
-  const float gl2e = gamma * kLog2e;
-  const int64_t Mw = ((M + W - 1) / W + kWarpStage - 1) / kWarpStage * kWarpStage;   // slice length
-  const int64_t mbase = (int64_t)warp * Mw;
-  const int nstage = (int)(Mw / kWarpStage);
+// Bounding box of the tile's active samples (identical in every warp: each
+// warp holds all of them); its centre o is the origin of the expanded form,
+// which the step uses only while g' R^2 <= 4 (R the half-diagonal).
+template <int D, int K>
+__device__ __forceinline__ bool tile_frame(const float (&x)[K][D], const bool (&act)[K], float gl2e, float (&lo)[D],
+                                           float (&hi)[D], float (&o)[D]) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) { lo[j] = INFINITY; hi[j] = -INFINITY; }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (act[k])
+#pragma unroll
+      for (int j = 0; j < D; ++j) { lo[j] = fminf(lo[j], x[k][j]); hi[j] = fmaxf(hi[j], x[k][j]); }
+  float R2 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], s));
+      hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], s));
+    }
+    o[j] = 0.5f * (lo[j] + hi[j]);
+    float h = 0.5f * (hi[j] - lo[j]);
+    R2 = fmaf(h, h, R2);
+  }
+  const bool expanded = (gl2e * R2 <= 4.0f) && (o[0] == o[0]);
+  if (!expanded)
+#pragma unroll
+    for (int j = 0; j < D; ++j) o[j] = 0.0f;
+  return expanded;
+}
 
-  float x[K][D];
-  bool act[K];
+// Adds the kWarpStage staged records rec to the pair sums S, G of this lane's
+// samples (U: the samples relative to the origin, packed in pairs).
+template <int D, int P>
+__device__ __forceinline__ void stage_accumulate(const u64* rec, bool expanded, float gl2e, const u64 (&U)[P][D],
+                                                 u64 (&S)[P], u64 (&G)[P][D]) {
+  constexpr int RP = FastRec<D>::kPairs;
+  if (expanded) {
+#pragma unroll kFastUnroll
+    for (int c = 0; c < kWarpStage; ++c) {
+      const ulonglong2* q = reinterpret_cast<const ulonglong2*>(rec + (size_t)c * RP);
+      u64 r[RP];
+#pragma unroll
+      for (int j = 0; j < RP / 2; ++j) {
+        ulonglong2 v = q[j];
+        r[2 * j] = v.x;
+        r[2 * j + 1] = v.y;
+      }
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        u64 arg = fma2(r[1], U[i][0], r[0]);
+#pragma unroll
+        for (int j = 1; j < D; ++j) arg = fma2(r[1 + j], U[i][j], arg);
+        const u64 e = ex2x2(arg);
+        S[i] = fma2(r[D + 1], e, S[i]);
+#pragma unroll
+        for (int j = 0; j < D; ++j) G[i][j] = fma2(e, r[D + 2 + j], G[i][j]);
+      }
+    }
+  } else {
+    const u64 ng = pk(-gl2e, -gl2e);
+    for (int c = 0; c < kWarpStage; ++c) {
+      const u64* r = rec + (size_t)c * RP;
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        u64 dx[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) dx[j] = add2(U[i][j], r[j]);
+        u64 r2 = mul2(dx[0], dx[0]);
+#pragma unroll
+        for (int j = 1; j < D; ++j) r2 = fma2(dx[j], dx[j], r2);
+        const u64 we = mul2(r[D + 1], ex2x2(fma2(r2, ng, r[D])));
+        S[i] = add2(S[i], we);
+#pragma unroll
+        for (int j = 0; j < D; ++j) G[i][j] = fma2(we, dx[j], G[i][j]);
+      }
+    }
+  }
+}
+
+// Loads the tile's samples (sorted positions [p0, p_end)).
+template <int D, int K>
+__device__ __forceinline__ void tile_load(const TileArgs& a, int64_t p0, int64_t p_end, int lane, float (&x)[K][D],
+                                          bool (&act)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int64_t p = p0 + k * 32 + lane;
@@ -230,34 +298,136 @@ __device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t
 #pragma unroll
     for (int j = 0; j < D; ++j) x[k][j] = act[k] ? a.x0[n * D + j] : 0.0f;
   }
+}
 
-  for (int t = 0; t < T; ++t) {
-    // tile origin and half-diagonal (identical in every warp)
-    float lo[D], hi[D];
+// End of step t: the warps' partial sums are added in a fixed order (every
+// warp computes the same totals), then the Euler update of Eq. (1); warp 0
+// writes the trace, the last logit and the checkpoint.  Begins and ends with
+// a block barrier (the reduction buffer aliases the stage buffers).
+template <int D, int W, int K, bool TRACE>
+__device__ __forceinline__ void tile_finish_step(const TileArgs& a, int t, int64_t p0, const bool (&act)[K],
+                                                 float (&x)[K][D], const float (&o)[D], bool expanded,
+                                                 const u64 (&S)[K / 2], const u64 (&G)[K / 2][D], float4* red,
+                                                 int warp, int lane) {
+  constexpr int P = K / 2;
+  constexpr int kTile = 32 * K;
+  const int64_t N = a.N;
+  const float gamma = a.gamma, bias = a.bias, eta = a.eta;
+  const int T = a.T;
+  const float gl2e = gamma * kLog2e;
+  __syncthreads();   // every warp has finished its centres before the reduction buffer overwrites the stages
 #pragma unroll
-    for (int j = 0; j < D; ++j) { lo[j] = INFINITY; hi[j] = -INFINITY; }
+  for (int i = 0; i < P; ++i) {
+    float s0, s1, g0[D], g1[D];
+    upk(S[i], s0, s1);
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (act[k])
+    for (int j = 0; j < D; ++j) upk(G[i][j], g0[j], g1[j]);
+    red[warp * kTile + (2 * i) * 32 + lane] = make_float4(s0, g0[0], g0[1], D == 3 ? g0[D - 1] : 0.0f);
+    red[warp * kTile + (2 * i + 1) * 32 + lane] = make_float4(s1, g1[0], g1[1], D == 3 ? g1[D - 1] : 0.0f);
+  }
+  __syncthreads();
 #pragma unroll
-        for (int j = 0; j < D; ++j) { lo[j] = fminf(lo[j], x[k][j]); hi[j] = fmaxf(hi[j], x[k][j]); }
-    float o[D], R2 = 0.0f;
+  for (int k = 0; k < K; ++k) {
+    float4 acc = red[k * 32 + lane];
+#pragma unroll
+    for (int w = 1; w < W; ++w) {
+      float4 b = red[w * kTile + k * 32 + lane];
+      acc.x += b.x;
+      acc.y += b.y;
+      acc.z += b.z;
+      acc.w += b.w;
+    }
+    const float Ssum = acc.x, Gs[3] = {acc.y, acc.z, acc.w};
+    float shat, ghat[D];
+    if (expanded) {
+      float u[D], u2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        u[j] = x[k][j] - o[j];
+        u2 = fmaf(u[j], u[j], u2);
+      }
+      const float f = ex2_approx(-gl2e * u2);
+      shat = f * Ssum;
+#pragma unroll
+      for (int j = 0; j < D; ++j) ghat[j] = f * fmaf(u[j], Ssum, -Gs[j]);
+    } else {
+      shat = Ssum;
+#pragma unroll
+      for (int j = 0; j < D; ++j) ghat[j] = Gs[j];
+    }
+    float d1, d2;
+    sigmoid_d12(shat + bias, d1, d2);
+    const float c = -eta * d1;
+    const int64_t p = p0 + k * 32 + lane;
+    const bool own = act[k] && warp == 0;
+    const int64_t n = (own && (TRACE || a.s_out != nullptr)) ? (int64_t)a.perm[p] - a.perm_base : 0;
+    if (own && a.s_out != nullptr && t == T - 1) a.s_out[n] = shat + bias;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-#pragma unroll
-      for (int s = 16; s > 0; s >>= 1) {
-        lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], s));
-        hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], s));
+      const float inc = __fmul_rn(c, -2.0f * gamma * ghat[j]);
+      if (TRACE && act[k] && warp == 0) {
+        a.traj[((int64_t)t * N + n) * D + j] = x[k][j];
+        a.steps[((int64_t)t * N + n) * D + j] = inc;
       }
-      o[j] = 0.5f * (lo[j] + hi[j]);
-      float h = 0.5f * (hi[j] - lo[j]);
-      R2 = fmaf(h, h, R2);
+      x[k][j] = __fadd_rn(x[k][j], inc);
     }
-    const bool expanded = (gl2e * R2 <= 4.0f) && (o[0] == o[0]);
-    if (!expanded)
+  }
+  __syncthreads();   // every warp has read the reduction buffer before the next step rebuilds the stages
+  if (a.ckpt != nullptr && (t + 1) % a.kck == 0 && warp == 0) {
+    float* dst = a.ckpt + (int64_t)((t + 1) / a.kck - 1) * N * D;
 #pragma unroll
-      for (int j = 0; j < D; ++j) o[j] = 0.0f;
+    for (int k = 0; k < K; ++k)
+      if (act[k]) {
+        const int64_t n = (int64_t)a.perm[p0 + k * 32 + lane] - a.perm_base;
+#pragma unroll
+        for (int j = 0; j < D; ++j) dst[n * D + j] = x[k][j];
+      }
+  }
+}
 
+// Writes x_T (and the trace's last state) of the tile's samples.
+template <int D, int K, bool TRACE>
+__device__ __forceinline__ void tile_store(const TileArgs& a, int64_t p0, const bool (&act)[K],
+                                           const float (&x)[K][D], int warp, int lane) {
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (act[k]) {
+        const int64_t n = (int64_t)a.perm[p0 + k * 32 + lane] - a.perm_base;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          if (a.xT) a.xT[n * D + j] = x[k][j];
+          if (TRACE) a.traj[((int64_t)a.T * a.N + n) * D + j] = x[k][j];
+        }
+      }
+  }
+  __syncthreads();   // the next tile of this block reuses the shared memory
+}
+
+template <int D, int W, int K, bool TRACE>
+__device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t p_end, unsigned char* smem) {
+  constexpr int RP = FastRec<D>::kPairs;
+  constexpr int P = K / 2;
+  constexpr int KT = FastRec<D>::kTab;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // each warp owns a contiguous slice of the centres and its own stage buffers
+  u64* wbuf = reinterpret_cast<u64*>(smem) + (size_t)warp * 2 * kWarpStage * RP;
+  float4* red = reinterpret_cast<float4*>(smem);   // aliases the stage buffers after a step's last stage
+  float4* wraw = reinterpret_cast<float4*>(smem + fast_region0_bytes<D, W, K>()) + (size_t)warp * kWarpStage * KT;
+  const float4* __restrict__ tab = a.tab;
+  const int64_t M = a.M;
+  const float gl2e = a.gamma * kLog2e;
+  const int64_t Mw = ((M + W - 1) / W + kWarpStage - 1) / kWarpStage * kWarpStage;   // slice length
+  const int64_t mbase = (int64_t)warp * Mw;
+  const int nstage = (int)(Mw / kWarpStage);
+
+  float x[K][D];
+  bool act[K];
+  tile_load<D, K>(a, p0, p_end, lane, x, act);
+
+  for (int t = 0; t < a.T; ++t) {
+    float lo[D], hi[D], o[D];
+    const bool expanded = tile_frame<D, K>(x, act, gl2e, lo, hi, o);
     u64 U[P][D], S[P], G[P][D];
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -274,137 +444,15 @@ __device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t
     __syncwarp();
     for (int st = 0; st < nstage; ++st) {
       if (st + 1 < nstage) stage_prefetch<D>(tab, M, mbase + (int64_t)(st + 1) * kWarpStage, wraw, lane);
-      const u64* rec = wbuf + (size_t)(st & 1) * kWarpStage * RP;
-      if (expanded) {
-#pragma unroll kFastUnroll
-        for (int c = 0; c < kWarpStage; ++c) {
-          const ulonglong2* q = reinterpret_cast<const ulonglong2*>(rec + (size_t)c * RP);
-          u64 r[RP];
-#pragma unroll
-          for (int j = 0; j < RP / 2; ++j) {
-            ulonglong2 v = q[j];
-            r[2 * j] = v.x;
-            r[2 * j + 1] = v.y;
-          }
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            u64 arg = fma2(r[1], U[i][0], r[0]);
-#pragma unroll
-            for (int j = 1; j < D; ++j) arg = fma2(r[1 + j], U[i][j], arg);
-            const u64 e = ex2x2(arg);
-            S[i] = fma2(r[D + 1], e, S[i]);
-#pragma unroll
-            for (int j = 0; j < D; ++j) G[i][j] = fma2(e, r[D + 2 + j], G[i][j]);
-          }
-        }
-      } else {
-        const u64 ng = pk(-gl2e, -gl2e);
-        for (int c = 0; c < kWarpStage; ++c) {
-          const u64* r = rec + (size_t)c * RP;
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            u64 dx[D];
-#pragma unroll
-            for (int j = 0; j < D; ++j) dx[j] = add2(U[i][j], r[j]);
-            u64 r2 = mul2(dx[0], dx[0]);
-#pragma unroll
-            for (int j = 1; j < D; ++j) r2 = fma2(dx[j], dx[j], r2);
-            const u64 we = mul2(r[D + 1], ex2x2(fma2(r2, ng, r[D])));
-            S[i] = add2(S[i], we);
-#pragma unroll
-            for (int j = 0; j < D; ++j) G[i][j] = fma2(we, dx[j], G[i][j]);
-          }
-        }
-      }
+      stage_accumulate<D, P>(wbuf + (size_t)(st & 1) * kWarpStage * RP, expanded, gl2e, U, S, G);
       if (st + 1 < nstage)
         stage_build<D>(M, mbase + (int64_t)(st + 1) * kWarpStage, expanded, o, gl2e, wraw,
                        wbuf + (size_t)((st + 1) & 1) * kWarpStage * RP, lane);
       __syncwarp();
     }
-    __syncthreads();   // every warp has finished its slice before the reduction buffer overwrites the stages
-
-    // partial sums -> shared memory, then the same fixed-order total in every warp
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      float s0, s1, g0[D], g1[D];
-      upk(S[i], s0, s1);
-#pragma unroll
-      for (int j = 0; j < D; ++j) upk(G[i][j], g0[j], g1[j]);
-      red[warp * kTile + (2 * i) * 32 + lane] = make_float4(s0, g0[0], g0[1], D == 3 ? g0[D - 1] : 0.0f);
-      red[warp * kTile + (2 * i + 1) * 32 + lane] = make_float4(s1, g1[0], g1[1], D == 3 ? g1[D - 1] : 0.0f);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      float4 acc = red[k * 32 + lane];
-#pragma unroll
-      for (int w = 1; w < W; ++w) {
-        float4 b = red[w * kTile + k * 32 + lane];
-        acc.x += b.x;
-        acc.y += b.y;
-        acc.z += b.z;
-        acc.w += b.w;
-      }
-      const float Ssum = acc.x, Gs[3] = {acc.y, acc.z, acc.w};
-      float shat, ghat[D];
-      if (expanded) {
-        float u[D], u2 = 0.0f;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          u[j] = x[k][j] - o[j];
-          u2 = fmaf(u[j], u[j], u2);
-        }
-        const float f = ex2_approx(-gl2e * u2);
-        shat = f * Ssum;
-#pragma unroll
-        for (int j = 0; j < D; ++j) ghat[j] = f * fmaf(u[j], Ssum, -Gs[j]);
-      } else {
-        shat = Ssum;
-#pragma unroll
-        for (int j = 0; j < D; ++j) ghat[j] = Gs[j];
-      }
-      float d1, d2;
-      sigmoid_d12(shat + bias, d1, d2);
-      const float c = -eta * d1;
-      const int64_t p = p0 + k * 32 + lane;
-      const bool own = act[k] && warp == 0;
-      const int64_t n = (own && (TRACE || a.s_out != nullptr)) ? (int64_t)a.perm[p] - a.perm_base : 0;
-      if (own && a.s_out != nullptr && t == T - 1) a.s_out[n] = shat + bias;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        const float inc = __fmul_rn(c, -2.0f * gamma * ghat[j]);
-        if (TRACE && act[k] && warp == 0) {
-          a.traj[((int64_t)t * N + n) * D + j] = x[k][j];
-          a.steps[((int64_t)t * N + n) * D + j] = inc;
-        }
-        x[k][j] = __fadd_rn(x[k][j], inc);
-      }
-    }
-    __syncthreads();   // every warp has read the reduction buffer before the next step rebuilds the stages
-    if (a.ckpt != nullptr && (t + 1) % a.kck == 0 && warp == 0) {
-      float* dst = a.ckpt + (int64_t)((t + 1) / a.kck - 1) * N * D;
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        if (act[k]) {
-          const int64_t n = (int64_t)a.perm[p0 + k * 32 + lane] - a.perm_base;
-#pragma unroll
-          for (int j = 0; j < D; ++j) dst[n * D + j] = x[k][j];
-        }
-    }
+    tile_finish_step<D, W, K, TRACE>(a, t, p0, act, x, o, expanded, S, G, red, warp, lane);
   }
-  if (warp == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (act[k]) {
-        const int64_t n = (int64_t)a.perm[p0 + k * 32 + lane] - a.perm_base;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          if (a.xT) a.xT[n * D + j] = x[k][j];
-          if (TRACE) a.traj[((int64_t)T * N + n) * D + j] = x[k][j];
-        }
-      }
-  }
-  __syncthreads();   // the next tile of this block reuses the shared memory
+  tile_store<D, K, TRACE>(a, p0, act, x, warp, lane);
 }
 
 }  // namespace pdmp

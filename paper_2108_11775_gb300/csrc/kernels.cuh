@@ -22,6 +22,17 @@ size_t morph_workspace(int kind, int d, int64_t M, int64_t N);
 cudaError_t morph_dispatch(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta,
                            float* xT, float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
 
+cudaError_t morph_inverse(int kind, int d, const FieldArgs& fa, const float* z, int64_t N, int T, float eta,
+                          float tol, int maxit, float* y, int32_t* iters, cudaStream_t st);
+
+size_t morph_rbf_cull_workspace(int d, int64_t M, int64_t N);
+cudaError_t morph_rbf_cull(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float r_cut,
+                           float* xT, float* ckpt, int k, void* ws, unsigned long long* work, cudaStream_t st);
+cudaError_t abs_weight_sum(const float* w, int64_t M, double* out, cudaStream_t st);
+
+cudaError_t uniform_log_density(const float* y, int64_t N, int d, const double* lo, const double* hi, float* lp,
+                                cudaStream_t st);
+
 int64_t vjp_blocks(int64_t N);
 cudaError_t morph_vjp(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                       const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias,

@@ -191,6 +191,20 @@ cudaError_t spatial_sort(int d, const float* x, int64_t N, const SortWs& s, cuda
   return sort_by_keys(s.keys, N, s.counts, s.offs, s.cursor, s.chunk_tot, s.cells, s.perm, st);
 }
 
+cudaError_t bounding_box(int d, const float* x, int64_t N, uint32_t* box, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(box, 0xff, sizeof(uint32_t) * d, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(box + d, 0x00, sizeof(uint32_t) * d, st)) != cudaSuccess) return e;
+  if (N <= 0) return cudaSuccess;
+  const unsigned nb = (unsigned)((N + 255) / 256);
+  const unsigned bb = nb < 1024 ? nb : 1024;
+  if (d == 2)
+    k_bbox<2><<<bb, 256, 0, st>>>(x, N, box);
+  else
+    k_bbox<3><<<bb, 256, 0, st>>>(x, N, box);
+  return cudaGetLastError();
+}
+
 cudaError_t exclusive_scan_u32(const uint32_t* in, int64_t n, uint32_t* out, uint32_t* chunk_tot, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t nchunks = (n + kScanChunk - 1) / kScanChunk;

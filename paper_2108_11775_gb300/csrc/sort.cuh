@@ -60,6 +60,8 @@ struct SortWs {
 int sort_bits(int d, int64_t N);
 SortWs sort_layout(void* ws, int d, int64_t N);
 size_t sort_workspace(int d, int64_t N);
+// bounding box of N points (d = 2, 3) as 2d ordered-float words: box[j] = min, box[d + j] = max
+cudaError_t bounding_box(int d, const float* x, int64_t N, uint32_t* box, cudaStream_t st);
 cudaError_t spatial_sort(int d, const float* x, int64_t N, const SortWs& s, cudaStream_t st);
 // exclusive prefix sum of n uint32 values (chunk_tot: ceil(n / kScanChunk) scratch words)
 cudaError_t exclusive_scan_u32(const uint32_t* in, int64_t n, uint32_t* out, uint32_t* chunk_tot, cudaStream_t st);

@@ -146,3 +146,57 @@ def test_labels_validation():
     assert L.pdmp_box_labels(9, A, 1, A, 10, A, None) == 1
     assert L.pdmp_box_labels(2, None, 3, A, 10, A, None) == 1
     assert L.pdmp_box_labels(2, A, 1, A, 0, A, None) == 0
+
+
+@nogpu
+def test_inverse_validation():
+    L = pdmp.lib()
+    fn = L.pdmp_morph_inverse
+    f = ctypes.byref(fld())
+    assert fn(f, A, 8, 4, 0.01, 1e-6, 0, A, None, None) == 1            # maxit < 1
+    assert fn(f, A, 8, 4, 0.01, -1.0, 10, A, None, None) == 1           # negative tolerance
+    assert fn(f, A, 8, 4, 0.01, float("nan"), 10, A, None, None) == 1
+    assert fn(f, MIS, 8, 4, 0.01, 1e-6, 10, A, None, None) == 1
+    assert fn(f, A, 8, 4, 0.01, 1e-6, 10, A, MIS + 1, None) == 1       # iters not 4-byte aligned
+    assert fn(f, A, -1, 4, 0.01, 1e-6, 10, A, None, None) == 1
+    assert fn(f, None, 0, 4, 0.01, 1e-6, 10, None, None, None) == 0      # empty batch
+    assert fn(ctypes.byref(fld(lipschitz=100.0)), A, 8, 4, 0.5, 1e-6, 10, A, None, None) == 2
+
+
+@nogpu
+def test_log_density_validation():
+    fn = pdmp.lib().pdmp_log_density
+    lo = (ctypes.c_double * 2)(0, 0)
+    hi = (ctypes.c_double * 2)(10, 10)
+    flat = (ctypes.c_double * 2)(10, 0)
+    f = ctypes.byref(fld())
+    P = lambda a: ctypes.cast(a, ctypes.POINTER(ctypes.c_double))
+    assert fn(f, A, 8, 4, 0.01, P(lo), P(flat), 1e-6, 10, A + 4096, A, None) == 1     # empty box
+    assert fn(f, A, 8, 4, 0.01, None, P(hi), 1e-6, 10, A + 4096, A, None) == 1
+    assert fn(f, A, 8, 4, 0.01, P(lo), P(hi), 1e-6, 10, A, A + 4096, None) == 1       # y aliases z
+    assert fn(f, A, 8, 4, 0.01, P(lo), P(hi), 1e-6, 0, A + 4096, A + 8192, None) == 1
+    assert fn(f, None, 0, 4, 0.01, P(lo), P(hi), 1e-6, 10, None, None, None) == 0
+
+
+@nogpu
+def test_culled_validation():
+    L = pdmp.lib()
+    f = fld()
+    need = L.pdmp_morph_culled_workspace(ctypes.byref(f), 1000)
+    assert need > 1000 * 8
+    assert L.pdmp_morph_culled_workspace(ctypes.byref(fld(kind=1, d=7, phase=A)), 1000) == 0
+    call = lambda ff, **kw: L.pdmp_morph_culled(
+        ctypes.byref(ff), kw.get("x0", A), kw.get("N", 1000), kw.get("T", 4), kw.get("eta", 0.01),
+        kw.get("r", 1.0), kw.get("xT", A), None, 0, kw.get("ws", A), kw.get("ws_bytes", need), kw.get("work", None),
+        None)
+    assert call(fld(kind=1, d=7, phase=A)) == 8                 # RFF: unsupported
+    assert call(fld(d=1)) == 8
+    assert call(f, r=0.0) == 1
+    assert call(f, r=float("inf")) == 1
+    assert call(f, ws=None) == 1
+    assert call(f, ws_bytes=need - 1) == 3
+    assert call(f, work=A + 4) == 1                              # not 8-byte aligned
+    assert call(f, N=0, x0=None, xT=None, ws=None) == 0
+    r = ctypes.c_float(0)
+    assert L.pdmp_cull_radius(ctypes.byref(f), 0.0, ctypes.byref(r), None, None) == 1
+    assert L.pdmp_cull_radius(ctypes.byref(fld(kind=1, d=7, phase=A)), 1e-6, ctypes.byref(r), None, None) == 8

@@ -363,3 +363,57 @@ def test_fit_full_size_2d_learns_the_boxes():
     sub = slice(0, 20000)
     lo_, _, _ = oracle.fit_objective(wk.field, wk.fit_X[sub], wk.fit_y[sub], 1e-4, w.cpu().numpy(), b)
     assert abs(lo_ - loss) < 0.05
+
+
+# --------------------------------------------------------------------------
+# Eq. (2): the inverse map
+@pytest.mark.parametrize("kind", [wl.RBF, wl.RFF])
+def test_inverse_matches_oracle_and_round_trips(kind):
+    f, x0, T, _, eta = _vjp_case(kind)
+    fld = pdmp.DeviceField.from_host(f)
+    z = pdmp.morph(fld, dev(x0), T, eta)
+    y, its = pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=80, want_iters=True)
+    y, its, z = y.cpu().numpy(), its.cpu().numpy(), z.cpu().numpy()
+    ref, _ = oracle.morph_inverse(f, z, T, eta, tol=1e-13, maxit=200)
+    assert max_abs(y, ref) <= 1e-4
+    assert max_abs(y, x0) <= 1e-4                      # round trip through the forward map
+    assert its.max() < 80
+    assert np.abs(z - x0).max() > 1e-3
+
+
+def test_log_density_matches_oracle_and_integrates_to_one():
+    """log p_z = log p_0(phi^{-1}(z)) - log det J: against the oracle's inverse
+    and log-det on sampled points, and normalised (Monte Carlo over a box that
+    contains the support of p_z)."""
+    w1 = wl.config1(N=256)
+    eta, _ = rbf_eta(w1.field, w1.lo, w1.hi)
+    T = 10
+    fld = pdmp.DeviceField.from_host(w1.field)
+    lo, hi = np.asarray(w1.lo, np.float64), np.asarray(w1.hi, np.float64)
+    # points of the base box pushed forward: log p_z(z) = -log vol - log det J(y)
+    y0 = wl.uniform_box(31, 3, 4096, lo, hi)
+    z = pdmp.morph(fld, dev(y0), T, eta)
+    lp, y = pdmp.log_density(fld, z, T, eta, lo, hi)
+    lp, y = lp.cpu().numpy(), y.cpu().numpy()
+    ref_ld, _, _ = oracle.logdet(w1.field, y0, T, eta)
+    inside = np.all((y0 > lo + 1e-3) & (y0 < hi - 1e-3), axis=1)
+    assert inside.mean() > 0.99
+    assert np.abs(lp[inside] - (-np.log(np.prod(hi - lo)) - ref_ld[inside])).max() <= 1e-4 * T
+    # arbitrary points, including outside the image of the box: the oracle's inverse decides
+    zq = wl.uniform_box(32, 3, 512, lo - 1.0, hi + 1.0)
+    lq, yq = pdmp.log_density(fld, dev(zq), T, eta, lo, hi)
+    lq, yq = lq.cpu().numpy(), yq.cpu().numpy()
+    ry, _ = oracle.morph_inverse(w1.field, zq, T, eta)
+    assert max_abs(yq, ry) <= 1e-4
+    rin = np.all((ry >= lo) & (ry <= hi), axis=1)
+    clear = np.all(np.minimum(np.abs(ry - lo), np.abs(ry - hi)) > 1e-3, axis=1)
+    assert np.array_equal(np.isfinite(lq)[clear], rin[clear])
+    rld, _, _ = oracle.logdet(w1.field, ry[rin & clear], T, eta)
+    assert np.abs(lq[rin & clear] + np.log(np.prod(hi - lo)) + rld).max() <= 1e-4 * T
+    # normalisation
+    n = 1 << 20
+    zb_lo, zb_hi = lo - 1.0, hi + 1.0
+    zs = wl.uniform_box(33, 3, n, zb_lo, zb_hi)
+    ls, _ = pdmp.log_density(fld, dev(zs), T, eta, lo, hi)
+    mass = float(torch.exp(ls.double()).mean()) * np.prod(zb_hi - zb_lo)
+    assert abs(mass - 1.0) <= 5e-3
