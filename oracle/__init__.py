@@ -21,6 +21,9 @@ below names the passage of the paper it follows:
 * ``fit`` / ``fit_objective`` -- Sec. 3.1: BCE minimised by gradient descent.
 * ``box_labels``     -- ground-truth occupancy labels of the dataset D.
 * ``mlp_*``          -- the surrogate network (no counterpart in the paper).
+* ``tnet_*``         -- Sec. 3.1's own occupancy model: a fully connected
+                        network with tanh hidden layers and a sigmoid output,
+                        used as the cost of the morph of Eq. (1).
 """
 from __future__ import annotations
 
@@ -88,7 +91,11 @@ def lib():
             L.orc_mlp_forward.argtypes = [_I, _ip, _dp, _dp, _dp, _L, _dp, _dp]
             L.orc_mlp_loss_backward.argtypes = [_I, _ip, _dp, _dp, _dp, _dp, _L, _dp, _dp, _dp]
             L.orc_mlp_encode.argtypes = [_dp, _L, _I, _dp]
-            for name in ("orc_eval", "orc_morph", "orc_morph_inverse", "orc_morph_vjp", "orc_logdet",
+            tnet = [_I, _I, _dp, _dp, _dp, _dp, _dp, _D]
+            L.orc_tnet_eval.argtypes = tnet + [_dp, _L, _dp, _dp, _dp, _dp]
+            L.orc_tnet_morph.argtypes = tnet + [_dp, _L, _I, _D, _dp]
+            L.orc_tnet_lipschitz.argtypes = [_I, _I, _dp, _dp, _dp, _dp, _dp]
+            for name in ("orc_tnet_eval", "orc_tnet_morph", "orc_tnet_lipschitz","orc_eval", "orc_morph", "orc_morph_inverse", "orc_morph_vjp", "orc_logdet",
                          "orc_lipschitz_rbf", "orc_lipschitz_rff", "orc_fit", "orc_fit_objective",
                          "orc_box_labels", "orc_mlp_forward", "orc_mlp_loss_backward", "orc_mlp_encode"):
                 getattr(L, name).restype = _I
@@ -312,3 +319,50 @@ def mlp_loss_backward(weights, biases, X, Y):
         ow += w.size
         ob += b.size
     return float(loss[0]), dws, dbs
+
+
+# ---------------------------------------------------------------------------
+class _Net:
+    """A tanh network's arrays promoted (exactly) to float64 and kept alive."""
+
+    def __init__(self, net):
+        self.W1, self.b1 = _d(net.W1), _d(net.b1)
+        self.W2, self.b2 = _d(net.W2), _d(net.b2)
+        self.w3, self.b3 = _d(net.w3), float(net.b3)
+        self.H, self.d = self.W1.shape
+        assert self.W2.shape == (self.H, self.H) and self.w3.shape == (self.H,)
+
+    def args(self):
+        return [self.d, self.H, _ptr(self.W1), _ptr(self.b1), _ptr(self.W2), _ptr(self.b2), _ptr(self.w3), self.b3]
+
+
+def tnet_evaluate(net, x, hess: bool = False) -> dict:
+    """Sec. 3.1: c = sigmoid(w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3) and its input derivatives."""
+    n = _Net(net)
+    x = _d(x).reshape(-1, n.d)
+    N = x.shape[0]
+    c, s, gc = np.zeros(N), np.zeros(N), np.zeros((N, n.d))
+    hc = np.zeros((N, n.d, n.d)) if hess else None
+    _check(lib().orc_tnet_eval(*n.args(), _ptr(x), N, _ptr(c), _ptr(s), _ptr(gc), _ptr(hc)), "tnet_eval")
+    out = {"c": c, "s": s, "grad": gc}
+    if hess:
+        out["hess"] = hc
+    return out
+
+
+def tnet_morph(net, x0, T: int, eta: float):
+    """Eq. (1) by Euler's method with the tanh network's occupancy as the cost."""
+    n = _Net(net)
+    x0 = _d(x0).reshape(-1, n.d)
+    xT = np.zeros_like(x0)
+    _check(lib().orc_tnet_morph(*n.args(), _ptr(x0), x0.shape[0], int(T), float(eta), _ptr(xT)), "tnet_morph")
+    return xT
+
+
+def tnet_lipschitz(net):
+    """(L, G): certified bounds on sup |Hess c|_2 and sup |grad s|_2 over all inputs."""
+    n = _Net(net)
+    L, G = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().orc_tnet_lipschitz(n.d, n.H, _ptr(n.W1), _ptr(n.W2), _ptr(n.w3), ctypes.byref(L),
+                                    ctypes.byref(G)), "tnet_lipschitz")
+    return float(L.value), float(G.value)

@@ -37,6 +37,10 @@
  *       dataset D of Sec. 3.1, from axis-aligned boxes.
  *   MLP forward/backward               -- the surrogate network (no
  *       counterpart in the paper): dense layers with SiLU, MSE loss.
+ *   tanh network cost                  -- Sec. 3.1's own occupancy model: a
+ *       fully connected network, tanh between hidden layers, sigmoid output;
+ *       its input gradient / Hessian, the morph of Eq. (1) through it, and a
+ *       certified Lipschitz bound from spectral norms.
  */
 #include <math.h>
 #include <pthread.h>
@@ -848,5 +852,210 @@ int orc_mlp_encode(const double* u, long n, int nf, double* out) {
       f *= 2.0;
     }
   }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* The paper's own occupancy network (Sec. 3.1): a fully connected       */
+/* network with tanh between the hidden layers and a sigmoid output.    */
+/* Two hidden layers of width H:                                        */
+/*   a1 = W1 x + b1, h1 = tanh(a1), a2 = W2 h1 + b2, h2 = tanh(a2),     */
+/*   s = w3 . h2 + b3,  c = sigma(s).                                   */
+/* W1 is H x d and W2 is H x H, row-major (row = output unit).          */
+/* ------------------------------------------------------------------ */
+#define TNET_HMAX 128
+
+typedef struct {
+  int d, H;
+  const double *W1, *b1, *W2, *b2, *w3;
+  double b3;
+} tnet_t;
+
+/* s, grad s and (optional) Hess s at x by the chain rule:
+ *   v2 = w3 (.) tanh'(a2),  u1 = W2^T v2,  g1 = u1 (.) tanh'(a1),  grad s = W1^T g1,
+ *   Hess s = W1^T diag(u1 (.) tanh''(a1)) W1 + P^T diag(w3 (.) tanh''(a2)) P,
+ *   P = W2 diag(tanh'(a1)) W1,
+ * with tanh' = 1 - tanh^2 and tanh'' = -2 tanh (1 - tanh^2). */
+static double tnet_logit(const tnet_t* n, const double* x, double* gs, double* hs) {
+  const int d = n->d, H = n->H;
+  double h1[TNET_HMAX], t1[TNET_HMAX], h2[TNET_HMAX], t2[TNET_HMAX], u1[TNET_HMAX];
+  for (int i = 0; i < H; ++i) {
+    double a = n->b1[i];
+    for (int k = 0; k < d; ++k) a += n->W1[i * d + k] * x[k];
+    h1[i] = tanh(a);
+    t1[i] = 1.0 - h1[i] * h1[i];
+  }
+  double s = n->b3;
+  for (int i = 0; i < H; ++i) {
+    double a = n->b2[i];
+    for (int j = 0; j < H; ++j) a += n->W2[i * H + j] * h1[j];
+    h2[i] = tanh(a);
+    t2[i] = 1.0 - h2[i] * h2[i];
+    s += n->w3[i] * h2[i];
+  }
+  for (int j = 0; j < H; ++j) {
+    double u = 0.0;
+    for (int i = 0; i < H; ++i) u += n->W2[i * H + j] * n->w3[i] * t2[i];
+    u1[j] = u;
+  }
+  for (int k = 0; k < d; ++k) {
+    double g = 0.0;
+    for (int j = 0; j < H; ++j) g += n->W1[j * d + k] * u1[j] * t1[j];
+    gs[k] = g;
+  }
+  if (hs) {
+    double P[TNET_HMAX * MAXD];
+    for (int i = 0; i < H; ++i)
+      for (int k = 0; k < d; ++k) {
+        double p = 0.0;
+        for (int j = 0; j < H; ++j) p += n->W2[i * H + j] * t1[j] * n->W1[j * d + k];
+        P[i * d + k] = p;
+      }
+    for (int k = 0; k < d; ++k)
+      for (int l = 0; l < d; ++l) {
+        double acc = 0.0;
+        for (int j = 0; j < H; ++j) acc += n->W1[j * d + k] * (u1[j] * (-2.0 * h1[j] * t1[j])) * n->W1[j * d + l];
+        for (int i = 0; i < H; ++i) acc += P[i * d + k] * (n->w3[i] * (-2.0 * h2[i] * t2[i])) * P[i * d + l];
+        hs[k * d + l] = acc;
+      }
+  }
+  return s;
+}
+
+static double tnet_cost(const tnet_t* n, const double* x, double* gc, double* hc, double* s_out) {
+  const int d = n->d;
+  double gs[MAXD], hs[MAXD * MAXD], sg[3];
+  double s = tnet_logit(n, x, gs, hc ? hs : NULL);
+  orc_sigmoid3(s, sg);
+  for (int i = 0; i < d; ++i) gc[i] = sg[1] * gs[i];
+  if (hc)
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) hc[i * d + j] = sg[1] * hs[i * d + j] + sg[2] * gs[i] * gs[j];
+  if (s_out) *s_out = s;
+  return sg[0];
+}
+
+static int tnet_ok(int d, int H) { return d >= 1 && d <= MAXD && H >= 1 && H <= TNET_HMAX; }
+
+typedef struct { const tnet_t* n; const double* X; double *c, *s, *gc, *hc; } tnet_eval_ctx;
+static void tnet_eval_range(void* p, long lo, long hi) {
+  tnet_eval_ctx* q = (tnet_eval_ctx*)p;
+  const int d = q->n->d;
+  for (long i = lo; i < hi; ++i) {
+    double s;
+    double c = tnet_cost(q->n, q->X + i * d, q->gc + i * d, q->hc ? q->hc + i * d * d : NULL, &s);
+    if (q->c) q->c[i] = c;
+    if (q->s) q->s[i] = s;
+  }
+}
+
+int orc_tnet_eval(int d, int H, const double* W1, const double* b1, const double* W2, const double* b2,
+                  const double* w3, double b3, const double* X, long n, double* c, double* s, double* gc,
+                  double* hc) {
+  if (!tnet_ok(d, H) || n < 0) return 1;
+  tnet_t net = {d, H, W1, b1, W2, b2, w3, b3};
+  tnet_eval_ctx q = {&net, X, c, s, gc, hc};
+  parallel_range(n, tnet_eval_range, &q);
+  return 0;
+}
+
+/* Eq. (1) by Euler's method with c the network's occupancy. */
+typedef struct { const tnet_t* n; const double* X0; int T; double eta; double* XT; } tnet_morph_ctx;
+static void tnet_morph_range(void* p, long lo, long hi) {
+  tnet_morph_ctx* q = (tnet_morph_ctx*)p;
+  const int d = q->n->d;
+  for (long i = lo; i < hi; ++i) {
+    double x[MAXD], g[MAXD];
+    for (int k = 0; k < d; ++k) x[k] = q->X0[i * d + k];
+    for (int t = 0; t < q->T; ++t) {
+      tnet_cost(q->n, x, g, NULL, NULL);
+      for (int k = 0; k < d; ++k) x[k] -= q->eta * g[k];
+    }
+    for (int k = 0; k < d; ++k) q->XT[i * d + k] = x[k];
+  }
+}
+
+int orc_tnet_morph(int d, int H, const double* W1, const double* b1, const double* W2, const double* b2,
+                   const double* w3, double b3, const double* X0, long n, int T, double eta, double* XT) {
+  if (!tnet_ok(d, H) || n < 0 || T < 0) return 1;
+  tnet_t net = {d, H, W1, b1, W2, b2, w3, b3};
+  tnet_morph_ctx q = {&net, X0, T, eta, XT};
+  parallel_range(n, tnet_morph_range, &q);
+  return 0;
+}
+
+/* Largest eigenvalue of a symmetric n x n matrix (cyclic Jacobi rotations
+ * until the off-diagonal mass is negligible); A is overwritten. */
+static double sym_max_eigenvalue(double* A, int n) {
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += A[i * n + j] * A[i * n + j];
+        if (i != j) off += A[i * n + j] * A[i * n + j];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {  /* columns p, q */
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = cs * akp - sn * akq;
+          A[k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {  /* rows p, q */
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = cs * apk - sn * aqk;
+          A[q * n + k] = sn * apk + cs * aqk;
+        }
+      }
+  }
+  double m = A[0];
+  for (int i = 1; i < n; ++i) m = A[i * n + i] > m ? A[i * n + i] : m;
+  return m;
+}
+
+/* spectral norm of the r x k matrix W from the largest eigenvalue of W^T W,
+ * with a relative margin for the eigenvalue's rounding */
+static double spectral_norm(const double* W, int r, int k) {
+  double* G = (double*)calloc((size_t)k * k, sizeof(double));
+  for (int a = 0; a < k; ++a)
+    for (int b = 0; b < k; ++b) {
+      double acc = 0.0;
+      for (int i = 0; i < r; ++i) acc += W[i * k + a] * W[i * k + b];
+      G[a * k + b] = acc;
+    }
+  double lam = sym_max_eigenvalue(G, k);
+  free(G);
+  return sqrt(fmax(lam, 0.0) * (1.0 + 1e-12));
+}
+
+/* Certified bounds over all of R^d (|tanh'| <= 1, |tanh''| <= 4/(3 sqrt 3)):
+ *   |grad s| <= G = |W1| |W2| |w3|_2,
+ *   |Hess s| <= |W1|^2 (k max_j sum_i |W2_ij| |w3_i| + k |W2|^2 max_i |w3_i|),
+ *   L = |Hess s| / 4 + G^2 / (6 sqrt 3)   (the sigmoid's |sigma'| <= 1/4, |sigma''| <= 1/(6 sqrt 3)),
+ * with |.| the spectral norm. */
+int orc_tnet_lipschitz(int d, int H, const double* W1, const double* W2, const double* w3, double* L, double* G) {
+  if (!tnet_ok(d, H)) return 1;
+  const double kappa = 4.0 / (3.0 * sqrt(3.0));
+  const double n1 = spectral_norm(W1, H, d), n2 = spectral_norm(W2, H, H);
+  double w3n = 0.0, w3max = 0.0, colmax = 0.0;
+  for (int i = 0; i < H; ++i) {
+    w3n += w3[i] * w3[i];
+    w3max = fmax(w3max, fabs(w3[i]));
+  }
+  for (int j = 0; j < H; ++j) {
+    double col = 0.0;
+    for (int i = 0; i < H; ++i) col += fabs(W2[i * H + j]) * fabs(w3[i]);
+    colmax = fmax(colmax, col);
+  }
+  const double g = n1 * n2 * sqrt(w3n);
+  const double hs = n1 * n1 * (kappa * colmax + kappa * n2 * n2 * w3max);
+  *G = g;
+  *L = 0.25 * hs + g * g / (6.0 * sqrt(3.0));
   return 0;
 }

@@ -415,3 +415,93 @@ def test_mlp_encoding_identities():
             np.testing.assert_allclose(s_, 2 * ps * pc, atol=1e-13)      # octaves double the angle
             np.testing.assert_allclose(c_, pc ** 2 - ps ** 2, atol=1e-13)
     np.testing.assert_allclose(e[:, 3:6], np.sin(np.pi * u), atol=1e-15)   # first octave is pi u
+
+
+# --------------------------------------------------------------------------
+# The tanh occupancy network of Sec. 3.1 as the cost
+def test_tanh_net_matches_sympy_on_a_tiny_network():
+    sp = pytest.importorskip("sympy")
+    net = wl.tanh_net(11, 2, 3, lo=0.0, hi=4.0, gain=1.5, out_scale=3.0, b3=0.3)
+    x0, x1 = sp.symbols("x0 x1")
+    X = sp.Matrix([x0, x1])
+    W1, b1 = sp.Matrix(net.W1.astype(float)), sp.Matrix(net.b1.astype(float))
+    W2, b2 = sp.Matrix(net.W2.astype(float)), sp.Matrix(net.b2.astype(float))
+    w3 = sp.Matrix(net.w3.astype(float))
+    h1 = (W1 * X + b1).applyfunc(sp.tanh)
+    h2 = (W2 * h1 + b2).applyfunc(sp.tanh)
+    s = (w3.T * h2)[0, 0] + net.b3
+    c = 1 / (1 + sp.exp(-s))
+    grad = [sp.diff(c, v) for v in (x0, x1)]
+    hess = [[sp.diff(c, a, b) for b in (x0, x1)] for a in (x0, x1)]
+    pts = wl.uniform_box(12, 3, 5, np.zeros(2), np.full(2, 4.0))
+    r = oracle.tnet_evaluate(net, pts, hess=True)
+    for i, p in enumerate(pts.astype(float)):
+        sub = {x0: p[0], x1: p[1]}
+        assert abs(r["c"][i] - float(c.subs(sub))) <= 1e-13
+        assert abs(r["s"][i] - float(s.subs(sub))) <= 1e-13
+        for a in range(2):
+            assert abs(r["grad"][i, a] - float(grad[a].subs(sub))) <= 1e-12
+            for b in range(2):
+                assert abs(r["hess"][i, a, b] - float(hess[a][b].subs(sub))) <= 1e-11
+
+
+@pytest.mark.parametrize("d,H", [(2, 64), (3, 32), (7, 16)])
+def test_tanh_net_derivatives_match_central_differences(d, H):
+    net = wl.tanh_net(13 + d, d, H, lo=-3.0, hi=3.0, gain=2.0, out_scale=2.0, b3=-0.5)
+    x = wl.uniform_box(14, 3, 6, np.full(d, -3.0), np.full(d, 3.0)).astype(np.float64)
+    r = oracle.tnet_evaluate(net, x, hess=True)
+    h = 1e-5
+    for i in range(x.shape[0]):
+        for a in range(d):
+            e = np.zeros(d)
+            e[a] = h
+            cp = oracle.tnet_evaluate(net, (x[i] + e)[None], hess=False)
+            cm = oracle.tnet_evaluate(net, (x[i] - e)[None], hess=False)
+            fd_g = (cp["c"][0] - cm["c"][0]) / (2 * h)
+            assert abs(r["grad"][i, a] - fd_g) <= 1e-8
+            fd_h = (cp["grad"][0] - cm["grad"][0]) / (2 * h)
+            assert np.abs(r["hess"][i, a] - fd_h).max() <= 1e-7
+        assert np.abs(r["hess"][i] - r["hess"][i].T).max() <= 1e-14
+
+
+def test_tanh_net_lipschitz_bound_dominates_sampled_derivatives():
+    for d, H, gain in ((2, 64, 1.0), (2, 64, 4.0), (3, 32, 2.0)):
+        net = wl.tanh_net(17 + H, d, H, gain=gain)
+        L, G = oracle.tnet_lipschitz(net)
+        x = wl.uniform_box(18, 3, 3000, np.full(d, -5.0), np.full(d, 15.0))
+        r = oracle.tnet_evaluate(net, x, hess=True)
+        hn = np.linalg.norm(r["hess"], ord=2, axis=(1, 2))
+        assert hn.max() <= L
+        sig = np.array([oracle.sigmoid3(v)[1] for v in r["s"]])
+        assert (np.linalg.norm(r["grad"], axis=1) / sig).max() <= G * (1 + 1e-12)
+        # the gradient bound is the product of the spectral norms (numpy's SVD)
+        W1, W2, w3 = (a.astype(np.float64) for a in (net.W1, net.W2, net.w3))
+        ref = np.linalg.norm(W1, 2) * np.linalg.norm(W2, 2) * np.linalg.norm(w3)
+        assert ref <= G <= ref * (1 + 1e-10)
+
+
+def test_tanh_net_morph_identity_one_step_and_contraction():
+    d, H = 2, 64
+    net = wl.tanh_net(19, d, H)
+    x0 = wl.uniform_box(20, 3, 50, np.zeros(2), np.full(2, 10.0))
+    zero = wl.TanhNet(net.W1, net.b1, net.W2, net.b2, np.zeros(H), net.b3)
+    assert np.array_equal(oracle.tnet_morph(zero, x0, 7, 0.1), x0.astype(np.float64))
+    L, _ = oracle.tnet_lipschitz(net)
+    eta = 0.5 / L
+    one = oracle.tnet_morph(net, x0, 1, eta)
+    h = 1e-6
+    for i in range(5):
+        g = np.zeros(d)
+        for a in range(d):
+            e = np.zeros(d)
+            e[a] = h
+            cp = oracle.tnet_evaluate(net, (x0[i] + e)[None])["c"][0]
+            cm = oracle.tnet_evaluate(net, (x0[i] - e)[None])["c"][0]
+            g[a] = (cp - cm) / (2 * h)
+        assert np.abs(one[i] - (x0[i] - eta * g)).max() <= 1e-9
+    # eta L < 1: two samples never swap order along the map (injective steps)
+    xa = oracle.tnet_morph(net, x0, 20, eta)
+    for i in range(10):
+        for j in range(i + 1, 10):
+            d0 = np.linalg.norm(x0[i] - x0[j])
+            assert np.linalg.norm(xa[i] - xa[j]) >= d0 * (1 - eta * L) ** 20 - 1e-12

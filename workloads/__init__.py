@@ -197,3 +197,28 @@ def random_field(seed: int, kind: int, d: int, M: int, lo=0.0, hi=10.0, gamma: f
     phase = f32(2.0 * np.pi * rng(seed, S_PHASE).random(M))
     w = f32(wscale * rng(seed, S_WEIGHTS).standard_normal(M) / np.sqrt(M))
     return Field(RFF, omega, w, phase=phase, bias=float(np.float32(bias)))
+
+
+class TanhNet:
+    """Weights of a tanh occupancy network (d -> H -> H -> 1), float32."""
+
+    def __init__(self, W1, b1, W2, b2, w3, b3):
+        self.W1, self.b1, self.W2, self.b2, self.w3 = (f32(a) for a in (W1, b1, W2, b2, w3))
+        self.b3 = float(np.float32(b3))
+        self.H, self.d = self.W1.shape
+
+
+def tanh_net(seed: int, d: int, H: int, lo=0.0, hi=10.0, gain: float = 1.0, out_scale: float = 2.0,
+             b3: float = -1.0) -> TanhNet:
+    """Random-initialised network whose first layer maps the box [lo, hi]^d to
+    about [-gain, gain] per unit (so the field varies across the box):
+    W1 ~ N(0, (2 gain / (hi - lo))^2 / d), b1 centres the box, W2 ~ N(0, 1/H),
+    w3 ~ N(0, out_scale^2 / H)."""
+    g = rng(seed, S_WEIGHTS)
+    span = float(hi) - float(lo)
+    W1 = g.standard_normal((H, d)) * (2.0 * gain / span) / np.sqrt(d)
+    b1 = -W1 @ np.full(d, 0.5 * (float(lo) + float(hi))) + 0.1 * g.standard_normal(H)
+    W2 = g.standard_normal((H, H)) / np.sqrt(H)
+    b2 = 0.1 * g.standard_normal(H)
+    w3 = g.standard_normal(H) * out_scale / np.sqrt(H)
+    return TanhNet(W1, b1, W2, b2, w3, b3)
