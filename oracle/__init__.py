@@ -21,6 +21,8 @@ below names the passage of the paper it follows:
 * ``fit`` / ``fit_objective`` -- Sec. 3.1: BCE minimised by gradient descent.
 * ``box_labels``     -- ground-truth occupancy labels of the dataset D.
 * ``mlp_*``          -- the surrogate network (no counterpart in the paper).
+* ``cspace_*``       -- Sec. 3.2, Eq. (3): the occupancy cost on a planar
+                        chain's body points pulled back to joint space.
 * ``tnet_*``         -- Sec. 3.1's own occupancy model: a fully connected
                         network with tanh hidden layers and a sigmoid output,
                         used as the cost of the morph of Eq. (1).
@@ -95,7 +97,13 @@ def lib():
             L.orc_tnet_eval.argtypes = tnet + [_dp, _L, _dp, _dp, _dp, _dp]
             L.orc_tnet_morph.argtypes = tnet + [_dp, _L, _I, _D, _dp]
             L.orc_tnet_lipschitz.argtypes = [_I, _I, _dp, _dp, _dp, _dp, _dp]
-            for name in ("orc_tnet_eval", "orc_tnet_morph", "orc_tnet_lipschitz","orc_eval", "orc_morph", "orc_morph_inverse", "orc_morph_vjp", "orc_logdet",
+            cs = _field_args() + [_I, _I, _dp, _dp]
+            L.orc_cspace_eval.argtypes = cs + [_dp, _L, _dp, _dp]
+            L.orc_cspace_points.argtypes = [_I, _I, _dp, _dp, _dp, _L, _dp]
+            L.orc_cspace_morph.argtypes = cs + [_dp, _L, _I, _D, _dp]
+            L.orc_cspace_lipschitz.argtypes = [_I, _I, _dp, _D, _D, _dp]
+            for name in ("orc_cspace_eval", "orc_cspace_points", "orc_cspace_morph", "orc_cspace_lipschitz",
+                         "orc_tnet_eval", "orc_tnet_morph", "orc_tnet_lipschitz","orc_eval", "orc_morph", "orc_morph_inverse", "orc_morph_vjp", "orc_logdet",
                          "orc_lipschitz_rbf", "orc_lipschitz_rff", "orc_fit", "orc_fit_objective",
                          "orc_box_labels", "orc_mlp_forward", "orc_mlp_loss_backward", "orc_mlp_encode"):
                 getattr(L, name).restype = _I
@@ -366,3 +374,48 @@ def tnet_lipschitz(net):
     _check(lib().orc_tnet_lipschitz(n.d, n.H, _ptr(n.W1), _ptr(n.W2), _ptr(n.w3), ctypes.byref(L),
                                     ctypes.byref(G)), "tnet_lipschitz")
     return float(L.value), float(G.value)
+
+
+# ---------------------------------------------------------------------------
+def _chain(chain):
+    return (int(chain.n), int(chain.p), _d(chain.base), _d(chain.lengths))
+
+
+def cspace_points(chain, Q):
+    """Body points psi_i(q) (N x n p x 2) of the planar chain."""
+    n, p, base, ln = _chain(chain)
+    Q = _d(Q).reshape(-1, n)
+    P = np.zeros((Q.shape[0], n * p, 2))
+    _check(lib().orc_cspace_points(n, p, _ptr(base), _ptr(ln), _ptr(Q), Q.shape[0], _ptr(P)), "cspace_points")
+    return P
+
+
+def cspace_evaluate(field, chain, Q):
+    """(f_c, grad_q f_c): the occupancy summed over the body points and its
+    joint-space gradient by Eq. (3)."""
+    f = _F(field)
+    n, p, base, ln = _chain(chain)
+    Q = _d(Q).reshape(-1, n)
+    fc, gq = np.zeros(Q.shape[0]), np.zeros_like(Q)
+    _check(lib().orc_cspace_eval(*f.args(), n, p, _ptr(base), _ptr(ln), _ptr(Q), Q.shape[0], _ptr(fc), _ptr(gq)),
+           "cspace_eval")
+    return fc, gq
+
+
+def cspace_morph(field, chain, Q0, T: int, eta: float):
+    """Eq. (1) in joint space with the gradient of Eq. (3)."""
+    f = _F(field)
+    n, p, base, ln = _chain(chain)
+    Q0 = _d(Q0).reshape(-1, n)
+    QT = np.zeros_like(Q0)
+    _check(lib().orc_cspace_morph(*f.args(), n, p, _ptr(base), _ptr(ln), _ptr(Q0), Q0.shape[0], int(T), float(eta),
+                                  _ptr(QT)), "cspace_morph")
+    return QT
+
+
+def cspace_lipschitz(chain, Lx: float, Gx: float) -> float:
+    """Certified bound on sup |Hess_q f_c| from task-space bounds Lx (Hessian) and Gx (gradient)."""
+    n, p, _, ln = _chain(chain)
+    out = ctypes.c_double(0)
+    _check(lib().orc_cspace_lipschitz(n, p, _ptr(ln), float(Lx), float(Gx), ctypes.byref(out)), "cspace_lipschitz")
+    return float(out.value)

@@ -37,6 +37,9 @@
  *       dataset D of Sec. 3.1, from axis-aligned boxes.
  *   MLP forward/backward               -- the surrogate network (no
  *       counterpart in the paper): dense layers with SiLU, MSE loss.
+ *   C-space pull-back                  -- Sec. 3.2, Eq. (3): a planar serial
+ *       chain's body points, the task-space gradient pulled back through the
+ *       kinematic Jacobians, the morph in joint space, a certified bound.
  *   tanh network cost                  -- Sec. 3.1's own occupancy model: a
  *       fully connected network, tanh between hidden layers, sigmoid output;
  *       its input gradient / Hessian, the morph of Eq. (1) through it, and a
@@ -1057,5 +1060,154 @@ int orc_tnet_lipschitz(int d, int H, const double* W1, const double* W2, const d
   const double hs = n1 * n1 * (kappa * colmax + kappa * n2 * n2 * w3max);
   *G = g;
   *L = 0.25 * hs + g * g / (6.0 * sqrt(3.0));
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Configuration space (Sec. 3.2, "Bringing Diffeomorphisms into        */
+/* Configuration Space", Eq. (3)).  A planar serial chain with n         */
+/* revolute joints: joint angles q, absolute link angles                */
+/* theta_k = q_1 + .. + q_k, joint positions o_1 = base,                */
+/* o_{k+1} = o_k + l_k (cos theta_k, sin theta_k).  Link k carries p     */
+/* body points psi = o_k + (r/p) l_k (cos theta_k, sin theta_k),         */
+/* r = 1..p, so b = n p.  The cost on the body points is                 */
+/* f_c(q) = sum_i c(psi_i(q)); its C-space gradient pulls the            */
+/* task-space gradients back through the kinematic Jacobians,            */
+/* grad_q f_c = sum_i J_i^T grad_x c(psi_i(q))  (Eq. (3) with the        */
+/* transpose the chain rule needs), where column j of J_i is             */
+/* z x (psi_i - o_j) for the joints j that move point i, else 0.         */
+/* ------------------------------------------------------------------ */
+#define CHAIN_MAX 16
+
+typedef struct {
+  int n, p;
+  double base[2];
+  const double* len;
+} chain_t;
+
+/* joint positions o[0..n] (o[n] the tip) and body points psi[0..n p) */
+static void chain_fk(const chain_t* ch, const double* q, double* o, double* psi) {
+  double th = 0.0;
+  o[0] = ch->base[0];
+  o[1] = ch->base[1];
+  for (int k = 0; k < ch->n; ++k) {
+    th += q[k];
+    const double cx = cos(th), sy = sin(th);
+    for (int r = 1; r <= ch->p; ++r) {
+      const double f = (double)r / ch->p;
+      psi[2 * (k * ch->p + r - 1)] = o[2 * k] + f * ch->len[k] * cx;
+      psi[2 * (k * ch->p + r - 1) + 1] = o[2 * k + 1] + f * ch->len[k] * sy;
+    }
+    o[2 * (k + 1)] = o[2 * k] + ch->len[k] * cx;
+    o[2 * (k + 1) + 1] = o[2 * k + 1] + ch->len[k] * sy;
+  }
+}
+
+/* f_c(q) and grad_q f_c by Eq. (3) */
+static double chain_cost(const field_t* f, const chain_t* ch, const double* q, double* gq) {
+  double o[2 * (CHAIN_MAX + 1)], psi[2 * CHAIN_MAX * 8];
+  chain_fk(ch, q, o, psi);
+  for (int j = 0; j < ch->n; ++j) gq[j] = 0.0;
+  double fc = 0.0;
+  for (int i = 0; i < ch->n * ch->p; ++i) {
+    const int link = i / ch->p;
+    double gx[2];
+    fc += cost_derivs(f, psi + 2 * i, gx, NULL, NULL, NULL);
+    for (int j = 0; j <= link; ++j) {
+      const double vx = psi[2 * i] - o[2 * j], vy = psi[2 * i + 1] - o[2 * j + 1];
+      gq[j] += -vy * gx[0] + vx * gx[1];     /* (z x v) . g */
+    }
+  }
+  return fc;
+}
+
+static int chain_ok(int n, int p) { return n >= 1 && n <= CHAIN_MAX && p >= 1 && p <= 8; }
+
+typedef struct { const field_t* f; const chain_t* ch; const double* Q; double *fc, *gq; } cs_eval_ctx;
+static void cs_eval_range(void* p, long lo, long hi) {
+  cs_eval_ctx* c = (cs_eval_ctx*)p;
+  const int n = c->ch->n;
+  for (long i = lo; i < hi; ++i) {
+    const double v = chain_cost(c->f, c->ch, c->Q + i * n, c->gq + i * n);
+    if (c->fc) c->fc[i] = v;
+  }
+}
+
+int orc_cspace_eval(int kind, int d, long M, const double* centres, const double* phase, double gamma,
+                    const double* w, double bias, int n, int p, const double* base, const double* len,
+                    const double* Q, long N, double* fc, double* gq) {
+  if (d != 2 || !chain_ok(n, p) || N < 0) return 1;
+  field_t f = make_field(kind, d, M, centres, phase, gamma, w, bias);
+  chain_t ch = {n, p, {base[0], base[1]}, len};
+  cs_eval_ctx c = {&f, &ch, Q, fc, gq};
+  parallel_range(N, cs_eval_range, &c);
+  return 0;
+}
+
+/* the body points themselves (for tests of the forward kinematics) */
+int orc_cspace_points(int n, int p, const double* base, const double* len, const double* Q, long N, double* P) {
+  if (!chain_ok(n, p) || N < 0) return 1;
+  chain_t ch = {n, p, {base[0], base[1]}, len};
+  double o[2 * (CHAIN_MAX + 1)];
+  for (long i = 0; i < N; ++i) chain_fk(&ch, Q + i * n, o, P + i * 2 * n * p);
+  return 0;
+}
+
+/* Eq. (1) in C-space: q_{t+1} = q_t - eta grad_q f_c(q_t) */
+typedef struct { const field_t* f; const chain_t* ch; const double* Q0; int T; double eta; double* QT; } cs_morph_ctx;
+static void cs_morph_range(void* p, long lo, long hi) {
+  cs_morph_ctx* c = (cs_morph_ctx*)p;
+  const int n = c->ch->n;
+  for (long i = lo; i < hi; ++i) {
+    double q[CHAIN_MAX], g[CHAIN_MAX];
+    for (int j = 0; j < n; ++j) q[j] = c->Q0[i * n + j];
+    for (int t = 0; t < c->T; ++t) {
+      chain_cost(c->f, c->ch, q, g);
+      for (int j = 0; j < n; ++j) q[j] -= c->eta * g[j];
+    }
+    for (int j = 0; j < n; ++j) c->QT[i * n + j] = q[j];
+  }
+}
+
+int orc_cspace_morph(int kind, int d, long M, const double* centres, const double* phase, double gamma,
+                     const double* w, double bias, int n, int p, const double* base, const double* len,
+                     const double* Q0, long N, int T, double eta, double* QT) {
+  if (d != 2 || !chain_ok(n, p) || N < 0 || T < 0) return 1;
+  field_t f = make_field(kind, d, M, centres, phase, gamma, w, bias);
+  chain_t ch = {n, p, {base[0], base[1]}, len};
+  cs_morph_ctx c = {&f, &ch, Q0, T, eta, QT};
+  parallel_range(N, cs_morph_range, &c);
+  return 0;
+}
+
+/* Certified bound on sup |Hess_q f_c|_2 from bounds Lx >= sup |Hess c|_2 and
+ * Gx >= sup |grad c| in the task space:
+ *   Hess_q f_c = sum_i [ J_i^T Hess c J_i + sum_a (dc/dx_a) Hess_q psi_{i,a} ],
+ * |J_i|_2^2 <= sum_{j <= k} |psi_i - o_j|^2 <= sum_{j <= k} R_{j,i}^2 and the
+ * entries of Hess_q psi_i (the second derivative about joints j, m is
+ * z x (z x (psi_i - o_max(j,m)))) have norm <= R_{max(j,m),i}, where R_{j,i}
+ * is the chain length from joint j to point i. */
+int orc_cspace_lipschitz(int n, int p, const double* len, double Lx, double Gx, double* Lq) {
+  if (!chain_ok(n, p)) return 1;
+  double total = 0.0;
+  for (int k = 0; k < n; ++k)
+    for (int r = 1; r <= p; ++r) {
+      double R[CHAIN_MAX];              /* R[j]: chain length from joint j to the point */
+      for (int j = 0; j <= k; ++j) {
+        double s = (double)r / p * len[k];
+        for (int m = j; m < k; ++m) s += len[m];
+        R[j] = s;
+      }
+      double jf = 0.0, hf = 0.0;
+      for (int j = 0; j <= k; ++j) {
+        jf += R[j] * R[j];
+        for (int m = 0; m <= k; ++m) {
+          const double rr = R[j > m ? j : m];
+          hf += rr * rr;
+        }
+      }
+      total += jf * Lx + Gx * sqrt(hf);
+    }
+  *Lq = total;
   return 0;
 }

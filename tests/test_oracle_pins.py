@@ -505,3 +505,76 @@ def test_tanh_net_morph_identity_one_step_and_contraction():
         for j in range(i + 1, 10):
             d0 = np.linalg.norm(x0[i] - x0[j])
             assert np.linalg.norm(xa[i] - xa[j]) >= d0 * (1 - eta * L) ** 20 - 1e-12
+
+
+# --------------------------------------------------------------------------
+# Configuration space: Eq. (3) on a planar serial chain
+def _cspace_case(seed=23, n=4, p=3, M=300):
+    f = wl.random_field(seed, wl.RBF, 2, M, lo=0, hi=10, gamma=2.0, wscale=1.0, bias=-0.5)
+    ch = wl.planar_arm(n, 4.0, (5.0, 5.0), p)
+    lo, hi = wl.joint_box(n)
+    Q = wl.uniform_box(seed, 3, 8, lo, hi).astype(np.float64)
+    return f, ch, Q
+
+
+def test_cspace_forward_kinematics_hand_cases():
+    ch = wl.Chain([1.0, 2.0], base=(1.0, -1.0), p=2)
+    P = oracle.cspace_points(ch, np.array([[0.0, 0.0], [np.pi / 2, -np.pi / 2], [np.pi, np.pi]]))
+    exp = np.array([
+        [[1.5, -1], [2, -1], [3, -1], [4, -1]],                 # straight along +x
+        [[1, -0.5], [1, 0], [2, 0], [3, 0]],                    # up, then right
+        [[0.5, -1], [0, -1], [1, -1], [2, -1]],                 # back along -x, then folded forward
+    ])
+    assert np.abs(P - exp).max() <= 1e-14
+
+
+def test_cspace_gradient_matches_central_differences():
+    f, ch, Q = _cspace_case()
+    fc, gq = oracle.cspace_evaluate(f, ch, Q)
+    h = 1e-6
+    for i in range(Q.shape[0]):
+        for j in range(ch.n):
+            e = np.zeros(ch.n)
+            e[j] = h
+            fp, _ = oracle.cspace_evaluate(f, ch, (Q[i] + e)[None])
+            fm, _ = oracle.cspace_evaluate(f, ch, (Q[i] - e)[None])
+            assert abs(gq[i, j] - (fp[0] - fm[0]) / (2 * h)) <= 1e-7 * (1 + abs(gq[i, j]))
+    # f_c is the occupancy summed over the body points
+    P = oracle.cspace_points(ch, Q)
+    c = oracle.evaluate(f, P.reshape(-1, 2))["c"].reshape(Q.shape[0], -1).sum(axis=1)
+    assert np.abs(fc - c).max() <= 1e-12
+
+
+def test_cspace_lipschitz_bound_dominates_sampled_hessian():
+    f, ch, _ = _cspace_case(seed=24, n=5, p=2)
+    Lx, Gx = oracle.lipschitz(f, np.full(2, -1.0), np.full(2, 11.0), cells=32)
+    Lq = oracle.cspace_lipschitz(ch, Lx, Gx)
+    lo, hi = wl.joint_box(ch.n)
+    Q = wl.uniform_box(25, 3, 60, lo, hi).astype(np.float64)
+    h = 1e-5
+    worst = 0.0
+    for q in Q:
+        Hs = np.zeros((ch.n, ch.n))
+        for j in range(ch.n):
+            e = np.zeros(ch.n)
+            e[j] = h
+            _, gp = oracle.cspace_evaluate(f, ch, (q + e)[None])
+            _, gm = oracle.cspace_evaluate(f, ch, (q - e)[None])
+            Hs[j] = (gp[0] - gm[0]) / (2 * h)
+        worst = max(worst, np.linalg.norm(0.5 * (Hs + Hs.T), 2))
+    assert worst <= Lq
+
+
+def test_cspace_morph_identity_and_one_step():
+    f, ch, Q = _cspace_case(seed=26)
+    zero = wl.Field(f.kind, f.centres, np.zeros_like(f.w), gamma=f.gamma, bias=f.bias)
+    assert np.array_equal(oracle.cspace_morph(zero, ch, Q, 5, 0.1), Q)
+    eta = 0.01
+    q1 = oracle.cspace_morph(f, ch, Q, 1, eta)
+    _, g = oracle.cspace_evaluate(f, ch, Q)
+    assert np.abs(q1 - (Q - eta * g)).max() <= 1e-15
+    q3 = oracle.cspace_morph(f, ch, Q, 3, eta)
+    q = Q.copy()
+    for _ in range(3):
+        q = q - eta * oracle.cspace_evaluate(f, ch, q)[1]
+    assert np.abs(q3 - q).max() <= 1e-14

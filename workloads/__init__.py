@@ -222,3 +222,24 @@ def tanh_net(seed: int, d: int, H: int, lo=0.0, hi=10.0, gain: float = 1.0, out_
     b2 = 0.1 * g.standard_normal(H)
     w3 = g.standard_normal(H) * out_scale / np.sqrt(H)
     return TanhNet(W1, b1, W2, b2, w3, b3)
+
+
+class Chain:
+    """A planar serial chain: n revolute joints at base, link lengths, p body points per link."""
+
+    def __init__(self, lengths, base=(0.0, 0.0), p: int = 4):
+        self.lengths = f32(np.asarray(lengths))
+        self.base = f32(np.asarray(base))
+        self.n = int(self.lengths.shape[0])
+        self.p = int(p)
+
+
+def planar_arm(n: int = 7, reach: float = 4.5, base=(5.0, 5.0), p: int = 4) -> Chain:
+    """An n-link planar arm of total reach `reach` (equal links) based at `base`
+    (the centre of the 2-D workspace [0, 10]^2), p body points per link."""
+    return Chain(np.full(n, reach / n), base, p)
+
+
+def joint_box(n: int):
+    """The joint limits [-pi, pi]^n."""
+    return np.full(n, -np.pi), np.full(n, np.pi)
