@@ -21,6 +21,8 @@ below names the passage of the paper it follows:
 * ``fit`` / ``fit_objective`` -- Sec. 3.1: BCE minimised by gradient descent.
 * ``box_labels``     -- ground-truth occupancy labels of the dataset D.
 * ``mlp_*``          -- the surrogate network (no counterpart in the paper).
+* ``philox4x32`` / ``uniform_batch`` -- the counter-based generator of the
+                        base samples a device-side sampler draws.
 * ``cspace_*``       -- Sec. 3.2, Eq. (3): the occupancy cost on a planar
                         chain's body points pulled back to joint space.
 * ``tnet_*``         -- Sec. 3.1's own occupancy model: a fully connected
@@ -102,7 +104,10 @@ def lib():
             L.orc_cspace_points.argtypes = [_I, _I, _dp, _dp, _dp, _L, _dp]
             L.orc_cspace_morph.argtypes = cs + [_dp, _L, _I, _D, _dp]
             L.orc_cspace_lipschitz.argtypes = [_I, _I, _dp, _D, _D, _dp]
-            for name in ("orc_cspace_eval", "orc_cspace_points", "orc_cspace_morph", "orc_cspace_lipschitz",
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            L.orc_philox4x32.argtypes = [u32p, u32p, u32p]
+            L.orc_uniform_batch.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _L, _I, _fp, _fp, _fp]
+            for name in ("orc_philox4x32", "orc_uniform_batch", "orc_cspace_eval", "orc_cspace_points", "orc_cspace_morph", "orc_cspace_lipschitz",
                          "orc_tnet_eval", "orc_tnet_morph", "orc_tnet_lipschitz","orc_eval", "orc_morph", "orc_morph_inverse", "orc_morph_vjp", "orc_logdet",
                          "orc_lipschitz_rbf", "orc_lipschitz_rff", "orc_fit", "orc_fit_objective",
                          "orc_box_labels", "orc_mlp_forward", "orc_mlp_loss_backward", "orc_mlp_encode"):
@@ -419,3 +424,24 @@ def cspace_lipschitz(chain, Lx: float, Gx: float) -> float:
     out = ctypes.c_double(0)
     _check(lib().orc_cspace_lipschitz(n, p, _ptr(ln), float(Lx), float(Gx), ctypes.byref(out)), "cspace_lipschitz")
     return float(out.value)
+
+
+# ---------------------------------------------------------------------------
+def philox4x32(counter, key):
+    """Philox4x32-10 of one 4-word counter under a 2-word key (uint32 words)."""
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib().orc_philox4x32(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p), out.ctypes.data_as(u32p))
+    return out
+
+
+def uniform_batch(seed: int, batch: int, n: int, lo, hi):
+    """Batch `batch` of n base samples uniform on [lo, hi] (float32) from the counter-based generator."""
+    lo = np.ascontiguousarray(np.asarray(lo, dtype=np.float32))
+    hi = np.ascontiguousarray(np.asarray(hi, dtype=np.float32))
+    d = lo.shape[0]
+    x = np.zeros((n, d), dtype=np.float32)
+    _check(lib().orc_uniform_batch(int(seed), int(batch), int(n), d, _ptr(lo), _ptr(hi), _ptr(x)), "uniform_batch")
+    return x

@@ -40,6 +40,9 @@
  *   C-space pull-back                  -- Sec. 3.2, Eq. (3): a planar serial
  *       chain's body points, the task-space gradient pulled back through the
  *       kinematic Jacobians, the morph in joint space, a certified bound.
+ *   Philox4x32-10, uniform batch       -- the base samples a device-side
+ *       sampler draws (Sec. 3.3's prior), from the generator's published
+ *       definition, so the oracle can regenerate them.
  *   tanh network cost                  -- Sec. 3.1's own occupancy model: a
  *       fully connected network, tanh between hidden layers, sigmoid output;
  *       its input gradient / Hessian, the morph of Eq. (1) through it, and a
@@ -1209,5 +1212,49 @@ int orc_cspace_lipschitz(int n, int p, const double* len, double Lx, double Gx, 
       total += jf * Lx + Gx * sqrt(hf);
     }
   *Lq = total;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Counter-based generator for base samples drawn on the device          */
+/* (the planner's prior, Sec. 3.3): Philox4x32 with 10 rounds (Salmon,   */
+/* Moraes, Dror, Shaw, SC'11), written from its published definition.    */
+/* Sample i, coordinate j of batch b is word (i d + j) mod 4 of block    */
+/* (i d + j) / 4 with counter (block, 0-hi, b, b-hi) and key (seed lo,    */
+/* seed hi); its top 24 bits u give the coordinate fmaf(u 2^-24,         */
+/* hi - lo, lo) in float32.                                              */
+/* ------------------------------------------------------------------ */
+static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+int orc_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  philox4x32_10(ctr, key, out);
+  return 0;
+}
+
+int orc_uniform_batch(uint64_t seed, uint64_t batch, long n, int d, const float* lo, const float* hi, float* x) {
+  if (d < 1 || d > MAXD || n < 0) return 1;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (long e = 0; e < n * d; ++e) {
+    const uint64_t blk = (uint64_t)e / 4;
+    const uint32_t ctr[4] = {(uint32_t)blk, (uint32_t)(blk >> 32), (uint32_t)batch, (uint32_t)(batch >> 32)};
+    uint32_t o[4];
+    philox4x32_10(ctr, key, o);
+    const int j = (int)(e % d);
+    const float u = (float)(o[e % 4] >> 8) * (1.0f / 16777216.0f);
+    x[e] = fmaf(u, hi[j] - lo[j], lo[j]);
+  }
   return 0;
 }

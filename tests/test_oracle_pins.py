@@ -578,3 +578,36 @@ def test_cspace_morph_identity_and_one_step():
     for _ in range(3):
         q = q - eta * oracle.cspace_evaluate(f, ch, q)[1]
     assert np.abs(q3 - q).max() <= 1e-14
+
+
+# --------------------------------------------------------------------------
+# The counter-based generator of device-drawn base samples
+def test_philox4x32_known_answers():
+    """Known-answer vectors published with the Philox generator (Random123)."""
+    cases = [
+        ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+        ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+        ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+         (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+    ]
+    for ctr, key, want in cases:
+        assert [int(v) for v in oracle.philox4x32(ctr, key)] == list(want)
+
+
+def test_uniform_batch_layout_and_range():
+    lo, hi = np.array([-1.0, 2.0, 0.0], np.float32), np.array([1.0, 6.0, 10.0], np.float32)
+    x = oracle.uniform_batch(1234, 7, 1000, lo, hi)
+    assert x.shape == (1000, 3) and (x >= lo).all() and (x < hi).all()
+    # element e = i d + j is word e mod 4 of block e / 4 with counter (block, 0, batch, 0)
+    for e in (0, 1, 5, 2999):
+        i, j = divmod(e, 3)
+        w = oracle.philox4x32((e // 4, 0, 7, 0), (1234, 0))[e % 4]
+        u = np.float32(int(w) >> 8) * np.float32(2.0 ** -24)
+        assert x[i, j] == np.float32(np.float32(u) * (hi[j] - lo[j]) + lo[j]) or \
+            abs(float(x[i, j]) - (float(u) * float(hi[j] - lo[j]) + float(lo[j]))) <= 1e-6
+    # roughly uniform per coordinate
+    m = (x - lo) / (hi - lo)
+    assert np.abs(m.mean(axis=0) - 0.5).max() < 0.03
+    # different batches and seeds differ
+    assert not np.array_equal(x, oracle.uniform_batch(1234, 8, 1000, lo, hi))
+    assert not np.array_equal(x, oracle.uniform_batch(1235, 7, 1000, lo, hi))
