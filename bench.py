@@ -287,6 +287,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
         line["extras"] = {
             "culled_morph": culled,
+            "tanh_net_cost": extra_tanh_net(pdmp, torch, n_sms, pk),
             "batched_256_envs": extra_batched(pdmp, torch, n_sms, pk),
             "rff7d_differentiation": extra_rff(pdmp, torch, n_sms, pk),
             "surrogate_3d": extra_surrogate(pdmp, torch, args),
@@ -360,6 +361,28 @@ def extra_culled(pdmp, torch, fld, x0, xT_dense, eta, eps=1e-6):
             "speedup_vs_dense": None, "evaluated_fraction": int(work.item()) / dense,
             "eps": eps, "r_cut": r, "sum_abs_w": W, "max_abs_dev_vs_dense": dev,
             "note": "features farther than r_cut from a tile dropped; s and |grad s| change by at most eps"}
+
+
+def extra_tanh_net(pdmp, torch, n_sms, pk, d=2, H=64, n=1 << 20, t_steps=50):
+    """The paper's own occupancy model (tanh network, Sec. 3.1) as the morph
+    cost: sample-steps per second and the fraction of the FP32 roofline for
+    the network's multiply-adds per sample-step (forward and input gradient)."""
+    net = wl.tanh_net(7, d, H)
+    dn = pdmp.DeviceTanhNet.from_host(net)
+    L, _ = pdmp.tanh_net_lipschitz(dn)
+    eta = float(np.float32(0.5 / L))
+    x0 = torch.from_numpy(wl.uniform_box(7, wl.S_SAMPLES, n, np.zeros(d), np.full(d, 10.0))).cuda()
+    out = torch.empty_like(x0)
+    run = lambda: pdmp.tanh_net_morph(dn, x0, t_steps, eta, out=out)
+    for _ in range(3):
+        run()
+    t = _time(torch, run, reps=5)
+    macs = 2 * H * H + 2 * d * H + 2 * H          # W2 h1 and W2^T v2; W1 x and W1^T g1; w3 h2 and w3 (.) (1 - h2^2)
+    rate = n * t_steps / t
+    peak = n_sms * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 * FP32_LANES_PER_SM / macs
+    return {"value": rate, "unit": "sample-steps/s", "ms": 1e3 * t, "N": n, "T": t_steps, "d": d, "H": H,
+            "macs_per_sample_step": macs, "roofline_frac": rate / peak, "L": L, "eta": eta,
+            "note": "FP32 multiply-adds at 128 lanes per SM per clock; tanh not counted"}
 
 
 def extra_rff(pdmp, torch, n_sms, pk):

@@ -258,6 +258,125 @@ pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const
                                  void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* The diffeomorphic sampler (Sec. 3.3).                                    */
+/* ---------------------------------------------------------------------- */
+/* A bounded concurrent bucket of d-dimensional float samples on the host
+ * (FIFO).  push copies up to n samples in, waiting up to timeout_ms for room
+ * (*pushed receives how many went in; fewer after a timeout or close); pop
+ * copies out up to n of the oldest without waiting (*popped: how many).
+ * Thread-safe; close wakes waiting pushers and makes later pushes push
+ * nothing.  Host memory only: usable without a GPU. */
+typedef struct pdmp_queue pdmp_queue;
+pdmp_status pdmp_queue_create(int32_t d, int64_t capacity, pdmp_queue** out);
+pdmp_status pdmp_queue_push(pdmp_queue* q, const float* x, int64_t n, int32_t timeout_ms, int64_t* pushed);
+pdmp_status pdmp_queue_pop(pdmp_queue* q, float* out, int64_t n, int64_t* popped);
+pdmp_status pdmp_queue_size(pdmp_queue* q, int64_t* n);
+pdmp_status pdmp_queue_close(pdmp_queue* q);
+pdmp_status pdmp_queue_destroy(pdmp_queue* q);
+
+/* The sampler keeps such a bucket filled from a background thread: batch
+ * base samples uniform on [lo, hi] drawn on the current device by a
+ * counter-based generator (Philox4x32-10; coordinate j of sample i of batch
+ * b is word (i d + j) mod 4 of block (i d + j) / 4 under counter (block, b)
+ * and key seed, the coordinate fmaf(top 24 bits * 2^-24, hi - lo, lo)),
+ * morphed by pdmp_morph (T, eta) and copied to pinned host memory.  Batches
+ * enter the bucket in order, so the k-th morphed sample drawn is sample
+ * k mod batch of batch k / batch.  draw never waits for the GPU: it takes up
+ * to n morphed samples from the bucket (*n_morphed receives how many; they
+ * come first in out) and fills the rest from the prior (the same generator,
+ * another key, on the host).  The field's device arrays must outlive the
+ * sampler.  A producer failure stops production and is reported by stats;
+ * draws then come from the prior. */
+typedef struct {
+  int32_t d;
+  float lo[8];
+  float hi[8];
+  int32_t batch;       /* samples per device batch */
+  int64_t capacity;    /* bucket size in samples (>= batch) */
+  int32_t T;
+  float eta;
+  uint64_t seed;
+} pdmp_sampler_config;
+
+typedef struct {
+  int64_t produced;      /* morphed samples pushed into the bucket */
+  int64_t batches;
+  int64_t drawn_morphed;
+  int64_t drawn_prior;
+  int64_t queued;        /* samples in the bucket now */
+  int32_t error;         /* 0, or the producer's failing status */
+} pdmp_sampler_stats_t;
+
+typedef struct pdmp_sampler pdmp_sampler;
+pdmp_status pdmp_sampler_create(const pdmp_field* f, const pdmp_sampler_config* cfg, pdmp_sampler** out);
+pdmp_status pdmp_sampler_draw(pdmp_sampler* s, float* out, int64_t n, int64_t* n_morphed);
+pdmp_status pdmp_sampler_stats(pdmp_sampler* s, pdmp_sampler_stats_t* stats);
+pdmp_status pdmp_sampler_destroy(pdmp_sampler* s);
+
+/* ---------------------------------------------------------------------- */
+/* Configuration space (Sec. 3.2, Eq. (3)).                                 */
+/* ---------------------------------------------------------------------- */
+/* A planar serial chain: n revolute joints (1..16) at base, link lengths
+ * (host values, the first n used), p body points per link (1..8) at
+ * fractions r/p of each link, r = 1..p.  Joint angles q (N x n, device,
+ * row-major); absolute link angles are the prefix sums of q. */
+typedef struct {
+  int32_t n;
+  int32_t p;
+  float base[2];
+  float lengths[16];
+} pdmp_chain;
+
+/* The T Euler steps of Eq. (1) in joint space with the cost
+ * f_c(q) = sum_i c(psi_i(q)) over the b = n p body points and its gradient
+ * by Eq. (3): grad_q f_c = sum_i J_i^T grad_x c(psi_i(q)).  The field is the
+ * 2-D workspace occupancy (RBF or RFF, d = 2).  q0 may alias qT.  ws:
+ * pdmp_cspace_workspace bytes (body points, their gradients and the fast
+ * kernel's workspace for N b points), 16-byte aligned. */
+size_t pdmp_cspace_workspace(const pdmp_field* f, const pdmp_chain* chain, int64_t N);
+pdmp_status pdmp_cspace_morph(const pdmp_field* f, const pdmp_chain* chain, const float* q0, int64_t N, int32_t T,
+                              float eta, float* qT, void* ws, size_t ws_bytes, void* stream);
+/* Certified bound *Lq >= sup |Hess_q f_c|_2 from task-space bounds
+ * Lx >= sup |Hess c|_2 and Gx >= sup |grad c| (host arithmetic):
+ * sum over body points of |J_i|^2 Lx + Gx |Hess_q psi_i|, both from the chain
+ * lengths between the joints and the point. */
+pdmp_status pdmp_cspace_lipschitz(const pdmp_chain* chain, double Lx, double Gx, double* Lq);
+
+/* ---------------------------------------------------------------------- */
+/* The paper's own occupancy model as the cost (Sec. 3.1).                  */
+/* ---------------------------------------------------------------------- */
+/* A fully connected network with tanh between its hidden layers and a
+ * sigmoid output:  s(x) = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3,
+ * c = sigma(s).  Device float32 arrays, row-major with rows = output units:
+ * W1 H x d, b1 H, W2 H x H, b2 H, w3 H.  Supported: d in {2, 3},
+ * H in {32, 64} (else PDMP_ERR_UNSUPPORTED).  lipschitz as in pdmp_field. */
+typedef struct {
+  int32_t d;
+  int32_t H;
+  const float* W1;
+  const float* b1;
+  const float* W2;
+  const float* b2;
+  const float* w3;
+  float b3;
+  double lipschitz;
+} pdmp_tanh_net;
+
+/* The T Euler steps of Eq. (1) with c the network's occupancy; x0, xT, ckpt,
+ * k as in pdmp_morph (x0 may alias xT). */
+pdmp_status pdmp_tanh_net_morph(const pdmp_tanh_net* net, const float* x0, int64_t N, int32_t T, float eta,
+                                float* xT, float* ckpt, int32_t k, void* stream);
+/* c, s (N each) and grad c (N x d) at N points; any output may be NULL. */
+pdmp_status pdmp_tanh_net_query(const pdmp_tanh_net* net, const float* x, int64_t N, float* c, float* s,
+                                float* grad, void* stream);
+/* Certified bounds over all of R^d, in FP64 on the host (the weights are
+ * copied from the device; synchronises the stream): *G >= sup |grad s| and
+ * *L >= sup |Hess c|_2, from the spectral norms of W1 and W2 and the maxima
+ * |tanh'| <= 1, |tanh''| <= 4 / (3 sqrt 3), sigma' <= 1/4,
+ * |sigma''| <= 1 / (6 sqrt 3). */
+pdmp_status pdmp_tanh_net_lipschitz(const pdmp_tanh_net* net, double* L, double* G, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Spatially culled morph (RBF, d = 2 or 3).                                */
 /* ---------------------------------------------------------------------- */
 /* The T Euler steps of pdmp_morph, but every sample tile sums, at every

@@ -22,7 +22,9 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "PdmpError", "DeviceField", "lib", "morph", "morph_trace", "morph_workspace", "morph_inverse", "log_density", "morph_culled", "morph_culled_workspace", "cull_radius", "morph_vjp", "morph_vjp_workspace", "logdet",
+    "PdmpError", "DeviceField", "lib", "morph", "morph_trace", "morph_workspace", "morph_inverse", "log_density", "morph_culled", "morph_culled_workspace", "cull_radius", "DeviceTanhNet", "tanh_net_morph", "cspace_morph", "cspace_workspace",
+    "cspace_lipschitz", "chain_struct", "Queue", "Sampler",
+    "tanh_net_query", "tanh_net_lipschitz", "morph_vjp", "morph_vjp_workspace", "logdet",
     "occupancy_query", "box_labels", "lipschitz_bound", "fit_occupancy", "fit_workspace", "stream_status", "Batch",
     "Surrogate", "displacement_rms", "morph_autograd",
     "RBF", "RFF",
@@ -51,6 +53,28 @@ class _Field(ctypes.Structure):
 
 _lib = None
 _lock = threading.Lock()
+
+
+class _SamplerConfig(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("lo", ctypes.c_float * 8), ("hi", ctypes.c_float * 8),
+                ("batch", ctypes.c_int32), ("capacity", ctypes.c_int64), ("T", ctypes.c_int32),
+                ("eta", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class _SamplerStats(ctypes.Structure):
+    _fields_ = [("produced", ctypes.c_int64), ("batches", ctypes.c_int64), ("drawn_morphed", ctypes.c_int64),
+                ("drawn_prior", ctypes.c_int64), ("queued", ctypes.c_int64), ("error", ctypes.c_int32)]
+
+
+class _Chain(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("p", ctypes.c_int32), ("base", ctypes.c_float * 2),
+                ("lengths", ctypes.c_float * 16)]
+
+
+class _TanhNet(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("H", ctypes.c_int32), ("W1", ctypes.c_void_p), ("b1", ctypes.c_void_p),
+                ("W2", ctypes.c_void_p), ("b2", ctypes.c_void_p), ("w3", ctypes.c_void_p), ("b3", ctypes.c_float),
+                ("lipschitz", ctypes.c_double)]
 _P = ctypes.c_void_p
 _i32, _i64, _f32, _f64, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_size_t
 _FP = ctypes.POINTER(_Field)
@@ -74,6 +98,21 @@ def lib():
                 "pdmp_morph_trace": [_FP, _P, _i64, _i32, _f32, _P, _P, _P, _sz, _P],
                 "pdmp_morph_vjp": [_FP, _P, _i64, _i32, _f32, _i32, _P, _P, _P, _P, _P, _P, _sz, _P],
                 "pdmp_logdet": [_FP, _P, _i64, _i32, _f32, _P, _P, _P],
+                "pdmp_queue_create": [_i32, _i64, ctypes.POINTER(_P)],
+                "pdmp_queue_push": [_P, _P, _i64, _i32, ctypes.POINTER(_i64)],
+                "pdmp_queue_pop": [_P, _P, _i64, ctypes.POINTER(_i64)],
+                "pdmp_queue_size": [_P, ctypes.POINTER(_i64)],
+                "pdmp_queue_close": [_P],
+                "pdmp_queue_destroy": [_P],
+                "pdmp_sampler_create": [_FP, ctypes.POINTER(_SamplerConfig), ctypes.POINTER(_P)],
+                "pdmp_sampler_draw": [_P, _P, _i64, ctypes.POINTER(_i64)],
+                "pdmp_sampler_stats": [_P, ctypes.POINTER(_SamplerStats)],
+                "pdmp_sampler_destroy": [_P],
+                "pdmp_cspace_morph": [_FP, ctypes.POINTER(_Chain), _P, _i64, _i32, _f32, _P, _P, _sz, _P],
+                "pdmp_cspace_lipschitz": [ctypes.POINTER(_Chain), _f64, _f64, ctypes.POINTER(_f64)],
+                "pdmp_tanh_net_morph": [ctypes.POINTER(_TanhNet), _P, _i64, _i32, _f32, _P, _P, _i32, _P],
+                "pdmp_tanh_net_query": [ctypes.POINTER(_TanhNet), _P, _i64, _P, _P, _P, _P],
+                "pdmp_tanh_net_lipschitz": [ctypes.POINTER(_TanhNet), ctypes.POINTER(_f64), ctypes.POINTER(_f64), _P],
                 "pdmp_morph_culled": [_FP, _P, _i64, _i32, _f32, _f32, _P, _P, _i32, _P, _sz, _P, _P],
                 "pdmp_cull_radius": [_FP, _f32, ctypes.POINTER(_f32), ctypes.POINTER(_f64), _P],
                 "pdmp_morph_inverse": [_FP, _P, _i64, _i32, _f32, _f32, _i32, _P, _P, _P],
@@ -91,6 +130,8 @@ def lib():
                 fn.restype = _i32
             L.pdmp_morph_workspace.argtypes = [_FP, _i64]
             L.pdmp_morph_workspace.restype = _sz
+            L.pdmp_cspace_workspace.argtypes = [_FP, ctypes.POINTER(_Chain), _i64]
+            L.pdmp_cspace_workspace.restype = _sz
             L.pdmp_morph_culled_workspace.argtypes = [_FP, _i64]
             L.pdmp_morph_culled_workspace.restype = _sz
             L.pdmp_morph_vjp_workspace.argtypes = [_FP, _i64, _i32, _i32, _i32]
@@ -254,6 +295,182 @@ def morph_noalloc(field: DeviceField, x0: torch.Tensor, T: int, eta: float,
             _ptr(out, shape=(N, d), name="out"), _stream())
     _check(st, "pdmp_morph_noalloc")
     return out
+
+
+class Queue:
+    """The bounded concurrent FIFO bucket of host samples (pdmp_queue_*); host only."""
+
+    def __init__(self, d: int, capacity: int):
+        h = ctypes.c_void_p()
+        _check(lib().pdmp_queue_create(int(d), int(capacity), ctypes.byref(h)), "pdmp_queue_create")
+        self._h, self.d = h, int(d)
+
+    def push(self, x, timeout_ms: int = 0) -> int:
+        import numpy as np
+        a = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.d)
+        n = ctypes.c_int64(0)
+        _check(lib().pdmp_queue_push(self._h, a.ctypes.data_as(ctypes.c_void_p), a.shape[0], int(timeout_ms),
+                                     ctypes.byref(n)), "pdmp_queue_push")
+        return int(n.value)
+
+    def pop(self, n: int):
+        import numpy as np
+        out = np.empty((int(n), self.d), dtype=np.float32)
+        got = ctypes.c_int64(0)
+        _check(lib().pdmp_queue_pop(self._h, out.ctypes.data_as(ctypes.c_void_p), int(n), ctypes.byref(got)),
+               "pdmp_queue_pop")
+        return out[:got.value]
+
+    def size(self) -> int:
+        n = ctypes.c_int64(0)
+        _check(lib().pdmp_queue_size(self._h, ctypes.byref(n)), "pdmp_queue_size")
+        return int(n.value)
+
+    def close(self):
+        _check(lib().pdmp_queue_close(self._h), "pdmp_queue_close")
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pdmp_queue_destroy(self._h)
+            self._h = None
+
+
+class Sampler:
+    """The diffeomorphic sampler of Sec. 3.3: a background thread fills a bucket
+    with morphed samples; draw() never waits for the GPU and falls back to the
+    prior (uniform on [lo, hi]) when the bucket is empty."""
+
+    def __init__(self, field: DeviceField, lo, hi, T: int, eta: float, batch: int = 65536,
+                 capacity: int = 1 << 20, seed: int = 0):
+        c = _SamplerConfig()
+        c.d = field.d
+        for j in range(field.d):
+            c.lo[j], c.hi[j] = float(lo[j]), float(hi[j])
+        c.batch, c.capacity, c.T, c.eta, c.seed = int(batch), int(capacity), int(T), float(eta), int(seed)
+        self._field = field                      # keeps the device arrays alive
+        self._fs = field.struct()
+        h = ctypes.c_void_p()
+        _check(lib().pdmp_sampler_create(ctypes.byref(self._fs), ctypes.byref(c), ctypes.byref(h)),
+               "pdmp_sampler_create")
+        self._h, self.d = h, field.d
+
+    def draw(self, n: int):
+        """(samples n x d float32 on the host, how many of them, first, are morphed)."""
+        import numpy as np
+        out = np.empty((int(n), self.d), dtype=np.float32)
+        m = ctypes.c_int64(0)
+        _check(lib().pdmp_sampler_draw(self._h, out.ctypes.data_as(ctypes.c_void_p), int(n), ctypes.byref(m)),
+               "pdmp_sampler_draw")
+        return out, int(m.value)
+
+    def stats(self) -> dict:
+        st = _SamplerStats()
+        _check(lib().pdmp_sampler_stats(self._h, ctypes.byref(st)), "pdmp_sampler_stats")
+        return {k: int(getattr(st, k)) for k, _ in _SamplerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().pdmp_sampler_destroy(self._h), "pdmp_sampler_destroy")
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def chain_struct(chain) -> _Chain:
+    """A planar serial chain (any object with lengths, base, p) as the C struct."""
+    c = _Chain()
+    ln = [float(v) for v in chain.lengths]
+    if not 1 <= len(ln) <= 16:
+        raise ValueError("a chain has 1 to 16 links")
+    c.n, c.p = len(ln), int(chain.p)
+    c.base[0], c.base[1] = (float(v) for v in chain.base)
+    for i, v in enumerate(ln):
+        c.lengths[i] = v
+    return c
+
+
+def cspace_workspace(field: DeviceField, chain, N: int) -> int:
+    f, c = field.struct(), chain_struct(chain)
+    return int(lib().pdmp_cspace_workspace(ctypes.byref(f), ctypes.byref(c), int(N)))
+
+
+def cspace_morph(field: DeviceField, chain, q0: torch.Tensor, T: int, eta: float, out: torch.Tensor | None = None,
+                 ws: torch.Tensor | None = None):
+    """Eq. (1) in joint space with the pulled-back gradient of Eq. (3)."""
+    f, c = field.struct(), chain_struct(chain)
+    N = q0.shape[0]
+    qT = torch.empty_like(q0) if out is None else out
+    if ws is None:
+        ws = torch.empty(max(cspace_workspace(field, chain, N), 16), dtype=torch.uint8, device=q0.device)
+    _check(lib().pdmp_cspace_morph(ctypes.byref(f), ctypes.byref(c), _ptr(q0, shape=(N, c.n), name="q0"), N, int(T),
+                                   float(eta), _ptr(qT), _ptr(ws, dtype=torch.uint8), ws.numel(), _stream()),
+           "pdmp_cspace_morph")
+    return qT
+
+
+def cspace_lipschitz(chain, Lx: float, Gx: float) -> float:
+    """Certified bound on the joint-space Hessian of the summed body-point occupancy."""
+    c = chain_struct(chain)
+    out = ctypes.c_double(0)
+    _check(lib().pdmp_cspace_lipschitz(ctypes.byref(c), float(Lx), float(Gx), ctypes.byref(out)),
+           "pdmp_cspace_lipschitz")
+    return float(out.value)
+
+
+class DeviceTanhNet:
+    """The tanh occupancy network of Sec. 3.1 (d -> H -> H -> 1) resident on the GPU (float32)."""
+
+    def __init__(self, W1, b1, W2, b2, w3, b3: float, lipschitz: float = 0.0, device="cuda"):
+        t = lambda a: torch.as_tensor(a, dtype=torch.float32).to(device).contiguous()
+        self.W1, self.b1, self.W2, self.b2, self.w3 = t(W1), t(b1), t(W2), t(b2), t(w3)
+        self.b3 = float(b3)
+        self.lipschitz = float(lipschitz)
+        self.H, self.d = self.W1.shape
+
+    @classmethod
+    def from_host(cls, net, lipschitz: float = 0.0, device="cuda"):
+        """From any object with W1, b1, W2, b2, w3, b3 (e.g. workloads.TanhNet)."""
+        return cls(net.W1, net.b1, net.W2, net.b2, net.w3, net.b3, lipschitz, device)
+
+    def struct(self) -> _TanhNet:
+        s = _TanhNet()
+        s.d, s.H = self.d, self.H
+        s.W1, s.b1, s.W2, s.b2, s.w3 = (t.data_ptr() for t in (self.W1, self.b1, self.W2, self.b2, self.w3))
+        s.b3, s.lipschitz = self.b3, self.lipschitz
+        return s
+
+
+def tanh_net_morph(net: DeviceTanhNet, x0: torch.Tensor, T: int, eta: float, out: torch.Tensor | None = None,
+                   ckpt: torch.Tensor | None = None, k: int = 0):
+    """Eq. (1) by Euler's method with the tanh network's occupancy as the cost."""
+    N, d = x0.shape[0], net.d
+    xT = torch.empty_like(x0) if out is None else out
+    s = net.struct()
+    _check(lib().pdmp_tanh_net_morph(ctypes.byref(s), _ptr(x0, shape=(N, d), name="x0"), N, int(T), float(eta),
+                                     _ptr(xT), _ptr(ckpt, name="ckpt"), int(k), _stream()), "pdmp_tanh_net_morph")
+    return xT
+
+
+def tanh_net_query(net: DeviceTanhNet, x: torch.Tensor):
+    """(c, s, grad c) of the tanh network at points x (N x d)."""
+    N, d = x.shape[0], net.d
+    c = torch.empty(N, device=x.device)
+    s_out = torch.empty(N, device=x.device)
+    g = torch.empty(N, d, device=x.device)
+    s = net.struct()
+    _check(lib().pdmp_tanh_net_query(ctypes.byref(s), _ptr(x, shape=(N, d), name="x"), N, _ptr(c), _ptr(s_out),
+                                     _ptr(g), _stream()), "pdmp_tanh_net_query")
+    return c, s_out, g
+
+
+def tanh_net_lipschitz(net: DeviceTanhNet):
+    """(L, G): certified bounds on sup |Hess c|_2 and sup |grad s| (FP64, host)."""
+    L, G = ctypes.c_double(0), ctypes.c_double(0)
+    s = net.struct()
+    _check(lib().pdmp_tanh_net_lipschitz(ctypes.byref(s), ctypes.byref(L), ctypes.byref(G), _stream()),
+           "pdmp_tanh_net_lipschitz")
+    return float(L.value), float(G.value)
 
 
 def cull_radius(field: DeviceField, eps: float):

@@ -2,6 +2,8 @@
 // the launchers in the other translation units.  Nothing here computes.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -122,6 +124,198 @@ pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t 
   }
   return cuda_status(pdmp::morph_dispatch(f->kind, f->d, field_args(f), x0, N, T, eta, xT, ckpt, k, nullptr,
                                           nullptr, ws, st));
+}
+
+static pdmp_status check_chain(const pdmp_chain* c) {
+  if (c == nullptr || c->n < 1 || c->n > pdmp::kChainMax || c->p < 1 || c->p > 8) return PDMP_ERR_INVALID_ARG;
+  if (!std::isfinite(c->base[0]) || !std::isfinite(c->base[1])) return PDMP_ERR_INVALID_ARG;
+  for (int k = 0; k < c->n; ++k)
+    if (!(c->lengths[k] >= 0.0f) || !std::isfinite(c->lengths[k])) return PDMP_ERR_INVALID_ARG;
+  return PDMP_OK;
+}
+
+size_t pdmp_cspace_workspace(const pdmp_field* f, const pdmp_chain* chain, int64_t N) {
+  if (check_field(f) != PDMP_OK || check_chain(chain) != PDMP_OK || f->d != 2 || N <= 0) return 0;
+  return pdmp::cspace_workspace(f->d, f->M, chain->n, chain->p, N);
+}
+
+pdmp_status pdmp_cspace_morph(const pdmp_field* f, const pdmp_chain* chain, const float* q0, int64_t N, int32_t T,
+                              float eta, float* qT, void* ws, size_t ws_bytes, void* stream) {
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if ((s = check_chain(chain)) != PDMP_OK) return s;
+  if (f->d != 2) return PDMP_ERR_UNSUPPORTED;
+  if (!(eta > 0.0f) || !std::isfinite(eta) || N < 0 || T < 0) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (N > (int64_t)INT32_MAX / (chain->n * chain->p)) return PDMP_ERR_INVALID_ARG;   // body points index the sort
+  if (!ok_ptr(q0, true) || !ok_ptr(qT, true) || !ok_ptr(ws, true)) return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::cspace_workspace(f->d, f->M, chain->n, chain->p, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = as_stream(stream);
+  if (T == 0) {
+    if (qT != q0) return cuda_status(cudaMemcpyAsync(qT, q0, sizeof(float) * N * chain->n, cudaMemcpyDeviceToDevice, st));
+    return PDMP_OK;
+  }
+  return cuda_status(pdmp::cspace_morph(field_args(f), f->kind, chain->n, chain->p, chain->base, chain->lengths, q0, N,
+                                        T, eta, qT, ws, st));
+}
+
+pdmp_status pdmp_cspace_lipschitz(const pdmp_chain* chain, double Lx, double Gx, double* Lq) {
+  pdmp_status s = check_chain(chain);
+  if (s != PDMP_OK) return s;
+  if (Lq == nullptr || !(Lx >= 0.0) || !(Gx >= 0.0) || !std::isfinite(Lx) || !std::isfinite(Gx))
+    return PDMP_ERR_INVALID_ARG;
+  const int n = chain->n, p = chain->p;
+  double total = 0.0;
+  for (int k = 0; k < n; ++k) {
+    for (int r = 1; r <= p; ++r) {
+      // reach[j]: chain length from joint j to this body point
+      double reach[pdmp::kChainMax];
+      double acc = (double)r / p * chain->lengths[k];
+      for (int j = k; j >= 0; --j) {
+        reach[j] = acc;
+        if (j > 0) acc += chain->lengths[j - 1];
+      }
+      double jac2 = 0.0, hess2 = 0.0;
+      for (int j = 0; j <= k; ++j) {
+        jac2 += reach[j] * reach[j];
+        for (int m = 0; m <= k; ++m) {
+          const double rr = reach[std::max(j, m)];
+          hess2 += rr * rr;
+        }
+      }
+      total += jac2 * Lx + Gx * std::sqrt(hess2);
+    }
+  }
+  *Lq = total;
+  return PDMP_OK;
+}
+
+static pdmp_status check_net(const pdmp_tanh_net* n) {
+  if (n == nullptr) return PDMP_ERR_INVALID_ARG;
+  if (n->d < 1 || n->d > 8 || n->H < 1 || n->H > 1024) return PDMP_ERR_INVALID_ARG;
+  if (!ok_ptr(n->W1, true) || !ok_ptr(n->b1, true) || !ok_ptr(n->W2, true) || !ok_ptr(n->b2, true) ||
+      !ok_ptr(n->w3, true))
+    return PDMP_ERR_INVALID_ARG;
+  if (!std::isfinite(n->b3) || n->lipschitz < 0.0 || std::isnan(n->lipschitz)) return PDMP_ERR_INVALID_ARG;
+  if (!((n->d == 2 || n->d == 3) && (n->H == 32 || n->H == 64))) return PDMP_ERR_UNSUPPORTED;
+  return PDMP_OK;
+}
+
+static pdmp::TanhNetArgs net_args(const pdmp_tanh_net* n) {
+  pdmp::TanhNetArgs a;
+  a.d = n->d;
+  a.H = n->H;
+  a.W1 = n->W1;
+  a.b1 = n->b1;
+  a.W2 = n->W2;
+  a.b2 = n->b2;
+  a.w3 = n->w3;
+  a.b3 = n->b3;
+  return a;
+}
+
+pdmp_status pdmp_tanh_net_morph(const pdmp_tanh_net* net, const float* x0, int64_t N, int32_t T, float eta,
+                                float* xT, float* ckpt, int32_t k, void* stream) {
+  pdmp_status s = check_net(net);
+  if (s != PDMP_OK) return s;
+  if (!(eta > 0.0f) || !std::isfinite(eta)) return PDMP_ERR_INVALID_ARG;
+  if (net->lipschitz > 0.0 && (double)eta * net->lipschitz >= 1.0) return PDMP_ERR_STEP_TOO_LARGE;
+  if (N < 0 || T < 0) return PDMP_ERR_INVALID_ARG;
+  if (ckpt != nullptr && (k < 1 || T % k != 0)) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || !ok_ptr(ckpt, false)) return PDMP_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  if (T == 0) {
+    if (xT != x0) return cuda_status(cudaMemcpyAsync(xT, x0, sizeof(float) * N * net->d, cudaMemcpyDeviceToDevice, st));
+    return PDMP_OK;
+  }
+  return cuda_status(pdmp::tanh_net_morph(net_args(net), x0, N, T, eta, xT, ckpt, k, st));
+}
+
+pdmp_status pdmp_tanh_net_query(const pdmp_tanh_net* net, const float* x, int64_t N, float* c, float* s_out,
+                                float* grad, void* stream) {
+  pdmp_status s = check_net(net);
+  if (s != PDMP_OK) return s;
+  if (N < 0) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x, true) || !ok_ptr(c, false) || !ok_ptr(s_out, false) || !ok_ptr(grad, false))
+    return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::tanh_net_query(net_args(net), x, N, c, s_out, grad, as_stream(stream)));
+}
+
+// largest eigenvalue of the symmetric n x n matrix a (overwritten) by Jacobi
+// rotations, each annihilating the largest off-diagonal entry
+static double largest_eigenvalue(std::vector<double>& a, int n) {
+  for (int it = 0; it < 50 * n * n; ++it) {
+    int p = 0, q = 1;
+    double big = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      diag = std::fmax(diag, std::fabs(a[i * n + i]));
+      for (int j = i + 1; j < n; ++j)
+        if (std::fabs(a[i * n + j]) > big) {
+          big = std::fabs(a[i * n + j]);
+          p = i;
+          q = j;
+        }
+    }
+    if (n < 2 || big <= 1e-17 * std::fmax(diag, 1e-300)) break;
+    const double app = a[p * n + p], aqq = a[q * n + q], apq = a[p * n + q];
+    const double phi = 0.5 * std::atan2(2.0 * apq, aqq - app);
+    const double c = std::cos(phi), s = std::sin(phi);
+    for (int k = 0; k < n; ++k) {
+      const double akp = a[k * n + p], akq = a[k * n + q];
+      a[k * n + p] = c * akp - s * akq;
+      a[k * n + q] = s * akp + c * akq;
+    }
+    for (int k = 0; k < n; ++k) {
+      const double apk = a[p * n + k], aqk = a[q * n + k];
+      a[p * n + k] = c * apk - s * aqk;
+      a[q * n + k] = s * apk + c * aqk;
+    }
+  }
+  double m = a[0];
+  for (int i = 1; i < n; ++i) m = std::fmax(m, a[i * n + i]);
+  return m;
+}
+
+// |W|_2 of the rows x cols matrix W (row-major), from W^T W, rounded up
+static double spectral(const std::vector<float>& W, int rows, int cols) {
+  std::vector<double> g((size_t)cols * cols, 0.0);
+  for (int r = 0; r < rows; ++r)
+    for (int a = 0; a < cols; ++a)
+      for (int b = 0; b < cols; ++b) g[a * cols + b] += (double)W[r * cols + a] * (double)W[r * cols + b];
+  return std::sqrt(std::fmax(largest_eigenvalue(g, cols), 0.0) * (1.0 + 1e-12));
+}
+
+pdmp_status pdmp_tanh_net_lipschitz(const pdmp_tanh_net* net, double* L, double* G, void* stream) {
+  pdmp_status s = check_net(net);
+  if (s != PDMP_OK && s != PDMP_ERR_UNSUPPORTED) return s;
+  if (L == nullptr) return PDMP_ERR_INVALID_ARG;
+  const int d = net->d, H = net->H;
+  std::vector<float> W1((size_t)H * d), W2((size_t)H * H), w3(H);
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(W1.data(), net->W1, sizeof(float) * W1.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(W2.data(), net->W2, sizeof(float) * W2.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w3.data(), net->w3, sizeof(float) * w3.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  const double n1 = spectral(W1, H, d), n2 = spectral(W2, H, H);
+  double w3sq = 0.0, w3inf = 0.0, col = 0.0;
+  for (int i = 0; i < H; ++i) {
+    w3sq += (double)w3[i] * w3[i];
+    w3inf = std::fmax(w3inf, std::fabs((double)w3[i]));
+  }
+  for (int j = 0; j < H; ++j) {
+    double c = 0.0;
+    for (int i = 0; i < H; ++i) c += std::fabs((double)W2[i * H + j]) * std::fabs((double)w3[i]);
+    col = std::fmax(col, c);
+  }
+  const double tanh2_max = 4.0 / (3.0 * std::sqrt(3.0));
+  const double grad_bound = n1 * n2 * std::sqrt(w3sq);
+  const double hess_s = n1 * n1 * tanh2_max * (col + n2 * n2 * w3inf);
+  if (G) *G = grad_bound;
+  *L = 0.25 * hess_s + grad_bound * grad_bound / (6.0 * std::sqrt(3.0));
+  return PDMP_OK;
 }
 
 static bool cull_field(const pdmp_field* f) { return f->kind == PDMP_KIND_RBF && (f->d == 2 || f->d == 3); }

@@ -43,9 +43,10 @@ struct BatchUnit {
 
 // ---------------------------------------------------------------- variants
 // (warps per block, samples per lane)
-constexpr int kBatchVariants = 4;
-static const int kVariantW[kBatchVariants] = {4, 2, 4, 8};
-static const int kVariantK[kBatchVariants] = {8, 8, 4, 8};
+// variant 0 is the single-field launch's shape (FastShape)
+constexpr int kBatchVariants = 5;
+static const int kVariantW[kBatchVariants] = {4, 2, 4, 8, 4};
+static const int kVariantK[kBatchVariants] = {10, 8, 4, 8, 8};
 
 static int variant_tile(int v) { return 32 * kVariantK[v]; }
 
@@ -186,6 +187,7 @@ k_morph_batched(const BatchEnv* __restrict__ envs, const BatchUnit* __restrict__
     a.traj = nullptr;
     a.steps = nullptr;
     a.s_out = nullptr;
+    a.g_out = nullptr;
     const int64_t p0 = E.sample_base + (int64_t)un.tile * kTile;
     const int64_t pend = E.sample_base + E.N;
     if (E.d == 2)
@@ -321,7 +323,7 @@ cudaError_t batch_prepare(const pdmp_env* envs, int n, int variant, void* ws, pd
       return e;                                                                                                      \
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_morph_batched<W_, K_>, block, smem))) return e; \
   }
-  PDMP_VARIANT(0, 4, 8) PDMP_VARIANT(1, 2, 8) PDMP_VARIANT(2, 4, 4) PDMP_VARIANT(3, 8, 8)
+  PDMP_VARIANT(0, 4, 10) PDMP_VARIANT(1, 2, 8) PDMP_VARIANT(2, 4, 4) PDMP_VARIANT(3, 8, 8) PDMP_VARIANT(4, 4, 8)
 #undef PDMP_VARIANT
   if (per_sm < 1) per_sm = 1;
   memset(plan, 0, sizeof(*plan));
@@ -386,7 +388,7 @@ cudaError_t batch_run(const pdmp_batch_plan* P, void* ws, cudaStream_t st) {
   if (P->variant == V)                                                                                      \
     k_morph_batched<W_, K_><<<(unsigned)P->grid, 32 * W_, P->smem_bytes, st>>>(envs, units, P->n_units, perm, \
                                                                                counter);
-  PDMP_VARIANT(0, 4, 8) PDMP_VARIANT(1, 2, 8) PDMP_VARIANT(2, 4, 4) PDMP_VARIANT(3, 8, 8)
+  PDMP_VARIANT(0, 4, 10) PDMP_VARIANT(1, 2, 8) PDMP_VARIANT(2, 4, 4) PDMP_VARIANT(3, 8, 8) PDMP_VARIANT(4, 4, 8)
 #undef PDMP_VARIANT
   return cudaGetLastError();
 }

@@ -39,7 +39,10 @@ __device__ __forceinline__ u64 ex2x2(u64 a) {
 
 // Tile shape: W warps per block (each summing over its share of M) and K
 // samples per lane (even: f32x2 pairs).  The single-field launch uses
-// W = 4, K = 8; the batched launch picks among a few shapes (autotuned).
+// W = 4, K = 10 (measured fastest on the 2-D fitted workload among K = 6..16,
+// W = 2..8, unroll 1..4 and 32..128-centre stages); the batched launch picks
+// among a few shapes (autotuned).  Shapes with K > 8 need more than 128
+// registers a thread and run 12 warps per SM, the others 16.
 #ifndef PDMP_WARP_STAGE
 #define PDMP_WARP_STAGE 64
 #endif
@@ -53,8 +56,10 @@ template <int W, int K>
 struct Shape {
   static_assert(K % 2 == 0, "samples per lane must be even (f32x2 pairs)");
   static constexpr int kWarps = W, kThreads = 32 * W, kK = K, kPairs = K / 2, kTile = 32 * K;
-  static constexpr int kMinBlocks = 16 / W;    // 16 warps per SM
+  static constexpr int kMinBlocks = (K > 8 ? 12 : 16) / W;   // warps per SM / warps per block
 };
+
+using FastShape = Shape<4, 10>;                // the single-field launch
 
 template <int D>
 struct FastRec {
@@ -203,6 +208,7 @@ struct TileArgs {
   float* traj;
   float* steps;
   float* s_out;   // optional: the logit s(x_{T-1}) of the last step, per sample
+  float* g_out;   // optional: grad c(x_{T-1}) of the last step, per sample (d values)
 };
 
 // Bounding box of the tile's active samples (identical in every warp: each
@@ -360,8 +366,12 @@ __device__ __forceinline__ void tile_finish_step(const TileArgs& a, int t, int64
     const float c = -eta * d1;
     const int64_t p = p0 + k * 32 + lane;
     const bool own = act[k] && warp == 0;
-    const int64_t n = (own && (TRACE || a.s_out != nullptr)) ? (int64_t)a.perm[p] - a.perm_base : 0;
+    const bool last_out = t == T - 1 && (a.s_out != nullptr || a.g_out != nullptr);
+    const int64_t n = (own && (TRACE || last_out)) ? (int64_t)a.perm[p] - a.perm_base : 0;
     if (own && a.s_out != nullptr && t == T - 1) a.s_out[n] = shat + bias;
+    if (own && a.g_out != nullptr && t == T - 1)
+#pragma unroll
+      for (int j = 0; j < D; ++j) a.g_out[n * D + j] = d1 * (-2.0f * gamma * ghat[j]);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       const float inc = __fmul_rn(c, -2.0f * gamma * ghat[j]);

@@ -12,6 +12,15 @@ cudaError_t morph_direct(int kind, int d, const FieldArgs& fa, const float* x0, 
                          float* xT, float* ckpt, int k, float* traj, float* steps, cudaStream_t st);
 // fast RBF path (d = 2, 3): spatially sorted tiles, expanded exponent, f32x2
 size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N);
+// grad c at N points by the fast RBF tile kernel (ws: morph_rbf_fast_workspace)
+cudaError_t grad_rbf_fast(int d, const FieldArgs& fa, const float* x, int64_t N, float* g, void* ws,
+                          cudaStream_t st);
+
+// planar serial chains for the C-space pull-back (Eq. 3)
+constexpr int kChainMax = 16;
+size_t cspace_workspace(int d, int64_t M, int n, int p, int64_t N);
+cudaError_t cspace_morph(const FieldArgs& fa, int kind, int n, int p, const float* base, const float* len,
+                         const float* q0, int64_t N, int T, float eta, float* qT, void* ws, cudaStream_t st);
 // s_out (optional): the logit at the last step's state, per sample
 cudaError_t morph_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
                            float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st,
@@ -24,6 +33,17 @@ cudaError_t morph_dispatch(int kind, int d, const FieldArgs& fa, const float* x0
 
 cudaError_t morph_inverse(int kind, int d, const FieldArgs& fa, const float* z, int64_t N, int T, float eta,
                           float tol, int maxit, float* y, int32_t* iters, cudaStream_t st);
+
+// the tanh occupancy network of Sec. 3.1 (d -> H -> H -> 1), float32 device arrays
+struct TanhNetArgs {
+  int d, H;
+  const float *W1, *b1, *W2, *b2, *w3;
+  float b3;
+};
+cudaError_t tanh_net_morph(const TanhNetArgs& net, const float* x0, int64_t N, int T, float eta, float* xT,
+                           float* ckpt, int k, cudaStream_t st);
+cudaError_t tanh_net_query(const TanhNetArgs& net, const float* x, int64_t N, float* c, float* s, float* g,
+                           cudaStream_t st);
 
 size_t morph_rbf_cull_workspace(int d, int64_t M, int64_t N);
 cudaError_t morph_rbf_cull(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float r_cut,

@@ -16,9 +16,10 @@
 // form only while g' R^2 <= 4 (R the tile's half-diagonal) and otherwise the
 // direct form x - mu_m for that step.
 //
-// Work split.  A block of 4 warps owns a tile of 256 samples; every warp holds
-// all 256 (8 per lane) and sums over its own quarter of each 256-centre stage;
-// the four partial sums are added in a fixed order once per step.
+// Work split.  A block of 4 warps owns a tile of 320 samples; every warp holds
+// all 320 (10 per lane, five f32x2 pairs) and sums over its own contiguous
+// quarter of the centres; the four partial sums are added in a fixed order
+// once per step.
 #include "fast_tile.cuh"
 #include "kernels.cuh"
 #include "sort.cuh"
@@ -26,11 +27,11 @@
 namespace pdmp {
 
 template <int D, bool TRACE>
-__global__ void __launch_bounds__(Shape<4, 8>::kThreads, Shape<4, 8>::kMinBlocks)
+__global__ void __launch_bounds__(FastShape::kThreads, FastShape::kMinBlocks)
 k_morph_rbf_fast(TileArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t p0 = (int64_t)blockIdx.x * Shape<4, 8>::kTile;
-  fast_tile<D, 4, 8, TRACE>(a, p0, a.N, smem);
+  const int64_t p0 = (int64_t)blockIdx.x * FastShape::kTile;
+  fast_tile<D, FastShape::kWarps, FastShape::kK, TRACE>(a, p0, a.N, smem);
 }
 
 // ------------------------------------------------------------------ host
@@ -45,13 +46,13 @@ size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N) {
 template <int D>
 static cudaError_t launch_fast(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
                                float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st,
-                               float* s_out) {
+                               float* s_out, float* g_out = nullptr) {
   float4* tab = reinterpret_cast<float4*>(ws);
   SortWs sw = sort_layout((char*)ws + table_bytes(D, fa.M), D, N);
   k_rbf_table<D><<<(unsigned)((fa.M + 255) / 256), 256, 0, st>>>(fa.centres, fa.w, fa.M, tab);
   cudaError_t e = spatial_sort(D, x0, N, sw, st);
   if (e != cudaSuccess) return e;
-  constexpr size_t smem = fast_smem_bytes<D, 4, 8>();
+  constexpr size_t smem = fast_smem_bytes<D, FastShape::kWarps, FastShape::kK>();
   TileArgs a;
   a.tab = tab;
   a.M = fa.M;
@@ -69,13 +70,14 @@ static cudaError_t launch_fast(const FieldArgs& fa, const float* x0, int64_t N, 
   a.traj = traj;
   a.steps = steps;
   a.s_out = s_out;
-  const unsigned blocks = (unsigned)((N + Shape<4, 8>::kTile - 1) / Shape<4, 8>::kTile);
+  a.g_out = g_out;
+  const unsigned blocks = (unsigned)((N + FastShape::kTile - 1) / FastShape::kTile);
   if (traj != nullptr) {
     cudaFuncSetAttribute(k_morph_rbf_fast<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_morph_rbf_fast<D, true><<<blocks, Shape<4, 8>::kThreads, smem, st>>>(a);
+    k_morph_rbf_fast<D, true><<<blocks, FastShape::kThreads, smem, st>>>(a);
   } else {
     cudaFuncSetAttribute(k_morph_rbf_fast<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_morph_rbf_fast<D, false><<<blocks, Shape<4, 8>::kThreads, smem, st>>>(a);
+    k_morph_rbf_fast<D, false><<<blocks, FastShape::kThreads, smem, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -84,6 +86,14 @@ cudaError_t morph_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t 
                            float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st, float* s_out) {
   if (d == 2) return launch_fast<2>(fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st, s_out);
   if (d == 3) return launch_fast<3>(fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st, s_out);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t grad_rbf_fast(int d, const FieldArgs& fa, const float* x, int64_t N, float* g, void* ws,
+                          cudaStream_t st) {
+  // one step with the update discarded: the per-sample gradient output only
+  if (d == 2) return launch_fast<2>(fa, x, N, 1, 0.0f, nullptr, nullptr, 0, nullptr, nullptr, ws, st, nullptr, g);
+  if (d == 3) return launch_fast<3>(fa, x, N, 1, 0.0f, nullptr, nullptr, 0, nullptr, nullptr, ws, st, nullptr, g);
   return cudaErrorInvalidValue;
 }
 

@@ -200,3 +200,28 @@ def test_culled_validation():
     r = ctypes.c_float(0)
     assert L.pdmp_cull_radius(ctypes.byref(f), 0.0, ctypes.byref(r), None, None) == 1
     assert L.pdmp_cull_radius(ctypes.byref(fld(kind=1, d=7, phase=A)), 1e-6, ctypes.byref(r), None, None) == 8
+
+
+@nogpu
+def test_tanh_net_validation():
+    L = pdmp.lib()
+
+    def net(d=2, H=64, W1=A, W2=A, b3=0.0, lipschitz=0.0):
+        n = pdmp._TanhNet()
+        n.d, n.H, n.W1, n.b1, n.W2, n.b2, n.w3, n.b3, n.lipschitz = d, H, W1, A, W2, A, A, b3, lipschitz
+        return n
+
+    call = lambda n, **kw: L.pdmp_tanh_net_morph(ctypes.byref(n), kw.get("x0", A), kw.get("N", 100),
+                                                 kw.get("T", 4), kw.get("eta", 0.01), kw.get("xT", A),
+                                                 kw.get("ckpt", None), kw.get("k", 0), None)
+    assert call(net(d=4)) == 8 and call(net(H=48)) == 8          # unsupported shapes
+    assert call(net(d=0)) == 1 and call(net(d=9)) == 1
+    assert call(net(W1=None)) == 1 and call(net(W2=MIS)) == 1
+    assert call(net(b3=float("nan"))) == 1
+    assert call(net(lipschitz=-1.0)) == 1
+    assert call(net(lipschitz=100.0), eta=0.011) == 2
+    assert call(net(), eta=0.0) == 1 and call(net(), N=-1) == 1
+    assert call(net(), ckpt=A, k=3) == 1
+    assert call(net(), N=0, x0=None, xT=None) == 0
+    assert L.pdmp_tanh_net_query(ctypes.byref(net()), MIS, 10, None, None, None, None) == 1
+    assert L.pdmp_tanh_net_lipschitz(ctypes.byref(net()), None, None, None) == 1

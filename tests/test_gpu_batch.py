@@ -37,7 +37,7 @@ def small_envs(seed=7, n=12):
     return envs, host
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_batched_matches_single_field_and_oracle(variant):
     envs, host = small_envs()
     b = pdmp.Batch(envs)
