@@ -288,6 +288,8 @@ def run_ours(args, world, rank, local):
         line["extras"] = {
             "culled_morph": culled,
             "tanh_net_cost": extra_tanh_net(pdmp, torch, n_sms, pk),
+            "cspace_7link": extra_cspace(pdmp, torch, fld, info),
+            "sampler": extra_sampler(pdmp, torch, fld, eta),
             "batched_256_envs": extra_batched(pdmp, torch, n_sms, pk),
             "rff7d_differentiation": extra_rff(pdmp, torch, n_sms, pk),
             "surrogate_3d": extra_surrogate(pdmp, torch, args),
@@ -339,6 +341,49 @@ def extra_batched(pdmp, torch, n_sms, pk):
             "roofline_frac": (work / t) / (work / t_peak), "variant": best,
             "variant_ms": [round(v, 3) for v in times], "launch": "CUDA graph of one pdmp_morph_batched",
             "gpu_launches_per_run": 11}
+
+
+def extra_cspace(pdmp, torch, fld, info, n=1 << 16, t_steps=20, links=7, per_link=4):
+    """Eq. (3) in joint space: a 7-link planar arm (4 body points a link) at
+    the centre of the fitted 2-D workspace; the step is the certified one
+    (eta = 0.5 / L_q from the field's bounds and the chain lengths).
+    Reports sample-steps/s and the body-point feature evaluations per second."""
+    chain = wl.planar_arm(links, 4.5, (5.0, 5.0), per_link)
+    _, G = pdmp.lipschitz_bound(fld, np.full(2, -0.5), np.full(2, 10.5), cells=128)
+    Lq = pdmp.cspace_lipschitz(chain, info["L"], G)
+    eta = float(np.float32(0.5 / Lq))
+    lo, hi = wl.joint_box(links)
+    q0 = torch.from_numpy(wl.uniform_box(11, wl.S_SAMPLES, n, lo, hi)).cuda()
+    out = torch.empty_like(q0)
+    ws = torch.empty(pdmp.cspace_workspace(fld, chain, n), dtype=torch.uint8, device="cuda")
+    run = lambda: pdmp.cspace_morph(fld, chain, q0, t_steps, eta, out=out, ws=ws)
+    run()
+    t = _time(torch, run, reps=3)
+    b = links * per_link
+    return {"value": n * t_steps / t, "unit": "sample-steps/s", "ms": 1e3 * t, "N": n, "T": t_steps,
+            "joints": links, "body_points": b, "feature_evals_per_s": n * t_steps * b * M / t, "eta": eta, "L_q": Lq,
+            "launches_per_step": 11}
+
+
+def extra_sampler(pdmp, torch, fld, eta, batch=1 << 16, capacity=1 << 20, t_steps=50):
+    """The diffeomorphic sampler (Sec. 3.3) on the fitted 2-D field: time for
+    the background producer to fill a bucket of 2^20 morphed samples, the
+    delivered rate, and the latency of a 10,000-sample draw from the full bucket."""
+    lo, hi = np.zeros(2), np.full(2, 10.0)
+    t0 = time.perf_counter()
+    s = pdmp.Sampler(fld, lo, hi, t_steps, eta, batch=batch, capacity=capacity, seed=3)
+    try:
+        while s.stats()["queued"] < capacity and time.perf_counter() - t0 < 60:
+            time.sleep(0.002)
+        fill = time.perf_counter() - t0
+        st = s.stats()
+        t1 = time.perf_counter()
+        _, m = s.draw(10_000)
+        draw_us = 1e6 * (time.perf_counter() - t1)
+    finally:
+        s.close()
+    return {"bucket_fill_s": fill, "bucket_samples": capacity, "delivered_per_s": st["produced"] / fill,
+            "batch": batch, "T": t_steps, "draw_10k_us": draw_us, "draw_10k_morphed": m, "error": st["error"]}
 
 
 def extra_culled(pdmp, torch, fld, x0, xT_dense, eta, eps=1e-6):
