@@ -39,6 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 LAUNCHES_PER_MORPH = 9
 FP32_LANES_PER_SM = 128           # FP32 pipe width per SM per clock
 MUFU_EX2_PER_SM = 32              # measured ex2 throughput per SM per clock on GB300
+MUFU_SINCOS_PER_SM = 15.6         # measured sin (or cos) throughput per SM per clock on GB300
 KERNEL_SOURCES = ["paper_2108_11775_gb300/csrc/morph_rbf_fast.cu", "paper_2108_11775_gb300/csrc/fast_tile.cuh",
                   "paper_2108_11775_gb300/csrc/sort.cu", "paper_2108_11775_gb300/csrc/common.cuh"]
 
@@ -447,7 +448,17 @@ def extra_rff(pdmp, torch, n_sms, pk):
     t_vjp = _time(torch, lambda: pdmp.morph_vjp(f, x0, T, eta, k, gT, ckpt=ck, g0=g0), reps=2)
     t_ld = _time(torch, lambda: pdmp.logdet(f, x0, T, eta), reps=1)
     work = float(N) * T * M
-    return {"forward": work / t_fwd, "vjp_per_pass": 2 * work / t_vjp, "logdet": work / t_ld, "unit": "feature-evals/s",
+    d = 7
+    clk = n_sms * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    # FP32 / MUFU rooflines per feature (128 FP32 lanes, 15.6 sin or cos per SM per clock):
+    # forward 2d+2 FP32 + 2 MUFU; VJP pass 4d+3 FP32 + 2 MUFU; log-det 2d+2 + d(d+1)/2 FP32 + 2 MUFU
+    mufu = MUFU_SINCOS_PER_SM / 2.0
+    peaks = {"forward": clk * min(FP32_LANES_PER_SM / (2 * d + 2), mufu),
+             "vjp_per_pass": clk * min(FP32_LANES_PER_SM / (4 * d + 3), mufu),
+             "logdet": clk * min(FP32_LANES_PER_SM / (2 * d + 2 + d * (d + 1) // 2), mufu)}
+    rates = {"forward": work / t_fwd, "vjp_per_pass": 2 * work / t_vjp, "logdet": work / t_ld}
+    return {**rates, "unit": "feature-evals/s",
+            "roofline_frac": {k: rates[k] / peaks[k] for k in rates}, "roofline_peak": peaks,
             "ms": {"forward": 1e3 * t_fwd, "vjp": 1e3 * t_vjp, "logdet": 1e3 * t_ld},
             "note": "VJP counts its recompute pass and its Hessian-vector pass (2 N T M)"}
 

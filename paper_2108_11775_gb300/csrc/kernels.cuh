@@ -12,6 +12,9 @@ cudaError_t morph_direct(int kind, int d, const FieldArgs& fa, const float* x0, 
                          float* xT, float* ckpt, int k, float* traj, float* steps, cudaStream_t st);
 // fast RBF path (d = 2, 3): spatially sorted tiles, expanded exponent, f32x2
 size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N);
+size_t morph_rff_fast_workspace(int d, int64_t M);
+cudaError_t morph_rff_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
+                           float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
 // grad c at N points by the fast RBF tile kernel (ws: morph_rbf_fast_workspace)
 cudaError_t grad_rbf_fast(int d, const FieldArgs& fa, const float* x, int64_t N, float* g, void* ws,
                           cudaStream_t st);

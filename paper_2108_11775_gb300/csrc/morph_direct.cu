@@ -135,13 +135,15 @@ namespace pdmp {
 // Chooses the kernel for a morph request.
 size_t morph_workspace(int kind, int d, int64_t M, int64_t N) {
   if (kind == PDMP_KIND_RBF && (d == 2 || d == 3) && N > 0) return morph_rbf_fast_workspace(d, M, N);
+  if (kind == PDMP_KIND_RFF && N > 0) return morph_rff_fast_workspace(d, M);
   return 0;
 }
 
 cudaError_t morph_dispatch(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta,
                            float* xT, float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st) {
   if (ws != nullptr && morph_workspace(kind, d, fa.M, N) > 0)
-    return morph_rbf_fast(d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
+    return kind == PDMP_KIND_RBF ? morph_rbf_fast(d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st)
+                                 : morph_rff_fast(d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
   return morph_direct(kind, d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, st);
 }
 }  // namespace pdmp

@@ -96,7 +96,7 @@ def test_morph_workspace_size_and_checks():
     f = fld()
     need = L.pdmp_morph_workspace(ctypes.byref(f), 1 << 20)
     assert need > (1 << 20) * 8                       # keys + permutation at least
-    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, phase=A)), 1 << 20) == 0   # RFF: direct path
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, phase=A)), 1 << 20) == 16 * 80   # RFF: pair table
     assert L.pdmp_morph_workspace(ctypes.byref(fld(d=1)), 1000) == 0
     assert morph_call(f, N=1 << 20, ws=A, ws_bytes=need - 1) == 3
     assert morph_call(f, N=1 << 20, ws=MIS, ws_bytes=need) == 1
