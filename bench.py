@@ -560,6 +560,50 @@ def run_reference(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(case: str):
+    """One small launch of one kernel family (for ncu captures of kernels other
+    than the headline one): inputs a few tens of MB, a handful of launches."""
+    import torch
+    import paper_2108_11775_gb300 as pdmp
+    torch.cuda.set_device(0)
+    out = {"case": case}
+    if case in ("rff7d", "vjp", "logdet"):
+        wk = wl.config3(N=1 << 17)
+        f = pdmp.DeviceField.from_host(wk.field)
+        L, _ = pdmp.lipschitz_bound(f)
+        eta = float(np.float32(0.5 / L))
+        x0 = torch.from_numpy(wk.x0).cuda()
+        T, k = 4, 2
+        ck = torch.empty(T // k, x0.shape[0], 7, device="cuda")
+        if case == "rff7d":
+            out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph(f, x0, T, eta, ckpt=ck, k=k), reps=1)
+        elif case == "vjp":
+            pdmp.morph(f, x0, T, eta, ckpt=ck, k=k)
+            gT = torch.from_numpy(wk.extra["gT"][:x0.shape[0]]).cuda()
+            out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_vjp(f, x0, T, eta, k, gT, ckpt=ck), reps=1)
+        else:
+            out["ms"] = 1e3 * _time(torch, lambda: pdmp.logdet(f, x0, T, eta), reps=1)
+    elif case == "culled":
+        lo, hi = np.zeros(2), np.full(2, 10.0)
+        centres = wl.uniform_box(2, wl.S_CENTRES, M, lo, hi)
+        boxes = wl.random_boxes(2, 64, lo, hi, 0.3, 1.5)
+        f = pdmp.DeviceField.from_host(wl.Field(wl.RBF, centres, wl.proxy_fitted_weights(2, centres, boxes), gamma=8.0))
+        x0 = torch.from_numpy(wl.uniform_box(2, wl.S_SAMPLES, 1 << 18, lo, hi)).cuda()
+        r, _ = pdmp.cull_radius(f, 1e-6)
+        out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_culled(f, x0, 3, 4.5e-4, r), reps=1)
+    elif case == "tanh":
+        net = pdmp.DeviceTanhNet.from_host(wl.tanh_net(7, 2, 64))
+        L, _ = pdmp.tanh_net_lipschitz(net)
+        x0 = torch.from_numpy(wl.uniform_box(7, wl.S_SAMPLES, 1 << 18, np.zeros(2), np.full(2, 10.0))).cuda()
+        out["ms"] = 1e3 * _time(torch, lambda: pdmp.tanh_net_morph(net, x0, 3, float(np.float32(0.5 / L))), reps=1)
+    else:
+        raise SystemExit(f"unknown case {case}")
+    status, detail = pdmp.stream_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status} ({detail})")
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -572,7 +616,12 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=1500)
     ap.add_argument("--workload", choices=["full", "small"], default="full",
                     help="small: 262,144 samples and 3 steps of the same workload (for ncu captures)")
+    ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "tanh"], default=None,
+                    help="run one small launch of that kernel family and exit (for ncu captures)")
     args = ap.parse_args()
+    if args.case:
+        profile_case(args.case)
+        return
     if args.workload == "small":
         global N, T, WORKLOAD
         N, T = SMALL["N"], SMALL["T"]
