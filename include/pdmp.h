@@ -96,10 +96,13 @@ pdmp_status pdmp_stream_status(void* stream, int32_t* detail);
  * ws: NULL, or ws_bytes >= pdmp_morph_workspace(f, N) bytes of caller-owned
  * device scratch.  With a workspace, RBF fields in d = 2 or 3 take the fast
  * path: samples are ordered spatially (a deterministic counting sort on
- * Morton cells) so that each tile of 256 samples is compact, and features are
+ * Morton cells) so that each tile of 320 samples is compact, and features are
  * evaluated in an expanded form about the tile's centre with packed f32x2
- * arithmetic (2d + 1 FP32 operations and one ex2 per feature).  Without one,
- * or for other fields, every feature is evaluated directly from x - mu.
+ * arithmetic (2d + 1 FP32 operations and one ex2 per feature); RFF fields
+ * take a packed-pair path over a table of duplicated records.  The RBF fast
+ * path needs N < 2^31 (PDMP_ERR_INVALID_ARG otherwise).  Without a
+ * workspace every feature is evaluated directly from x - mu (RBF) or
+ * omega . x + b (RFF).
  * Sample state lives in registers for all T steps; features are evaluated in
  * FP32 with exp2 / sin / cos on the special-function unit.  Calls that share
  * a workspace must not overlap on the GPU. */
@@ -389,7 +392,7 @@ pdmp_status pdmp_tanh_net_lipschitz(const pdmp_tanh_net* net, double* L, double*
  * work (device, 8-byte aligned, may be NULL) is incremented by the number of
  * feature evaluations performed (sum over tiles and steps of the visited
  * centres times the tile's samples).  x0 may alias xT; checkpoints as in
- * pdmp_morph.  PDMP_ERR_UNSUPPORTED for RFF fields or d = 1. */
+ * pdmp_morph.  N < 2^31.  PDMP_ERR_UNSUPPORTED for RFF fields or d = 1. */
 size_t pdmp_morph_culled_workspace(const pdmp_field* f, int64_t N);
 pdmp_status pdmp_morph_culled(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float r_cut,
                               float* xT, float* ckpt, int32_t k, void* ws, size_t ws_bytes,

@@ -103,6 +103,9 @@ size_t pdmp_morph_workspace(const pdmp_field* f, int64_t N) {
 static pdmp_status check_ws(const pdmp_field* f, int64_t N, void* ws, size_t ws_bytes) {
   if (ws == nullptr) return PDMP_OK;
   if (!aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+  // the fast paths index samples through an int32 permutation
+  if (N > (int64_t)INT32_MAX && f->kind == PDMP_KIND_RBF && pdmp::morph_workspace(f->kind, f->d, f->M, 1) > 0)
+    return PDMP_ERR_INVALID_ARG;
   if (ws_bytes < pdmp::morph_workspace(f->kind, f->d, f->M, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
   return PDMP_OK;
 }
@@ -332,7 +335,8 @@ pdmp_status pdmp_morph_culled(const pdmp_field* f, const float* x0, int64_t N, i
   if (s != PDMP_OK) return s;
   if (!cull_field(f)) return PDMP_ERR_UNSUPPORTED;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
-  if (N < 0 || T < 0 || !(r_cut > 0.0f) || !std::isfinite(r_cut)) return PDMP_ERR_INVALID_ARG;
+  if (N < 0 || N > (int64_t)INT32_MAX || T < 0 || !(r_cut > 0.0f) || !std::isfinite(r_cut)) return PDMP_ERR_INVALID_ARG;
+  if (f->M > (int64_t)INT32_MAX) return PDMP_ERR_INVALID_ARG;
   if (ckpt != nullptr && (k < 1 || T % k != 0)) return PDMP_ERR_INVALID_ARG;
   if (N == 0) return PDMP_OK;
   if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || !ok_ptr(ckpt, false) || !ok_ptr(ws, true) ||

@@ -225,3 +225,12 @@ def test_tanh_net_validation():
     assert call(net(), N=0, x0=None, xT=None) == 0
     assert L.pdmp_tanh_net_query(ctypes.byref(net()), MIS, 10, None, None, None, None) == 1
     assert L.pdmp_tanh_net_lipschitz(ctypes.byref(net()), None, None, None) == 1
+
+
+@nogpu
+def test_fast_paths_reject_sample_counts_past_int32():
+    L = pdmp.lib()
+    f = fld()
+    big = (1 << 31) + 5
+    assert morph_call(f, N=big, ws=A, ws_bytes=1 << 62) == 1
+    assert L.pdmp_morph_culled(ctypes.byref(f), A, big, 4, 0.01, 1.0, A, None, 0, A, 1 << 62, None, None) == 1
