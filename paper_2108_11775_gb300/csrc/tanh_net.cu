@@ -13,7 +13,10 @@
 // (the weight pair from shared memory, the activation duplicated), reading
 // per inner step one 16-byte activation vector and two 16-byte weight pairs.
 // W2 is staged once per block in both layouts (unit pairs of a column for the
-// forward product, of a row for the backward one).  Partial sums over the
+// forward product, of a row for the backward one); the activation tile holds
+// h1 for the forward product and then v2 for the backward one, and each
+// thread keeps 1 - h1^2 of its own units in registers (62.6 KB of shared
+// memory a block for H = 64: three blocks per SM).  Partial sums over the
 // 8 unit groups are added in a fixed order, so results are deterministic.
 #include "fast_tile.cuh"
 #include "kernels.cuh"
@@ -32,9 +35,9 @@ struct NetSmem {
   // offsets in floats
   static constexpr int kW2f = 0;                                  // forward pairs: [j][i/2] (W2[i][j], W2[i+1][j])
   static constexpr int kW2b = kW2f + H * H;                       // backward pairs: [i][j/2] = W2 row-major
-  static constexpr int kH1 = kW2b + H * H;                        // h1: [j][sample]
-  static constexpr int kV2 = kH1 + H * kNetTile;                  // v2: [i][sample]
-  static constexpr int kW1 = kV2 + H * kNetTile;                  // W1: H x d (d <= 4)
+  static constexpr int kH1 = kW2b + H * H;                        // h1 [j][sample], then v2 [i][sample]
+  static constexpr int kV2 = kH1;
+  static constexpr int kW1 = kH1 + H * kNetTile;                  // W1: H x d (d <= 4)
   static constexpr int kB1 = kW1 + H * 4;
   static constexpr int kB2 = kB1 + H;
   static constexpr int kW3 = kB2 + H;
@@ -48,7 +51,7 @@ struct NetSmem {
 __device__ __forceinline__ u64 dup2(float v) { return pk(v, v); }
 
 template <int D, int H>
-__global__ void __launch_bounds__(kNetThreads)
+__global__ void __launch_bounds__(kNetThreads, 3)
 k_tanh_net_morph(TanhNetArgs net, const float* __restrict__ x0, int64_t N, int T, float eta, float* __restrict__ xT,
                  float* __restrict__ ckpt, int kck) {
   using L = NetSmem<H>;
@@ -80,7 +83,9 @@ k_tanh_net_morph(TanhNetArgs net, const float* __restrict__ x0, int64_t N, int T
     }
     __syncthreads();
     for (int t = 0; t < T; ++t) {
-      // layer 1 (h1 for this thread's 4 samples x UP units)
+      // layer 1 (h1 for this thread's 4 samples x UP units); the thread keeps
+      // 1 - h1^2 of exactly the units whose backward it computes
+      float t1[4][UP];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int s = sg * 4 + q;
@@ -93,7 +98,9 @@ k_tanh_net_morph(TanhNetArgs net, const float* __restrict__ x0, int64_t N, int T
           float a = sm[L::kB1 + i];
 #pragma unroll
           for (int k = 0; k < D; ++k) a = fmaf(sm[L::kW1 + i * D + k], xs[k], a);
-          sm[L::kH1 + i * kNetTile + s] = tanhf(a);
+          const float h = tanhf(a);
+          sm[L::kH1 + i * kNetTile + s] = h;
+          t1[q][u] = fmaf(-h, h, 1.0f);
         }
       }
       __syncthreads();
@@ -122,6 +129,7 @@ k_tanh_net_morph(TanhNetArgs net, const float* __restrict__ x0, int64_t N, int T
 #pragma unroll
           for (int p = 0; p < PP; ++p) acc[q][p] = fma2(w[p], hv[q], acc[q][p]);
       }
+      __syncthreads();   // every thread has read h1 before v2 takes its place
       // h2 = tanh(a2); s partial over this thread's units; v2 = w3 (.) (1 - h2^2)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -178,8 +186,7 @@ k_tanh_net_morph(TanhNetArgs net, const float* __restrict__ x0, int64_t N, int T
 #pragma unroll
           for (int r = 0; r < 2; ++r) {
             const int j = ug * UP + 2 * p + r;
-            const float h = sm[L::kH1 + j * kNetTile + s];
-            const float g = (r ? u1 : u0) * fmaf(-h, h, 1.0f);
+            const float g = (r ? u1 : u0) * t1[q][2 * p + r];
 #pragma unroll
             for (int k = 0; k < D; ++k) gp[k] = fmaf(sm[L::kW1 + j * D + k], g, gp[k]);
           }
