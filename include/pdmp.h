@@ -85,6 +85,12 @@ int32_t pdmp_version(void);
  * code or the flag value. */
 pdmp_status pdmp_stream_status(void* stream, int32_t* detail);
 
+/* Host-side watchdog: waits for the work queued on `stream` so far, polling
+ * an event, for at most timeout_ms milliseconds (>= 0).  PDMP_ERR_TIMEOUT if
+ * the work has not finished by then (it keeps running; call again to keep
+ * waiting); otherwise as pdmp_stream_status. */
+pdmp_status pdmp_stream_wait(void* stream, int32_t timeout_ms, int32_t* detail);
+
 /* ---------------------------------------------------------------------- */
 /* Sec. 3.2 (Eq. 1, "Drawing Samples"): morph a batch of base samples.      */
 /* ---------------------------------------------------------------------- */

@@ -22,7 +22,7 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "PdmpError", "DeviceField", "lib", "morph", "morph_trace", "morph_workspace", "morph_inverse", "log_density", "morph_culled", "morph_culled_workspace", "cull_radius", "DeviceTanhNet", "tanh_net_morph", "cspace_morph", "cspace_workspace",
+    "PdmpError", "DeviceField", "lib", "stream_wait", "morph", "morph_trace", "morph_workspace", "morph_inverse", "log_density", "morph_culled", "morph_culled_workspace", "cull_radius", "DeviceTanhNet", "tanh_net_morph", "cspace_morph", "cspace_workspace",
     "cspace_lipschitz", "chain_struct", "Queue", "Sampler",
     "tanh_net_query", "tanh_net_lipschitz", "morph_vjp", "morph_vjp_workspace", "logdet",
     "occupancy_query", "box_labels", "lipschitz_bound", "fit_occupancy", "fit_workspace", "stream_status", "Batch",
@@ -94,6 +94,7 @@ def lib():
             L.pdmp_version.restype = _i32
             sigs = {
                 "pdmp_stream_status": [_P, ctypes.POINTER(_i32)],
+                "pdmp_stream_wait": [_P, _i32, ctypes.POINTER(_i32)],
                 "pdmp_morph": [_FP, _P, _i64, _i32, _f32, _P, _P, _i32, _P, _sz, _P],
                 "pdmp_morph_trace": [_FP, _P, _i64, _i32, _f32, _P, _P, _P, _sz, _P],
                 "pdmp_morph_vjp": [_FP, _P, _i64, _i32, _f32, _i32, _P, _P, _P, _P, _P, _P, _sz, _P],
@@ -225,6 +226,15 @@ def stream_status():
     st = lib().pdmp_stream_status(_stream(), ctypes.byref(detail))
     return int(st), int(detail.value)
 
+
+
+def stream_wait(timeout_ms: int):
+    """(status, detail): waits at most timeout_ms for the current stream's
+    queued work (host-side watchdog); status PDMP_ERR_TIMEOUT (6) if it is
+    still running, else as stream_status."""
+    d = ctypes.c_int32(0)
+    st = lib().pdmp_stream_wait(_stream(), int(timeout_ms), ctypes.byref(d))
+    return int(st), int(d.value)
 
 def morph_workspace(field: DeviceField, N: int) -> int:
     f = field.struct()
@@ -885,6 +895,43 @@ class Surrogate:
             o += s[0] * s[1]
         out_b = [b[0:H], b[H:2 * H], b[2 * H:3 * H], b[3 * H:3 * H + 3]]
         return out_w, out_b
+
+    def save(self, path: str) -> None:
+        """Writes the network: a one-line JSON header (format, sizes, the
+        normalisation, the Adam step), then the FP32 master weights, biases and
+        Adam moments as raw little-endian float32."""
+        import json
+        import numpy as np
+        head = {"format": "pdmp-surrogate-1", "nw": MLP_NW, "nb": MLP_NB, "enc": MLP_ENC, "hidden": MLP_H,
+                "lo": self.lo, "in_scale": self.in_scale, "out_scale": self.out_scale, "step": self.step}
+        with open(path, "wb") as f:
+            f.write((json.dumps(head) + "\n").encode())
+            for t in (self.W, self.b, self.adam):
+                f.write(t.detach().cpu().numpy().astype("<f4").tobytes())
+
+    @classmethod
+    def load(cls, path: str, device="cuda") -> "Surrogate":
+        """Reads what save() wrote and rebuilds the BF16 copies."""
+        import json
+        import numpy as np
+        with open(path, "rb") as f:
+            head = json.loads(f.readline().decode())
+            raw = np.frombuffer(f.read(), dtype="<f4")
+        if head.get("format") != "pdmp-surrogate-1" or head["nw"] != MLP_NW or head["nb"] != MLP_NB:
+            raise ValueError(f"{path}: not a surrogate of this build ({head.get('format')})")
+        nw, nb = MLP_NW, MLP_NB
+        if raw.size != nw + nb + 2 * nw + 2 * nb:
+            raise ValueError(f"{path}: {raw.size} floats, expected {3 * (nw + nb)}")
+        net = cls.__new__(cls)
+        t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
+        net.W, net.b, net.adam = t(raw[:nw]), t(raw[nw:nw + nb]), t(raw[nw + nb:])
+        net.W_bf16 = torch.empty(MLP_NW, dtype=torch.int16, device=device)
+        net.Wt_bf16 = torch.empty(2 * MLP_H * MLP_H, dtype=torch.int16, device=device)
+        net.lo, net.in_scale, net.out_scale = head["lo"], head["in_scale"], head["out_scale"]
+        net.step = int(head["step"])
+        net._ws = None
+        net.refresh()
+        return net
 
     def bf16_weights(self):
         """The BF16 weights the kernels use, upcast to float64 numpy arrays."""

@@ -3,7 +3,11 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "kernels.cuh"
 
@@ -42,6 +46,12 @@ pdmp_status check_step(const pdmp_field* f, float eta) {
 }
 
 }  // namespace pdmp_host
+
+// an NVTX range around a boundary call (visible to ncu's --nvtx filters)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 static pdmp::FieldArgs field_args(const pdmp_field* f) {
   pdmp::FieldArgs a;
@@ -95,6 +105,36 @@ pdmp_status pdmp_stream_status(void* stream, int32_t* detail) {
   return flag ? PDMP_ERR_DEVICE_FLAG : PDMP_OK;
 }
 
+pdmp_status pdmp_stream_wait(void* stream, int32_t timeout_ms, int32_t* detail) {
+  if (timeout_ms < 0) return PDMP_ERR_INVALID_ARG;
+  cudaStream_t st = as_stream(stream);
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+  if (e != cudaSuccess) {
+    if (ev) cudaEventDestroy(ev);
+    if (detail) *detail = (int32_t)e;
+    return PDMP_ERR_CUDA;
+  }
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  for (;;) {
+    e = cudaEventQuery(ev);
+    if (e != cudaErrorNotReady) break;
+    if (std::chrono::steady_clock::now() >= deadline) {
+      cudaEventDestroy(ev);
+      if (detail) *detail = 0;
+      return PDMP_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) {
+    if (detail) *detail = (int32_t)e;
+    return PDMP_ERR_CUDA;
+  }
+  return pdmp_stream_status(stream, detail);   // the work is done: read and clear the device flag
+}
+
 size_t pdmp_morph_workspace(const pdmp_field* f, int64_t N) {
   if (f == nullptr || check_field(f) != PDMP_OK || N <= 0) return 0;
   return pdmp::morph_workspace(f->kind, f->d, f->M, N);
@@ -112,6 +152,7 @@ static pdmp_status check_ws(const pdmp_field* f, int64_t N, void* ws, size_t ws_
 
 pdmp_status pdmp_morph(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* xT,
                        float* ckpt, int32_t k, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("pdmp_morph");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
@@ -144,6 +185,7 @@ size_t pdmp_cspace_workspace(const pdmp_field* f, const pdmp_chain* chain, int64
 
 pdmp_status pdmp_cspace_morph(const pdmp_field* f, const pdmp_chain* chain, const float* q0, int64_t N, int32_t T,
                               float eta, float* qT, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("pdmp_cspace_morph");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_chain(chain)) != PDMP_OK) return s;
@@ -219,6 +261,7 @@ static pdmp::TanhNetArgs net_args(const pdmp_tanh_net* n) {
 
 pdmp_status pdmp_tanh_net_morph(const pdmp_tanh_net* net, const float* x0, int64_t N, int32_t T, float eta,
                                 float* xT, float* ckpt, int32_t k, void* stream) {
+  NvtxRange nvtx_range("pdmp_tanh_net_morph");
   pdmp_status s = check_net(net);
   if (s != PDMP_OK) return s;
   if (!(eta > 0.0f) || !std::isfinite(eta)) return PDMP_ERR_INVALID_ARG;
@@ -331,6 +374,7 @@ size_t pdmp_morph_culled_workspace(const pdmp_field* f, int64_t N) {
 pdmp_status pdmp_morph_culled(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float r_cut,
                               float* xT, float* ckpt, int32_t k, void* ws, size_t ws_bytes,
                               unsigned long long* work, void* stream) {
+  NvtxRange nvtx_range("pdmp_morph_culled");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if (!cull_field(f)) return PDMP_ERR_UNSUPPORTED;
@@ -384,6 +428,7 @@ pdmp_status pdmp_cull_radius(const pdmp_field* f, float eps, float* r_cut, doubl
 
 pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* traj,
                              float* steps, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("pdmp_morph_trace");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
@@ -399,6 +444,7 @@ pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, in
 
 pdmp_status pdmp_morph_inverse(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, float tol,
                                int32_t maxit, float* y, int32_t* iters, void* stream) {
+  NvtxRange nvtx_range("pdmp_morph_inverse");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
@@ -415,6 +461,7 @@ pdmp_status pdmp_morph_inverse(const pdmp_field* f, const float* z, int64_t N, i
 
 pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, const double* lo,
                              const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* stream) {
+  NvtxRange nvtx_range("pdmp_log_density");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
@@ -440,6 +487,7 @@ size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32
 pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, int32_t k,
                            const float* ckpt, const float* gT, float* g0, float* gw, float* gbias, void* ws,
                            size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("pdmp_morph_vjp");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
@@ -470,6 +518,7 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
 
 pdmp_status pdmp_logdet(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* logdet,
                         float* xT, void* stream) {
+  NvtxRange nvtx_range("pdmp_logdet");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
@@ -481,6 +530,7 @@ pdmp_status pdmp_logdet(const pdmp_field* f, const float* x0, int64_t N, int32_t
 
 pdmp_status pdmp_occupancy_query(const pdmp_field* f, const float* x, int64_t N, float* c, float* s_out, float* grad,
                                  void* stream) {
+  NvtxRange nvtx_range("pdmp_occupancy_query");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if (N < 0) return PDMP_ERR_INVALID_ARG;
@@ -500,6 +550,7 @@ pdmp_status pdmp_box_labels(int32_t d, const float* boxes, int64_t nb, const flo
 
 pdmp_status pdmp_lipschitz_bound(const pdmp_field* f, const double* lo, const double* hi, int32_t cells, double* L,
                                  double* G, void* stream) {
+  NvtxRange nvtx_range("pdmp_lipschitz_bound");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if (L == nullptr) return PDMP_ERR_INVALID_ARG;
@@ -551,6 +602,7 @@ pdmp_status pdmp_batch_prepare(const pdmp_env* envs, int32_t n_envs, int32_t var
 }
 
 pdmp_status pdmp_morph_batched(const pdmp_batch_plan* plan, void* ws, void* stream) {
+  NvtxRange nvtx_range("pdmp_morph_batched");
   if (plan == nullptr || ws == nullptr || !aligned16(ws) || plan->n_envs < 1) return PDMP_ERR_INVALID_ARG;
   if (plan->variant < 0 || plan->variant >= pdmp::batch_variants()) return PDMP_ERR_INVALID_ARG;
   return cuda_status(pdmp::batch_run(plan, ws, as_stream(stream)));
@@ -663,6 +715,7 @@ size_t pdmp_mlp_train_workspace(int32_t B) { return B < 1 ? 0 : pdmp::mlp_train_
 pdmp_status pdmp_mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int32_t B, float lr,
                                 float beta1, float beta2, float eps, int32_t step, float* loss, void* ws,
                                 size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("pdmp_mlp_train_step");
   pdmp_status s = check_mlp(net, true);
   if (s != PDMP_OK) return s;
   if (B < 1 || step < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
@@ -687,6 +740,7 @@ size_t pdmp_surrogate_workspace(const pdmp_field* f, int64_t N) {
 pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const float* x0, int64_t N, int32_t T,
                                  float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, size_t ws_bytes,
                                  void* stream) {
+  NvtxRange nvtx_range("pdmp_surrogate_infer");
   pdmp_status s = check_mlp(net, false);
   if (s != PDMP_OK) return s;
   if ((s = check_field(f)) != PDMP_OK) return s;
@@ -711,6 +765,7 @@ size_t pdmp_fit_workspace(int64_t M, int64_t n) {
 pdmp_status pdmp_fit_occupancy(const pdmp_field* f, const float* X, const uint8_t* y, int64_t n, float l2,
                                int32_t power_iters, int32_t iters, float* w_out, float* bias_out, float* loss_out,
                                float* alpha_out, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("pdmp_fit_occupancy");
   if (f == nullptr) return PDMP_ERR_INVALID_ARG;
   pdmp_field g = *f;
   g.w = w_out;  // the fit ignores f->w; validate the geometry with the output in its place

@@ -234,3 +234,8 @@ def test_fast_paths_reject_sample_counts_past_int32():
     big = (1 << 31) + 5
     assert morph_call(f, N=big, ws=A, ws_bytes=1 << 62) == 1
     assert L.pdmp_morph_culled(ctypes.byref(f), A, big, 4, 0.01, 1.0, A, None, 0, A, 1 << 62, None, None) == 1
+
+
+@nogpu
+def test_stream_wait_rejects_a_negative_timeout():
+    assert pdmp.lib().pdmp_stream_wait(None, -1, None) == 1

@@ -95,3 +95,18 @@ def test_batched_config4_shape_sampled():
         idx = np.arange(0, w.x0.shape[0], 97)
         ref = oracle.morph(w.field, w.x0[idx], T, eta)
         assert np.abs(outs[i].cpu().numpy()[idx] - ref).max() <= 1e-4
+
+
+def test_host_watchdog_times_out_then_completes():
+    """pdmp_stream_wait on a morph that runs for about a second: a 1 ms limit
+    reports a timeout while the kernel keeps running, a long one then sees it
+    finish (nothing faults or hangs: the kernel ends by itself)."""
+    wk = wl.config2(N=1 << 20, M=16384, n_fit=1000)
+    fld = pdmp.DeviceField.from_host(wl.Field(wl.RBF, wk.field.centres, np.full(16384, 0.01, np.float32), gamma=8.0))
+    x0 = torch.from_numpy(wk.x0).cuda()
+    out = pdmp.morph(fld, x0, 300, 1e-4)
+    st, _ = pdmp.stream_wait(1)
+    assert st == 6
+    st, detail = pdmp.stream_wait(120_000)
+    assert st == 0 and detail == 0
+    assert torch.isfinite(out).all()

@@ -123,3 +123,18 @@ def test_surrogate_inference_fallback_is_the_plain_morph():
     if idx.size:
         ref = oracle.morph(wk.field.with_weights(fld.w.cpu().numpy(), bias=fld.bias), x0.cpu().numpy()[idx], T, eta)
         assert np.abs(o[idx] - ref).max() <= 1e-4
+
+
+def test_save_and_load_round_trip(tmp_path):
+    net = pdmp.Surrogate(LO, HI, [0.05, 0.07, 0.03], seed=9)
+    x0 = torch.from_numpy(wl.uniform_box(9, 3, 4096, LO, HI)).cuda()
+    xT = x0 + 0.01
+    for _ in range(3):
+        net.train_step(x0, xT)
+    path = str(tmp_path / "net.bin")
+    net.save(path)
+    other = pdmp.Surrogate.load(path)
+    assert torch.equal(net.forward(x0), other.forward(x0))
+    net.train_step(x0, xT)
+    other.train_step(x0, xT)                 # Adam moments and step restored: the next step agrees
+    assert torch.equal(net.W, other.W) and torch.equal(net.adam, other.adam)
