@@ -560,7 +560,7 @@ def run_reference(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(case: str):
+def profile_case(case: str, reps: int = 1):
     """One small launch of one kernel family (for ncu captures of kernels other
     than the headline one): inputs a few tens of MB, a handful of launches."""
     import torch
@@ -576,13 +576,13 @@ def profile_case(case: str):
         T, k = 4, 2
         ck = torch.empty(T // k, x0.shape[0], 7, device="cuda")
         if case == "rff7d":
-            out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph(f, x0, T, eta, ckpt=ck, k=k), reps=1)
+            out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph(f, x0, T, eta, ckpt=ck, k=k), reps=reps)
         elif case == "vjp":
             pdmp.morph(f, x0, T, eta, ckpt=ck, k=k)
             gT = torch.from_numpy(wk.extra["gT"][:x0.shape[0]]).cuda()
-            out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_vjp(f, x0, T, eta, k, gT, ckpt=ck), reps=1)
+            out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_vjp(f, x0, T, eta, k, gT, ckpt=ck), reps=reps)
         else:
-            out["ms"] = 1e3 * _time(torch, lambda: pdmp.logdet(f, x0, T, eta), reps=1)
+            out["ms"] = 1e3 * _time(torch, lambda: pdmp.logdet(f, x0, T, eta), reps=reps)
     elif case == "culled":
         lo, hi = np.zeros(2), np.full(2, 10.0)
         centres = wl.uniform_box(2, wl.S_CENTRES, M, lo, hi)
@@ -590,12 +590,12 @@ def profile_case(case: str):
         f = pdmp.DeviceField.from_host(wl.Field(wl.RBF, centres, wl.proxy_fitted_weights(2, centres, boxes), gamma=8.0))
         x0 = torch.from_numpy(wl.uniform_box(2, wl.S_SAMPLES, 1 << 18, lo, hi)).cuda()
         r, _ = pdmp.cull_radius(f, 1e-6)
-        out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_culled(f, x0, 3, 4.5e-4, r), reps=1)
+        out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_culled(f, x0, 3, 4.5e-4, r), reps=reps)
     elif case == "tanh":
         net = pdmp.DeviceTanhNet.from_host(wl.tanh_net(7, 2, 64))
         L, _ = pdmp.tanh_net_lipschitz(net)
         x0 = torch.from_numpy(wl.uniform_box(7, wl.S_SAMPLES, 1 << 18, np.zeros(2), np.full(2, 10.0))).cuda()
-        out["ms"] = 1e3 * _time(torch, lambda: pdmp.tanh_net_morph(net, x0, 3, float(np.float32(0.5 / L))), reps=1)
+        out["ms"] = 1e3 * _time(torch, lambda: pdmp.tanh_net_morph(net, x0, 3, float(np.float32(0.5 / L))), reps=reps)
     else:
         raise SystemExit(f"unknown case {case}")
     status, detail = pdmp.stream_status()
@@ -618,9 +618,10 @@ def main():
                     help="small: 262,144 samples and 3 steps of the same workload (for ncu captures)")
     ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "tanh"], default=None,
                     help="run one small launch of that kernel family and exit (for ncu captures)")
+    ap.add_argument("--case-reps", type=int, default=1, help="timed repetitions of --case (best of)")
     args = ap.parse_args()
     if args.case:
-        profile_case(args.case)
+        profile_case(args.case, reps=args.case_reps)
         return
     if args.workload == "small":
         global N, T, WORKLOAD

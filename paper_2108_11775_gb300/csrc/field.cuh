@@ -111,4 +111,30 @@ __device__ __forceinline__ void finish_grad_s(const float* gs, float gamma, floa
   for (int j = 0; j < D; ++j) grad_s[j] = KIND == PDMP_KIND_RBF ? -2.0f * gamma * gs[j] : gs[j];
 }
 
+// log det of the symmetric positive definite D x D matrix whose lower
+// triangle is in a (overwritten by its Cholesky factor); NaN when a pivot is
+// not positive
+template <int D>
+__device__ __forceinline__ float chol_logdet(float (&a)[D][D]) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    float p = a[j][j];
+#pragma unroll
+    for (int q = 0; q < j; ++q) p = fmaf(-a[j][q], a[j][q], p);
+    if (!(p > 0.0f)) return nanf("");
+    float l = sqrtf(p), inv = 1.0f / l;
+    a[j][j] = l;
+    acc += logf(p);
+#pragma unroll
+    for (int i = j + 1; i < D; ++i) {
+      float v = a[i][j];
+#pragma unroll
+      for (int q = 0; q < j; ++q) v = fmaf(-a[i][q], a[j][q], v);
+      a[i][j] = v * inv;
+    }
+  }
+  return acc;
+}
+
 }  // namespace pdmp

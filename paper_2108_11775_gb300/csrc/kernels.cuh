@@ -53,6 +53,9 @@ cudaError_t morph_rbf_cull(int d, const FieldArgs& fa, const float* x0, int64_t 
                            float* xT, float* ckpt, int k, void* ws, unsigned long long* work, cudaStream_t st);
 cudaError_t abs_weight_sum(const float* w, int64_t M, double* out, cudaStream_t st);
 
+cudaError_t logdet_rff7_mma(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld, float* xT,
+                            cudaStream_t st);
+
 cudaError_t uniform_log_density(const float* y, int64_t N, int d, const double* lo, const double* hi, float* lp,
                                 cudaStream_t st);
 

@@ -266,29 +266,6 @@ __global__ void k_sum_rows(const float* __restrict__ rows, int64_t nrows, int64_
 // ------------------------------------------------------------------ log-det
 // Cholesky of the SPD d x d matrix a (row-major, lower triangle used);
 // returns sum log diag(L)^2, or NaN after raising the flag if a pivot <= 0.
-template <int D>
-__device__ __forceinline__ float chol_logdet(float (&a)[D][D]) {
-  float acc = 0.0f;
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    float p = a[j][j];
-#pragma unroll
-    for (int q = 0; q < j; ++q) p = fmaf(-a[j][q], a[j][q], p);
-    if (!(p > 0.0f)) return nanf("");
-    float l = sqrtf(p), inv = 1.0f / l;
-    a[j][j] = l;
-    acc += logf(p);
-#pragma unroll
-    for (int i = j + 1; i < D; ++i) {
-      float v = a[i][j];
-#pragma unroll
-      for (int q = 0; q < j; ++q) v = fmaf(-a[i][q], a[j][q], v);
-      a[i][j] = v * inv;
-    }
-  }
-  return acc;
-}
-
 template <int KIND, int D>
 __global__ void __launch_bounds__(kVjpThreads)
 k_logdet(FieldArgs fa, const float* __restrict__ x0, int64_t N, int T, float eta, float* __restrict__ logdet,
@@ -458,6 +435,7 @@ cudaError_t morph_vjp(int kind, int d, const FieldArgs& fa, const float* x0, int
 
 cudaError_t logdet(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
                    float* xT, cudaStream_t st) {
+  if (kind == PDMP_KIND_RFF && d == 7) return logdet_rff7_mma(fa, x0, N, T, eta, ld, xT, st);
   PDMP_DISPATCH(launch_logdet, fa, x0, N, T, eta, ld, xT, st);
 }
 
