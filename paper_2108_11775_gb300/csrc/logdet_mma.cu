@@ -60,7 +60,7 @@ __device__ __forceinline__ void q_entry(int n, int& a, int& b) {
   b = n - a * (a + 1) / 2;
 }
 
-__global__ void __launch_bounds__(kLdWarps * 32)
+__global__ void __launch_bounds__(kLdWarps * 32, 3)
 k_logdet_rff7_mma(FieldArgs fa, const float* __restrict__ x0, int64_t N, int T, float eta,
                   float* __restrict__ logdet, float* __restrict__ xT) {
   extern __shared__ __align__(16) float sm[];
