@@ -9,7 +9,10 @@
  *            Float arrays are float32, row-major, torch-contiguous: a batch of
  *            N points in d dimensions is N x d with the d coordinates of a point
  *            adjacent.  The caller owns every buffer, including workspaces; the
- *            library allocates no device memory.
+ *            compute calls allocate no device memory.  The exceptions say so:
+ *            pdmp_sampler_create allocates its batch buffers (freed by
+ *            pdmp_sampler_destroy), pdmp_morph_noalloc and the small bound /
+ *            radius reductions use fixed device arrays of the library.
  * Alignment  Every device array must be 16-byte aligned (cudaMalloc and torch
  *            allocations are).  Misaligned pointers give PDMP_ERR_INVALID_ARG.
  * Ordering   Every call is asynchronous on `stream` (a cudaStream_t; NULL is the

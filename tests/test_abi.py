@@ -239,3 +239,14 @@ def test_fast_paths_reject_sample_counts_past_int32():
 @nogpu
 def test_stream_wait_rejects_a_negative_timeout():
     assert pdmp.lib().pdmp_stream_wait(None, -1, None) == 1
+
+
+def test_header_is_plain_c99():
+    """The boundary header compiles as pedantic C99 (no C++ or CUDA types)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    r = subprocess.run(["gcc", "-fsyntax-only", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-x", "c",
+                        HEADER], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
