@@ -43,6 +43,13 @@ __device__ __forceinline__ u64 ex2x2(u64 a) {
 // W = 2..8, unroll 1..4 and 32..128-centre stages); the batched launch picks
 // among a few shapes (autotuned).  Shapes with K > 8 need more than 128
 // registers a thread and run 12 warps per SM, the others 16.
+// The expanded exponent a_m + b_m . u carries a rounding error of about
+// 2^-24 (|a_m| + |b_m . u|) <= 2^-24 3 g' R^2 for the features that matter
+// (those within a few widths of the sample), i.e. a relative error of about
+// 1.4e-6 in each feature at g' R^2 = 8; wider tiles take the direct form.
+#ifndef PDMP_EXPAND_LIMIT
+#define PDMP_EXPAND_LIMIT 8.0f
+#endif
 #ifndef PDMP_WARP_STAGE
 #define PDMP_WARP_STAGE 64
 #endif
@@ -213,7 +220,8 @@ struct TileArgs {
 
 // Bounding box of the tile's active samples (identical in every warp: each
 // warp holds all of them); its centre o is the origin of the expanded form,
-// which the step uses only while g' R^2 <= 4 (R the half-diagonal).
+// which the step uses only while g' R^2 <= PDMP_EXPAND_LIMIT (R the
+// half-diagonal).
 template <int D, int K>
 __device__ __forceinline__ bool tile_frame(const float (&x)[K][D], const bool (&act)[K], float gl2e, float (&lo)[D],
                                            float (&hi)[D], float (&o)[D]) {
@@ -236,7 +244,7 @@ __device__ __forceinline__ bool tile_frame(const float (&x)[K][D], const bool (&
     float h = 0.5f * (hi[j] - lo[j]);
     R2 = fmaf(h, h, R2);
   }
-  const bool expanded = (gl2e * R2 <= 4.0f) && (o[0] == o[0]);
+  const bool expanded = (gl2e * R2 <= PDMP_EXPAND_LIMIT) && (o[0] == o[0]);
   if (!expanded)
 #pragma unroll
     for (int j = 0; j < D; ++j) o[j] = 0.0f;
