@@ -105,7 +105,7 @@ pdmp_status pdmp_stream_wait(void* stream, int32_t timeout_ms, int32_t* detail);
  * ws: NULL, or ws_bytes >= pdmp_morph_workspace(f, N) bytes of caller-owned
  * device scratch.  With a workspace, RBF fields in d = 2 or 3 take the fast
  * path: samples are ordered spatially (a deterministic counting sort on
- * Morton cells) so that each tile of 320 samples is compact, and features are
+ * Hilbert-ordered cells) so that each tile of 320 samples is compact, and features are
  * evaluated in an expanded form about the tile's centre with packed f32x2
  * arithmetic (2d + 1 FP32 operations and one ex2 per feature); RFF fields
  * take a packed-pair path over a table of duplicated records.  The RBF fast

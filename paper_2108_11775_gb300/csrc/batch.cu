@@ -137,18 +137,18 @@ __global__ void k_batch_keys(const BatchEnv* __restrict__ envs, const int64_t* _
   const float cells = (float)(1u << E.bits);
   const uint32_t* b = boxes + 6 * e;
   const float* x = E.x0 + n * E.d;
-  // the Morton code is assembled in a branch per dimension (one code path
+  // the Hilbert index is computed in a branch per dimension (one code path
   // with a dimension chosen at run time inside the loop assembled wrong keys)
   uint32_t key;
   if (E.d == 2) {
-    const uint32_t c0 = cell_coord(x[0], from_ordered(b[0]), from_ordered(b[3]), cells);
-    const uint32_t c1 = cell_coord(x[1], from_ordered(b[1]), from_ordered(b[4]), cells);
-    key = spread2(c0) | (spread2(c1) << 1);
+    uint32_t c[2] = {cell_coord(x[0], from_ordered(b[0]), from_ordered(b[3]), cells),
+                     cell_coord(x[1], from_ordered(b[1]), from_ordered(b[4]), cells)};
+    key = hilbert_key<2>(c, E.bits);
   } else {
-    const uint32_t c0 = cell_coord(x[0], from_ordered(b[0]), from_ordered(b[3]), cells);
-    const uint32_t c1 = cell_coord(x[1], from_ordered(b[1]), from_ordered(b[4]), cells);
-    const uint32_t c2 = cell_coord(x[2], from_ordered(b[2]), from_ordered(b[5]), cells);
-    key = spread3(c0) | (spread3(c1) << 1) | (spread3(c2) << 2);
+    uint32_t c[3] = {cell_coord(x[0], from_ordered(b[0]), from_ordered(b[3]), cells),
+                     cell_coord(x[1], from_ordered(b[1]), from_ordered(b[4]), cells),
+                     cell_coord(x[2], from_ordered(b[2]), from_ordered(b[5]), cells)};
+    key = hilbert_key<3>(c, E.bits);
   }
   key += (uint32_t)E.cell_base;
   keys[g] = key;

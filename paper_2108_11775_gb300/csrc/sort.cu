@@ -1,8 +1,9 @@
 // Spatial ordering of the samples for the fast RBF morph: a counting sort of
-// the samples by the Morton index of their grid cell (over the samples'
+// the samples by the Hilbert index of their grid cell (over the samples'
 // bounding box), made deterministic by ordering each cell's samples by their
 // original index.  Consecutive samples of the resulting permutation are
-// spatially close, which keeps a tile's extent small.
+// spatially close (the Hilbert order never jumps between distant cells),
+// which keeps a tile's extent small.
 #include "kernels.cuh"
 #include "sort.cuh"
 
@@ -43,11 +44,7 @@ __global__ void k_cell_keys(const float* __restrict__ x, int64_t N, const uint32
   uint32_t c[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) c[j] = cell_coord(x[n * D + j], from_ordered(box[j]), from_ordered(box[D + j]), cells);
-  uint32_t key;
-  if (D == 2)
-    key = spread2(c[0]) | (spread2(c[1]) << 1);
-  else
-    key = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[D - 1]) << 2);
+  const uint32_t key = hilbert_key<D>(c, bits);
   keys[n] = key;
   atomicAdd(&counts[key], 1u);
 }

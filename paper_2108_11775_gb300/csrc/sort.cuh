@@ -35,6 +35,44 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
   return v;
 }
 
+// Hilbert index of the cell (c_0 .. c_{n-1}), each coordinate `bits` wide,
+// by Skilling's method ("Programming the Hilbert curve", 2004): the
+// coordinates are turned in place into the transposed index (undoing the
+// curve's reflections and exchanges level by level, then Gray-decoding), whose
+// bits interleaved with c_0 most significant give the index.  Consecutive
+// indices are adjacent cells, so a run of sorted samples never jumps.
+template <int n>
+__device__ __forceinline__ uint32_t hilbert_key(uint32_t (&c)[n], int bits) {
+  const uint32_t top = 1u << (bits - 1);
+  for (uint32_t q = top; q > 1; q >>= 1) {
+    const uint32_t p = q - 1;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      if (c[i] & q) {
+        c[0] ^= p;                        // reflect
+      } else {
+        const uint32_t t = (c[0] ^ c[i]) & p;   // exchange the low bits of c_0 and c_i
+        c[0] ^= t;
+        c[i] ^= t;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 1; i < n; ++i) c[i] ^= c[i - 1];
+  uint32_t t = 0;
+  for (uint32_t q = top; q > 1; q >>= 1)
+    if (c[n - 1] & q) t ^= q - 1;
+#pragma unroll
+  for (int i = 0; i < n; ++i) c[i] ^= t;
+  uint32_t key = 0;
+  if (n == 2) {
+    key = (spread2(c[0]) << 1) | spread2(c[n - 1]);
+  } else {
+    key = (spread3(c[0]) << 2) | (spread3(c[1 % n]) << 1) | spread3(c[n - 1]);
+  }
+  return key;
+}
+
 // cell index in [0, cells) of v along one axis of the box [lo, hi]; NaN and
 // values below lo give 0, values at or above hi give cells - 1
 __device__ __forceinline__ uint32_t cell_coord(float v, float lo, float hi, float cells) {
