@@ -97,7 +97,7 @@ def test_morph_ragged_shapes(kind, d, M, N, T):
 
 @pytest.mark.parametrize("d", [2, 3])
 def test_fast_path_dense_tiles_per_step_and_final(d):
-    """Enough samples that the sorted 256-sample tiles are compact, so the
+    """Enough samples that the sorted 320-sample tiles are compact, so the
     fast kernel runs its expanded form; checked on a subset of the samples."""
     if d == 2:
         f = wl.config1().field
