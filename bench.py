@@ -283,11 +283,13 @@ def run_ours(args, world, rank, local):
         line["cpu_baseline"] = cpu_baseline(wk, fld, eta, target_s=args.cpu_seconds)
     if not args.no_extras and args.workload == "full":
         culled = extra_culled(pdmp, torch, fld, x0, xT, eta)
+        vjp2d = extra_vjp_rbf2d(pdmp, torch, fld, x0, eta, n_sms, pk)
         culled["speedup_vs_dense"] = (float(N) * T * M / achieved) / (culled["ms"] / 1e3)
         del x0, xT, ws, flush
         torch.cuda.empty_cache()
         line["extras"] = {
             "culled_morph": culled,
+            "vjp_rbf2d": vjp2d,
             "tanh_net_cost": extra_tanh_net(pdmp, torch, n_sms, pk),
             "cspace_7link": extra_cspace(pdmp, torch, fld, info),
             "sampler": extra_sampler(pdmp, torch, fld, eta),
@@ -429,6 +431,24 @@ def extra_tanh_net(pdmp, torch, n_sms, pk, d=2, H=64, n=1 << 20, t_steps=50):
     return {"value": rate, "unit": "sample-steps/s", "ms": 1e3 * t, "N": n, "T": t_steps, "d": d, "H": H,
             "macs_per_sample_step": macs, "roofline_frac": rate / peak, "L": L, "eta": eta,
             "note": "FP32 multiply-adds at 128 lanes per SM per clock; tanh not counted"}
+
+
+def extra_vjp_rbf2d(pdmp, torch, fld, x0, eta, n_sms, pk, k=5):
+    """The VJP of the T-step map on the 2-D fitted workload (N = 2^20, T = 50,
+    M = 16,384): checkpoints every k steps from the forward, then the VJP kernel
+    (per segment a recompute pass and a Hessian-vector pass).  The rate counts
+    both passes (2 N T M); the roofline per pass is the forward's 2d + 2 FP32
+    operations per feature, so the fraction is a lower bound (a Hessian-vector
+    feature costs more)."""
+    gT = torch.from_numpy(wl.f32(wl.rng(2, wl.S_COTANGENT).standard_normal((x0.shape[0], D)))).cuda()
+    ck = torch.empty(T // k, x0.shape[0], D, device="cuda")
+    pdmp.morph(fld, x0, T, eta, ckpt=ck, k=k)
+    g0 = torch.empty_like(x0)
+    t = _time(torch, lambda: pdmp.morph_vjp(fld, x0, T, eta, k, gT, ckpt=ck, g0=g0), reps=2)
+    work = 2.0 * x0.shape[0] * T * M
+    peak = alu_peak(n_sms, float(pk.get("sm_max_mhz", 2070.0)))
+    return {"value": work / t, "unit": "feature-evals/s (2 passes)", "ms": 1e3 * t, "k": k,
+            "roofline_frac_vs_forward_count": work / t / peak}
 
 
 def extra_rff(pdmp, torch, n_sms, pk):
