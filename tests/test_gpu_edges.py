@@ -1,0 +1,78 @@
+"""Edge cases of the morph at the limits: very many centres, very many
+samples (sampled against the oracle), and non-finite samples, which must not
+disturb the other samples of their tile."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2108_11775_gb300 as pdmp
+import workloads as wl
+from gpu_util import max_abs, rbf_eta, setup_oracle_threads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available()
+    setup_oracle_threads()
+    yield
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def test_a_million_centres():
+    """M = 2^20 centres on [0,10]^2 (gamma = 64, so a feature is narrow),
+    4096 samples, T = 2: fast and direct paths against the oracle on 48 samples."""
+    M = 1 << 20
+    f = wl.random_field(61, wl.RBF, 2, M, lo=0, hi=10, gamma=64.0, wscale=0.05, bias=-0.5)
+    fld = pdmp.DeviceField.from_host(f)
+    lo, hi = np.zeros(2), np.full(2, 10.0)
+    x0 = wl.uniform_box(61, 3, 4096, lo, hi)
+    eta = 1e-4
+    idx = np.arange(0, 4096, 85)
+    ref = oracle.morph(f, x0[idx], 2, eta)
+    for fast in (True, False):
+        out = pdmp.morph(fld, dev(x0), 2, eta, fast=fast).cpu().numpy()
+        assert max_abs(out[idx], ref) <= 1e-4
+    assert pdmp.stream_status()[0] == 0
+
+
+def test_sixteen_million_samples():
+    """N = 2^24 samples (the largest configuration's sample count), M = 256,
+    T = 3, on the fast path: sampled against the oracle, every output finite."""
+    N = 1 << 24
+    f = wl.random_field(62, wl.RBF, 2, 256, lo=0, hi=10, gamma=4.0, wscale=1.0)
+    eta, L = rbf_eta(f, np.full(2, -0.5), np.full(2, 10.5), cells=32)
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    x0 = wl.uniform_box(62, 3, N, np.zeros(2), np.full(2, 10.0))
+    out = pdmp.morph(fld, dev(x0), 3, eta)
+    assert bool(torch.isfinite(out).all())
+    idx = np.sort(wl.rng(62, 9).choice(N, 256, replace=False))
+    ref = oracle.morph(f, x0[idx], 3, eta)
+    assert max_abs(out.cpu().numpy()[idx], ref) <= 1e-4
+
+
+def test_non_finite_samples_stay_local():
+    """NaN and infinite samples give non-finite outputs and leave every other
+    sample (also those in their tiles) within the tolerance of the oracle."""
+    w1 = wl.config1(N=4096)
+    eta, L = rbf_eta(w1.field, w1.lo, w1.hi)
+    fld = pdmp.DeviceField.from_host(w1.field, lipschitz=L)
+    x0 = w1.x0.copy()
+    bad = np.array([5, 700, 701, 3000])
+    x0[bad[0], 0] = np.nan
+    x0[bad[1], 1] = np.inf
+    x0[bad[2]] = -np.inf
+    x0[bad[3], 0] = np.nan
+    good = np.setdiff1d(np.arange(4096), bad)
+    for fast in (True, False):
+        out = pdmp.morph(fld, dev(x0), w1.T, eta, fast=fast).cpu().numpy()
+        assert not np.isfinite(out[bad]).all(axis=1).any()
+        idx = good[::41]
+        ref = oracle.morph(w1.field, x0[idx], w1.T, eta)
+        assert max_abs(out[idx], ref) <= 1e-4
+        assert np.isfinite(out[good]).all()
