@@ -279,9 +279,10 @@ def run_ours(args, world, rank, local):
         "gpu_launches": args.steps * LAUNCHES_PER_MORPH,
         "wall_s_timed": wall1 - wall0,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    # the oracle baseline and the extras run at N = 1 only (a multi-GPU run times the headline step)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wk, fld, eta, target_s=args.cpu_seconds)
-    if not args.no_extras and args.workload == "full":
+    if world == 1 and not args.no_extras and args.workload == "full":
         culled = extra_culled(pdmp, torch, fld, x0, xT, eta)
         vjp2d = extra_vjp_rbf2d(pdmp, torch, fld, x0, eta, n_sms, pk)
         culled["speedup_vs_dense"] = (float(N) * T * M / achieved) / (culled["ms"] / 1e3)
