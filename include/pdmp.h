@@ -409,8 +409,8 @@ pdmp_status pdmp_morph_culled(const pdmp_field* f, const float* x0, int64_t N, i
 
 /* The smallest r_cut >= 1/sqrt(2 gamma) for which both dropped parts above
  * are at most eps (W computed on the device in FP64; synchronises the
- * stream).  *r_cut receives it (host float, rounded up); *w_abs (may be NULL)
- * receives W. */
+ * stream; calls from several host threads are serialised).  *r_cut
+ * receives it (host float, rounded up); *w_abs (may be NULL) receives W. */
 pdmp_status pdmp_cull_radius(const pdmp_field* f, float eps, float* r_cut, double* w_abs, void* stream);
 
 /* ---------------------------------------------------------------------- */
@@ -480,7 +480,7 @@ pdmp_status pdmp_box_labels(int32_t d, const float* boxes, int64_t nb, const flo
 /* Sec. 3.2: a certified Lipschitz constant of grad c, which sets eta < 1/L. */
 /* ---------------------------------------------------------------------- */
 /* Computed in FP64 on the device, then copied to the host (this call
- * synchronises `stream`).
+ * synchronises `stream`; calls from several host threads are serialised).
  *   |Hess c| <= |Hess s| / 4 + |grad s|^2 / (6 sqrt 3).
  * RBF: |grad phi_m| and |Hess phi_m| are radial functions of r = |x - mu_m|;
  * the box [lo, hi] (host, d doubles each) is cut into cells^d cells, each

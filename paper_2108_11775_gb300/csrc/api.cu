@@ -4,6 +4,7 @@
 #include <cstring>
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -46,6 +47,10 @@ pdmp_status check_step(const pdmp_field* f, float eta) {
 }
 
 }  // namespace pdmp_host
+
+// the bound and radius calls reduce into fixed device slots of the library and
+// synchronise before they return; this lock serialises them across host threads
+static std::mutex g_slot_lock;
 
 // an NVTX range around a boundary call (visible to ncu's --nvtx filters)
 struct NvtxRange {
@@ -401,6 +406,7 @@ pdmp_status pdmp_cull_radius(const pdmp_field* f, float eps, float* r_cut, doubl
   if (f->kind != PDMP_KIND_RBF) return PDMP_ERR_UNSUPPORTED;
   if (!(eps > 0.0f) || !std::isfinite(eps) || r_cut == nullptr) return PDMP_ERR_INVALID_ARG;
   cudaStream_t st = as_stream(stream);
+  std::lock_guard<std::mutex> slot(g_slot_lock);
   double* dsum = nullptr;
   cudaError_t e = cudaGetSymbolAddress((void**)&dsum, pdmp::g_abs_weight_sum);
   if (e == cudaSuccess) e = pdmp::abs_weight_sum(f->w, f->M, dsum, st);
@@ -563,6 +569,7 @@ pdmp_status pdmp_lipschitz_bound(const pdmp_field* f, const double* lo, const do
     }
     if (ncells > (double)(1 << 24)) return PDMP_ERR_INVALID_ARG;
   }
+  std::lock_guard<std::mutex> slot(g_slot_lock);
   return cuda_status(pdmp::lipschitz_bound(f->kind, f->d, field_args(f), lo, hi, cells, L, G, as_stream(stream)));
 }
 

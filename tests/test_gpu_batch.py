@@ -110,3 +110,35 @@ def test_host_watchdog_times_out_then_completes():
     st, detail = pdmp.stream_wait(120_000)
     assert st == 0 and detail == 0
     assert torch.isfinite(out).all()
+
+
+def test_bound_calls_from_several_host_threads():
+    """pdmp_lipschitz_bound and pdmp_cull_radius reduce into fixed device slots;
+    called from four host threads at once they still return each field's own
+    bound (the library serialises them)."""
+    import threading
+    fields = [wl.random_field(70 + i, wl.RBF, 2, 512 * (i + 1), lo=0, hi=10, gamma=4.0, wscale=0.5 + i) for i in range(4)]
+    devs = [pdmp.DeviceField.from_host(f) for f in fields]
+    lo, hi = np.full(2, -0.5), np.full(2, 10.5)
+    serial = [pdmp.lipschitz_bound(d, lo, hi, cells=32) for d in devs]
+    radii = [pdmp.cull_radius(d, 1e-6) for d in devs]
+    out = [None] * 4
+
+    def work(i):
+        torch.cuda.set_device(0)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            res = []
+            for _ in range(20):
+                res.append((pdmp.lipschitz_bound(devs[i], lo, hi, cells=32), pdmp.cull_radius(devs[i], 1e-6)))
+            out[i] = res
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=120)
+    for i in range(4):
+        assert out[i] is not None
+        for lb, rr in out[i]:
+            assert lb == serial[i] and rr == radii[i]
