@@ -284,12 +284,15 @@ def run_ours(args, world, rank, local):
         line["cpu_baseline"] = cpu_baseline(wk, fld, eta, target_s=args.cpu_seconds)
     if world == 1 and not args.no_extras and args.workload == "full":
         culled = extra_culled(pdmp, torch, fld, x0, xT, eta)
+        pdmp.morph(fld, x0, T, eta, out=xT, ws=ws)
+        inverse = extra_inverse(pdmp, torch, fld, x0, xT, eta, n_sms, pk)
         vjp2d = extra_vjp_rbf2d(pdmp, torch, fld, x0, eta, n_sms, pk)
         culled["speedup_vs_dense"] = (float(N) * T * M / achieved) / (culled["ms"] / 1e3)
         del x0, xT, ws, flush
         torch.cuda.empty_cache()
         line["extras"] = {
             "culled_morph": culled,
+            "inverse_2d": inverse,
             "vjp_rbf2d": vjp2d,
             "tanh_net_cost": extra_tanh_net(pdmp, torch, n_sms, pk),
             "cspace_7link": extra_cspace(pdmp, torch, fld, info),
@@ -410,6 +413,42 @@ def extra_culled(pdmp, torch, fld, x0, xT_dense, eta, eps=1e-6):
             "speedup_vs_dense": None, "evaluated_fraction": int(work.item()) / dense,
             "eps": eps, "r_cut": r, "sum_abs_w": W, "max_abs_dev_vs_dense": dev,
             "note": "features farther than r_cut from a tile dropped; s and |grad s| change by at most eps"}
+
+
+def extra_inverse(pdmp, torch, fld, x0, xT, eta, n_sms, pk, n=1 << 18, n_direct=1 << 16, tol=1e-6):
+    """Eq. (2) on the 2-D fitted workload: the first n morphed samples x_T
+    (T = 50) taken back to x_0 by per-step fixed points on sorted tiles.  The
+    rate counts the feature evaluations performed (the kernel's own counter:
+    per block, its iterations summed over the steps times its samples times
+    M), against the forward's FP32 roofline; the direct kernel runs on the
+    first n_direct samples for comparison.  Also the log-density of the same
+    samples (inverse, log-det, uniform base density on the box)."""
+    z = xT[:n].contiguous()
+    ws = torch.empty(pdmp.morph_workspace(fld, n), dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(z)
+    work = torch.zeros(1, dtype=torch.int64, device="cuda")
+    run = lambda: pdmp.morph_inverse(fld, z, T, eta, tol=tol, out=y, ws=ws)
+    run()
+    t = _time(torch, run, reps=2)
+    pdmp.morph_inverse(fld, z, T, eta, tol=tol, out=y, ws=ws, work=work)
+    evals = float(work.item())
+    rt = float((y - x0[:n]).abs().max())
+    zd = xT[:n_direct].contiguous()
+    yd = torch.empty_like(zd)
+    wd = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rund = lambda: pdmp.morph_inverse(fld, zd, T, eta, tol=tol, out=yd, fast=False)
+    rund()
+    td = _time(torch, rund, reps=1)
+    pdmp.morph_inverse(fld, zd, T, eta, tol=tol, out=yd, fast=False, work=wd)
+    peak = alu_peak(n_sms, float(pk.get("sm_max_mhz", 2070.0)))
+    lo, hi = np.zeros(D), np.full(D, 10.0)
+    tl = _time(torch, lambda: pdmp.log_density(fld, z, T, eta, lo, hi, tol=tol, ws=ws), reps=1)
+    return {"value": evals / t, "unit": "feature-evals/s", "ms": 1e3 * t, "N": n, "T": T, "tol": tol,
+            "roofline_frac": evals / t / peak, "sample_steps_per_s": n * T / t,
+            "mean_iterations_per_step": evals / (n * T * M), "round_trip_max_abs": rt,
+            "direct_kernel": {"value": float(wd.item()) / td, "N": n_direct, "ms": 1e3 * td},
+            "log_density": {"samples_per_s": n / tl, "ms": 1e3 * tl},
+            "launches_per_call": 9}
 
 
 def extra_tanh_net(pdmp, torch, n_sms, pk, d=2, H=64, n=1 << 20, t_steps=50):
@@ -612,6 +651,14 @@ def profile_case(case: str, reps: int = 1):
         x0 = torch.from_numpy(wl.uniform_box(2, wl.S_SAMPLES, 1 << 18, lo, hi)).cuda()
         r, _ = pdmp.cull_radius(f, 1e-6)
         out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_culled(f, x0, 3, 4.5e-4, r), reps=reps)
+    elif case == "inverse":
+        lo, hi = np.zeros(2), np.full(2, 10.0)
+        centres = wl.uniform_box(2, wl.S_CENTRES, M, lo, hi)
+        boxes = wl.random_boxes(2, 64, lo, hi, 0.3, 1.5)
+        f = pdmp.DeviceField.from_host(wl.Field(wl.RBF, centres, wl.proxy_fitted_weights(2, centres, boxes), gamma=8.0))
+        x0 = torch.from_numpy(wl.uniform_box(2, wl.S_SAMPLES, 1 << 18, lo, hi)).cuda()
+        z = pdmp.morph(f, x0, 2, 4.5e-4)
+        out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_inverse(f, z, 2, 4.5e-4), reps=reps)
     elif case == "tanh":
         net = pdmp.DeviceTanhNet.from_host(wl.tanh_net(7, 2, 64))
         L, _ = pdmp.tanh_net_lipschitz(net)
@@ -637,7 +684,7 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=1500)
     ap.add_argument("--workload", choices=["full", "small"], default="full",
                     help="small: 262,144 samples and 3 steps of the same workload (for ncu captures)")
-    ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "tanh"], default=None,
+    ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "inverse", "tanh"], default=None,
                     help="run one small launch of that kernel family and exit (for ncu captures)")
     ap.add_argument("--case-reps", type=int, default=1, help="timed repetitions of --case (best of)")
     args = ap.parse_args()

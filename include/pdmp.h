@@ -418,22 +418,33 @@ pdmp_status pdmp_cull_radius(const pdmp_field* f, float eps, float* r_cut, doubl
 /* ---------------------------------------------------------------------- */
 /* y[n] = phi^{-1}(z[n]): the T Euler steps of pdmp_morph are undone last
  * first, each by the fixed point y = z + eta grad c(y) (a contraction when
- * eta L < 1), iterated until every sample of a block of 256 moves by at most
+ * eta L < 1), iterated until every sample of a block moves by at most
  * tol * (1 + |y|) per coordinate, or maxit times.  iters (N, may be NULL)
  * receives, per sample, the largest number of iterations any step of its
- * block used (maxit means the tolerance was not reached).  y may alias z. */
+ * block used (maxit means the tolerance was not reached).  y may alias z.
+ * ws: NULL, or ws_bytes >= pdmp_morph_workspace(f, N) bytes of device
+ * scratch.  With a workspace, RBF fields in d = 2 or 3 run on the forward's
+ * spatially sorted tiles (blocks of 320 samples in Hilbert order, the
+ * expanded exponent about the tile's current centre; N < 2^31); other fields
+ * and ws = NULL use blocks of 256 samples in input order, every feature
+ * evaluated directly.  work (device, 8-byte aligned, may be NULL) is
+ * incremented by the feature evaluations performed (per block, its
+ * iterations summed over the steps times its samples times M). */
 pdmp_status pdmp_morph_inverse(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, float tol,
-                               int32_t maxit, float* y, int32_t* iters, void* stream);
+                               int32_t maxit, float* y, int32_t* iters, void* ws, size_t ws_bytes,
+                               unsigned long long* work, void* stream);
 
 /* Density of the morphed samples (Sec. 3.2, "Drawing Samples", by the
  * change of variables through the T-step map) for a base density uniform on
  * the box [lo, hi] (host arrays of d doubles):
  *   log_p[n] = -log vol(box) - log det J(y[n])   if y[n] lies in the box,
  *            = -inf                                otherwise,
- * with y = phi^{-1}(z) from pdmp_morph_inverse (tol, maxit as there) written
- * to y (N x d, must not alias z) and log det J as pdmp_logdet computes it. */
+ * with y = phi^{-1}(z) from pdmp_morph_inverse (tol, maxit, ws, ws_bytes as
+ * there) written to y (N x d, must not alias z) and log det J as pdmp_logdet
+ * computes it. */
 pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, const double* lo,
-                             const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* stream);
+                             const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* ws,
+                             size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Chain rule through Eq. (1): vector-Jacobian product of the T-step map.   */

@@ -116,8 +116,8 @@ def lib():
                 "pdmp_tanh_net_lipschitz": [ctypes.POINTER(_TanhNet), ctypes.POINTER(_f64), ctypes.POINTER(_f64), _P],
                 "pdmp_morph_culled": [_FP, _P, _i64, _i32, _f32, _f32, _P, _P, _i32, _P, _sz, _P, _P],
                 "pdmp_cull_radius": [_FP, _f32, ctypes.POINTER(_f32), ctypes.POINTER(_f64), _P],
-                "pdmp_morph_inverse": [_FP, _P, _i64, _i32, _f32, _f32, _i32, _P, _P, _P],
-                "pdmp_log_density": [_FP, _P, _i64, _i32, _f32, _P, _P, _f32, _i32, _P, _P, _P],
+                "pdmp_morph_inverse": [_FP, _P, _i64, _i32, _f32, _f32, _i32, _P, _P, _P, _sz, _P, _P],
+                "pdmp_log_density": [_FP, _P, _i64, _i32, _f32, _P, _P, _f32, _i32, _P, _P, _P, _sz, _P],
                 "pdmp_occupancy_query": [_FP, _P, _i64, _P, _P, _P, _P],
                 "pdmp_box_labels": [_i32, _P, _i64, _P, _i64, _P, _P],
                 "pdmp_lipschitz_bound": [_FP, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _i32,
@@ -517,20 +517,26 @@ def morph_culled(field: DeviceField, x0: torch.Tensor, T: int, eta: float, r_cut
 
 
 def morph_inverse(field: DeviceField, z: torch.Tensor, T: int, eta: float, tol: float = 1e-6, maxit: int = 60,
-                  want_iters: bool = False):
-    """Eq. (2): the inverse of the T-step map by per-step fixed points."""
+                  want_iters: bool = False, out: torch.Tensor | None = None, fast: bool = True,
+                  ws: torch.Tensor | None = None, work: torch.Tensor | None = None):
+    """Eq. (2): the inverse of the T-step map by per-step fixed points.
+    ``fast`` gives the library the morph's workspace so that 2-D / 3-D RBF
+    fields run on sorted tiles; ``work`` (int64 CUDA tensor of one element)
+    is incremented by the feature evaluations performed."""
     fn = lib().pdmp_morph_inverse
     N, d = z.shape[0], field.d
-    y = torch.empty_like(z)
+    y = torch.empty_like(z) if out is None else out
     its = torch.empty(N, device=z.device, dtype=torch.int32) if want_iters else None
+    wp, wb, _keep = _workspace(field, N, fast, ws)
     f = field.struct()
     _check(fn(ctypes.byref(f), _ptr(z, shape=(N, d), name="z"), N, int(T), float(eta), float(tol), int(maxit),
-              _ptr(y), _ptr(its, dtype=torch.int32, name="iters"), _stream()), "pdmp_morph_inverse")
+              _ptr(y, shape=(N, d), name="out"), _ptr(its, dtype=torch.int32, name="iters"), wp, wb,
+              _ptr(work, dtype=torch.int64, name="work"), _stream()), "pdmp_morph_inverse")
     return (y, its) if want_iters else y
 
 
 def log_density(field: DeviceField, z: torch.Tensor, T: int, eta: float, lo, hi, tol: float = 1e-6,
-                maxit: int = 60):
+                maxit: int = 60, fast: bool = True, ws: torch.Tensor | None = None):
     """log p_z of morphed samples for a base density uniform on [lo, hi]; returns (log_p, y = phi^{-1}(z))."""
     fn = lib().pdmp_log_density
     N, d = z.shape[0], field.d
@@ -538,9 +544,11 @@ def log_density(field: DeviceField, z: torch.Tensor, T: int, eta: float, lo, hi,
     hi_h = (ctypes.c_double * d)(*[float(v) for v in hi])
     y = torch.empty_like(z)
     lp = torch.empty(N, device=z.device, dtype=torch.float32)
+    wp, wb, _keep = _workspace(field, N, fast, ws)
     f = field.struct()
     _check(fn(ctypes.byref(f), _ptr(z, shape=(N, d), name="z"), N, int(T), float(eta), ctypes.addressof(lo_h),
-              ctypes.addressof(hi_h), float(tol), int(maxit), _ptr(y), _ptr(lp), _stream()), "pdmp_log_density")
+              ctypes.addressof(hi_h), float(tol), int(maxit), _ptr(y), _ptr(lp), wp, wb, _stream()),
+           "pdmp_log_density")
     return lp, y
 
 

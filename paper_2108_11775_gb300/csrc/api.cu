@@ -449,24 +449,29 @@ pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, in
 }
 
 pdmp_status pdmp_morph_inverse(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, float tol,
-                               int32_t maxit, float* y, int32_t* iters, void* stream) {
+                               int32_t maxit, float* y, int32_t* iters, void* ws, size_t ws_bytes,
+                               unsigned long long* work, void* stream) {
   NvtxRange nvtx_range("pdmp_morph_inverse");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
   if ((s = check_step(f, eta)) != PDMP_OK) return s;
   if (N < 0 || T < 0 || maxit < 1 || !(tol >= 0.0f) || !std::isfinite(tol)) return PDMP_ERR_INVALID_ARG;
   if (N == 0) return PDMP_OK;
-  if (!ok_ptr(z, true) || !ok_ptr(y, true) || !ok_ptr(iters, false)) return PDMP_ERR_INVALID_ARG;
+  if (!ok_ptr(z, true) || !ok_ptr(y, true) || !ok_ptr(iters, false) || (reinterpret_cast<uintptr_t>(work) & 7u) != 0)
+    return PDMP_ERR_INVALID_ARG;
+  if ((s = check_ws(f, N, ws, ws_bytes)) != PDMP_OK) return s;
   cudaStream_t st = as_stream(stream);
   if (T == 0) {
     if (y != z) return cuda_status(cudaMemcpyAsync(y, z, sizeof(float) * N * f->d, cudaMemcpyDeviceToDevice, st));
     return PDMP_OK;
   }
-  return cuda_status(pdmp::morph_inverse(f->kind, f->d, field_args(f), z, N, T, eta, tol, maxit, y, iters, st));
+  return cuda_status(
+      pdmp::morph_inverse(f->kind, f->d, field_args(f), z, N, T, eta, tol, maxit, y, iters, ws, work, st));
 }
 
 pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, const double* lo,
-                             const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* stream) {
+                             const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* ws,
+                             size_t ws_bytes, void* stream) {
   NvtxRange nvtx_range("pdmp_log_density");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
@@ -477,7 +482,8 @@ pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int
   if (N == 0) return PDMP_OK;
   if (!ok_ptr(z, true) || !ok_ptr(y, true) || !ok_ptr(log_p, true) || y == z) return PDMP_ERR_INVALID_ARG;
   cudaStream_t st = as_stream(stream);
-  if ((s = pdmp_morph_inverse(f, z, N, T, eta, tol, maxit, y, nullptr, stream)) != PDMP_OK) return s;
+  if ((s = pdmp_morph_inverse(f, z, N, T, eta, tol, maxit, y, nullptr, ws, ws_bytes, nullptr, stream)) != PDMP_OK)
+    return s;
   if ((s = cuda_status(pdmp::logdet(f->kind, f->d, field_args(f), y, N, T, eta, log_p, nullptr, st))) != PDMP_OK)
     return s;
   return cuda_status(pdmp::uniform_log_density(y, N, f->d, lo, hi, log_p, st));

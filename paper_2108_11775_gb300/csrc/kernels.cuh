@@ -12,6 +12,8 @@ cudaError_t morph_direct(int kind, int d, const FieldArgs& fa, const float* x0, 
                          float* xT, float* ckpt, int k, float* traj, float* steps, cudaStream_t st);
 // fast RBF path (d = 2, 3): spatially sorted tiles, expanded exponent, f32x2
 size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N);
+// bytes of the centre table at the start of that workspace (the sort's buffers follow)
+size_t rbf_fast_table_bytes(int d, int64_t M);
 size_t morph_rff_fast_workspace(int d, int64_t M);
 cudaError_t morph_rff_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
                            float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
@@ -34,8 +36,11 @@ size_t morph_workspace(int kind, int d, int64_t M, int64_t N);
 cudaError_t morph_dispatch(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta,
                            float* xT, float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
 
+// ws: NULL (direct kernel) or morph_rbf_fast_workspace bytes (RBF, d = 2, 3: sorted tiles);
+// work (device, may be NULL) is incremented by the feature evaluations performed
 cudaError_t morph_inverse(int kind, int d, const FieldArgs& fa, const float* z, int64_t N, int T, float eta,
-                          float tol, int maxit, float* y, int32_t* iters, cudaStream_t st);
+                          float tol, int maxit, float* y, int32_t* iters, void* ws, unsigned long long* work,
+                          cudaStream_t st);
 
 // the tanh occupancy network of Sec. 3.1 (d -> H -> H -> 1), float32 device arrays
 struct TanhNetArgs {

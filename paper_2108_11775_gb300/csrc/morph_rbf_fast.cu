@@ -36,12 +36,12 @@ k_morph_rbf_fast(TileArgs a) {
 }
 
 // ------------------------------------------------------------------ host
-static size_t table_bytes(int d, int64_t M) {
+size_t rbf_fast_table_bytes(int d, int64_t M) {
   return (((size_t)M * 16 * (d == 2 ? 1 : 2)) + 255) & ~size_t(255);
 }
 
 size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N) {
-  return table_bytes(d, M) + sort_workspace(d, N);
+  return rbf_fast_table_bytes(d, M) + sort_workspace(d, N);
 }
 
 template <int D>
@@ -49,7 +49,7 @@ static cudaError_t launch_fast(const FieldArgs& fa, const float* x0, int64_t N, 
                                float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st,
                                float* s_out, float* g_out = nullptr) {
   float4* tab = reinterpret_cast<float4*>(ws);
-  SortWs sw = sort_layout((char*)ws + table_bytes(D, fa.M), D, N);
+  SortWs sw = sort_layout((char*)ws + rbf_fast_table_bytes(D, fa.M), D, N);
   k_rbf_table<D><<<(unsigned)((fa.M + 255) / 256), 256, 0, st>>>(fa.centres, fa.w, fa.M, tab);
   cudaError_t e = spatial_sort(D, x0, N, sw, st);
   if (e != cudaSuccess) return e;

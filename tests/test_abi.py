@@ -153,14 +153,19 @@ def test_inverse_validation():
     L = pdmp.lib()
     fn = L.pdmp_morph_inverse
     f = ctypes.byref(fld())
-    assert fn(f, A, 8, 4, 0.01, 1e-6, 0, A, None, None) == 1            # maxit < 1
-    assert fn(f, A, 8, 4, 0.01, -1.0, 10, A, None, None) == 1           # negative tolerance
-    assert fn(f, A, 8, 4, 0.01, float("nan"), 10, A, None, None) == 1
-    assert fn(f, MIS, 8, 4, 0.01, 1e-6, 10, A, None, None) == 1
-    assert fn(f, A, 8, 4, 0.01, 1e-6, 10, A, MIS + 1, None) == 1       # iters not 4-byte aligned
-    assert fn(f, A, -1, 4, 0.01, 1e-6, 10, A, None, None) == 1
-    assert fn(f, None, 0, 4, 0.01, 1e-6, 10, None, None, None) == 0      # empty batch
-    assert fn(ctypes.byref(fld(lipschitz=100.0)), A, 8, 4, 0.5, 1e-6, 10, A, None, None) == 2
+    need = L.pdmp_morph_workspace(f, 8)
+    assert need > 0
+    assert fn(f, A, 8, 4, 0.01, 1e-6, 0, A, None, None, 0, None, None) == 1            # maxit < 1
+    assert fn(f, A, 8, 4, 0.01, -1.0, 10, A, None, None, 0, None, None) == 1           # negative tolerance
+    assert fn(f, A, 8, 4, 0.01, float("nan"), 10, A, None, None, 0, None, None) == 1
+    assert fn(f, MIS, 8, 4, 0.01, 1e-6, 10, A, None, None, 0, None, None) == 1
+    assert fn(f, A, 8, 4, 0.01, 1e-6, 10, A, MIS + 1, None, 0, None, None) == 1       # iters not 4-byte aligned
+    assert fn(f, A, -1, 4, 0.01, 1e-6, 10, A, None, None, 0, None, None) == 1
+    assert fn(f, A, 8, 4, 0.01, 1e-6, 10, A, None, A + 8192, need - 1, None, None) == 3   # workspace too small
+    assert fn(f, A, 8, 4, 0.01, 1e-6, 10, A, None, MIS, need, None, None) == 1         # workspace misaligned
+    assert fn(f, A, 8, 4, 0.01, 1e-6, 10, A, None, None, 0, A + 4, None) == 1          # work not 8-byte aligned
+    assert fn(f, None, 0, 4, 0.01, 1e-6, 10, None, None, None, 0, None, None) == 0      # empty batch
+    assert fn(ctypes.byref(fld(lipschitz=100.0)), A, 8, 4, 0.5, 1e-6, 10, A, None, None, 0, None, None) == 2
 
 
 @nogpu
@@ -170,12 +175,14 @@ def test_log_density_validation():
     hi = (ctypes.c_double * 2)(10, 10)
     flat = (ctypes.c_double * 2)(10, 0)
     f = ctypes.byref(fld())
+    need = pdmp.lib().pdmp_morph_workspace(f, 8)
     P = lambda a: ctypes.cast(a, ctypes.POINTER(ctypes.c_double))
-    assert fn(f, A, 8, 4, 0.01, P(lo), P(flat), 1e-6, 10, A + 4096, A, None) == 1     # empty box
-    assert fn(f, A, 8, 4, 0.01, None, P(hi), 1e-6, 10, A + 4096, A, None) == 1
-    assert fn(f, A, 8, 4, 0.01, P(lo), P(hi), 1e-6, 10, A, A + 4096, None) == 1       # y aliases z
-    assert fn(f, A, 8, 4, 0.01, P(lo), P(hi), 1e-6, 0, A + 4096, A + 8192, None) == 1
-    assert fn(f, None, 0, 4, 0.01, P(lo), P(hi), 1e-6, 10, None, None, None) == 0
+    assert fn(f, A, 8, 4, 0.01, P(lo), P(flat), 1e-6, 10, A + 4096, A, None, 0, None) == 1     # empty box
+    assert fn(f, A, 8, 4, 0.01, None, P(hi), 1e-6, 10, A + 4096, A, None, 0, None) == 1
+    assert fn(f, A, 8, 4, 0.01, P(lo), P(hi), 1e-6, 10, A, A + 4096, None, 0, None) == 1       # y aliases z
+    assert fn(f, A, 8, 4, 0.01, P(lo), P(hi), 1e-6, 0, A + 4096, A + 8192, None, 0, None) == 1
+    assert fn(f, A, 8, 4, 0.01, P(lo), P(hi), 1e-6, 10, A + 4096, A + 8192, A + 16384, need - 1, None) == 3
+    assert fn(f, None, 0, 4, 0.01, P(lo), P(hi), 1e-6, 10, None, None, None, 0, None) == 0
 
 
 @nogpu

@@ -368,17 +368,66 @@ def test_fit_full_size_2d_learns_the_boxes():
 # --------------------------------------------------------------------------
 # Eq. (2): the inverse map
 @pytest.mark.parametrize("kind", [wl.RBF, wl.RFF])
-def test_inverse_matches_oracle_and_round_trips(kind):
+@pytest.mark.parametrize("fast", [True, False])
+def test_inverse_matches_oracle_and_round_trips(kind, fast):
     f, x0, T, _, eta = _vjp_case(kind)
     fld = pdmp.DeviceField.from_host(f)
     z = pdmp.morph(fld, dev(x0), T, eta)
-    y, its = pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=80, want_iters=True)
+    y, its = pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=80, want_iters=True, fast=fast)
     y, its, z = y.cpu().numpy(), its.cpu().numpy(), z.cpu().numpy()
     ref, _ = oracle.morph_inverse(f, z, T, eta, tol=1e-13, maxit=200)
     assert max_abs(y, ref) <= 1e-4
     assert max_abs(y, x0) <= 1e-4                      # round trip through the forward map
     assert its.max() < 80
     assert np.abs(z - x0).max() > 1e-3
+
+
+@pytest.mark.parametrize("d,N", [(2, 1000), (3, 1000), (3, 321)])
+def test_inverse_sorted_tiles_ragged_in_place_and_work(d, N):
+    """The sorted-tile inverse (RBF, d = 2, 3): ragged tiles, in place, the
+    work counter, and agreement with the direct kernel and the oracle."""
+    f = wl.random_field(40 + d, wl.RBF, d, 700, lo=0.0, hi=5.0, gamma=4.0, wscale=1.5)
+    lo, hi = np.zeros(d), np.full(d, 5.0)
+    eta, _ = rbf_eta(f, lo - 0.5, hi + 0.5, cells=32 if d == 2 else 12)
+    T = 8
+    x0 = wl.uniform_box(41 + d, 3, N, lo, hi)
+    fld = pdmp.DeviceField.from_host(f)
+    z = pdmp.morph(fld, dev(x0), T, eta)
+    zc = z.clone()
+    work = torch.zeros(1, dtype=torch.int64, device="cuda")
+    y, its = pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=60, want_iters=True, out=z, work=work)
+    assert y.data_ptr() == z.data_ptr()
+    y, its = y.cpu().numpy(), its.cpu().numpy()
+    ref, _ = oracle.morph_inverse(f, zc.cpu().numpy(), T, eta, tol=1e-13, maxit=200)
+    assert max_abs(y, ref) <= 1e-4
+    assert max_abs(y, x0) <= 1e-4
+    assert 1 <= its.min() and its.max() < 60
+    wv = int(work.item())
+    assert wv % f.M == 0 and T * N * f.M <= wv <= T * 60 * N * f.M
+    yd = pdmp.morph_inverse(fld, zc, T, eta, tol=1e-6, maxit=60, fast=False).cpu().numpy()
+    assert max_abs(y, yd) <= 1e-4
+    assert np.abs(zc.cpu().numpy() - x0).max() > 1e-3
+
+
+def test_inverse_fitted_2d_sampled_at_the_bench_size():
+    """The inverse as the benchmark runs it: the first 2^18 samples of the
+    2-D fitted workload morphed through T = 50 steps, then inverted on sorted
+    tiles; sampled samples against the oracle's inverse and the round trip."""
+    wk = wl.config2()
+    f = wk.field.with_weights(wl.proxy_fitted_weights(2, wk.field.centres, wk.boxes))
+    eta, L = rbf_eta(f, wk.lo - 0.5, wk.hi + 0.5, cells=96)
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    n = 1 << 18
+    x0 = np.ascontiguousarray(wk.x0[:n])
+    z = pdmp.morph(fld, dev(x0), wk.T, eta)
+    work = torch.zeros(1, dtype=torch.int64, device="cuda")
+    y = pdmp.morph_inverse(fld, z, wk.T, eta, tol=1e-6, maxit=60, work=work).cpu().numpy()
+    assert np.isfinite(y).all()
+    assert max_abs(y, x0) <= 1e-4
+    idx = np.concatenate([np.sort(wl.rng(9, 1).choice(n, 24, replace=False)), [0, n - 1]])
+    ref, _ = oracle.morph_inverse(f, z.cpu().numpy()[idx], wk.T, eta, tol=1e-13, maxit=200)
+    assert max_abs(y[idx], ref) <= 1e-4
+    assert int(work.item()) >= n * wk.T * f.M
 
 
 def test_log_density_matches_oracle_and_integrates_to_one():
