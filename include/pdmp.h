@@ -108,11 +108,14 @@ pdmp_status pdmp_stream_wait(void* stream, int32_t timeout_ms, int32_t* detail);
  * Hilbert-ordered cells) so that each tile of 320 samples is compact, and features are
  * evaluated in an expanded form about the tile's centre with packed f32x2
  * arithmetic (2d + 1 FP32 operations and one ex2 per feature); RFF fields
- * take a packed-pair path over a table of duplicated records.  The RBF fast
+ * with d <= 7 put both contractions of a step, theta = omega . x + b and
+ * sum_m w_m sin(theta_m) omega_m, on the tensor cores (TF32 with hi/lo
+ * splits) and d = 8 takes a packed-pair path.  The RBF fast
  * path needs N < 2^31 (PDMP_ERR_INVALID_ARG otherwise).  Without a
  * workspace every feature is evaluated directly from x - mu (RBF) or
  * omega . x + b (RFF).
- * Sample state lives in registers for all T steps; features are evaluated in
+ * Sample state stays on chip (registers or shared memory) for all T steps;
+ * features are evaluated in
  * FP32 with exp2 / sin / cos on the special-function unit.  Calls that share
  * a workspace must not overlap on the GPU. */
 size_t pdmp_morph_workspace(const pdmp_field* f, int64_t N);

@@ -31,6 +31,25 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
+// TF32 tensor-core pieces: round to TF32 (nearest, ties away), and
+// D += A B for one m16n8k8 tile (A row-major 16 x 8, B column-major 8 x 8, FP32
+// accumulate).  Fragments: with g = lane / 4 and t = lane % 4, a0 = A[g][t],
+// a1 = A[g + 8][t], a2 = A[g][t + 4], a3 = A[g + 8][t + 4]; b0 = B[t][g],
+// b1 = B[t + 4][g]; d0 = D[g][2t], d1 = D[g][2t + 1], d2 = D[g + 8][2t],
+// d3 = D[g + 8][2t + 1].
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ u64 ex2x2(u64 a) {
   float lo, hi;
   upk(a, lo, hi);

@@ -15,6 +15,10 @@ size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N);
 // bytes of the centre table at the start of that workspace (the sort's buffers follow)
 size_t rbf_fast_table_bytes(int d, int64_t M);
 size_t morph_rff_fast_workspace(int d, int64_t M);
+// RFF with both contractions on the tensor cores (d = 1 .. 7)
+size_t morph_rff_mma_workspace(int64_t M);
+cudaError_t morph_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
+                          float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
 cudaError_t morph_rff_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
                            float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st);
 // grad c at N points by the fast RBF tile kernel (ws: morph_rbf_fast_workspace)

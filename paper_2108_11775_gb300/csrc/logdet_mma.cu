@@ -39,19 +39,6 @@ struct LdSmem {
   static constexpr size_t bytes() { return (size_t)kEnd * 4; }
 };
 
-__device__ __forceinline__ uint32_t ld_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void ld_mma(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                       uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 // the lower-triangle entry (a, b) of column n = a (a + 1) / 2 + b (0..27)
 __device__ __forceinline__ void q_entry(int n, int& a, int& b) {
   a = (int)((sqrtf(8.0f * n + 1.0f) - 1.0f) * 0.5f);
@@ -154,8 +141,8 @@ k_logdet_rff7_mma(FieldArgs fa, const float* __restrict__ x0, int64_t N, int T, 
             p0 = r0[qa[nt]] * r0[qb[nt]];
             p1 = r1[qa[nt]] * r1[qb[nt]];
           }
-          const uint32_t p0h = ld_tf32(p0), p1h = ld_tf32(p1);
-          fr[nt] = make_uint4(p0h, p1h, ld_tf32(p0 - __uint_as_float(p0h)), ld_tf32(p1 - __uint_as_float(p1h)));
+          const uint32_t p0h = tf32_rna(p0), p1h = tf32_rna(p1);
+          fr[nt] = make_uint4(p0h, p1h, tf32_rna(p0 - __uint_as_float(p0h)), tf32_rna(p1 - __uint_as_float(p1h)));
         }
 #pragma unroll
         for (int r = 0; r < kLdRows; ++r) {
@@ -176,14 +163,14 @@ k_logdet_rff7_mma(FieldArgs fa, const float* __restrict__ x0, int64_t N, int T, 
               for (int j = 0; j < kLdD; ++j) G[r][h][j] = fmaf(gsn, om[q][j], G[r][h][j]);
             }
           // A fragment: a0 (row g, k t), a1 (row g + 8, k t), a2 (row g, k t + 4), a3 (row g + 8, k t + 4)
-          const uint32_t h0 = ld_tf32(c[0][0]), h1 = ld_tf32(c[1][0]), h2 = ld_tf32(c[0][1]), h3 = ld_tf32(c[1][1]);
-          const uint32_t l0 = ld_tf32(c[0][0] - __uint_as_float(h0)), l1 = ld_tf32(c[1][0] - __uint_as_float(h1));
-          const uint32_t l2 = ld_tf32(c[0][1] - __uint_as_float(h2)), l3 = ld_tf32(c[1][1] - __uint_as_float(h3));
+          const uint32_t h0 = tf32_rna(c[0][0]), h1 = tf32_rna(c[1][0]), h2 = tf32_rna(c[0][1]), h3 = tf32_rna(c[1][1]);
+          const uint32_t l0 = tf32_rna(c[0][0] - __uint_as_float(h0)), l1 = tf32_rna(c[1][0] - __uint_as_float(h1));
+          const uint32_t l2 = tf32_rna(c[0][1] - __uint_as_float(h2)), l3 = tf32_rna(c[1][1] - __uint_as_float(h3));
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt) {
-            ld_mma(acc[r][nt], h0, h1, h2, h3, fr[nt].x, fr[nt].y);   // hi x hi
-            ld_mma(acc[r][nt], h0, h1, h2, h3, fr[nt].z, fr[nt].w);   // hi x lo
-            ld_mma(acc[r][nt], l0, l1, l2, l3, fr[nt].x, fr[nt].y);   // lo x hi
+            mma_tf32(acc[r][nt], h0, h1, h2, h3, fr[nt].x, fr[nt].y);   // hi x hi
+            mma_tf32(acc[r][nt], h0, h1, h2, h3, fr[nt].z, fr[nt].w);   // hi x lo
+            mma_tf32(acc[r][nt], l0, l1, l2, l3, fr[nt].x, fr[nt].y);   // lo x hi
           }
         }
       }

@@ -133,17 +133,28 @@ cudaError_t morph_direct(int kind, int d, const FieldArgs& fa, const float* x0, 
 
 namespace pdmp {
 // Chooses the kernel for a morph request.
+// RFF fields with d <= 7 take the tensor-core kernel (1.10x the packed-pair
+// kernel at d = 1, 1.55x at d = 7, measured on 2^20 samples, M = 4096);
+// d = 8 (eight dimensions and the phase do not fit its eight k slots) the
+// packed-pair one.
+static bool rff_mma(int d) { return d <= 7; }
+
 size_t morph_workspace(int kind, int d, int64_t M, int64_t N) {
   if (kind == PDMP_KIND_RBF && (d == 2 || d == 3) && N > 0) return morph_rbf_fast_workspace(d, M, N);
-  if (kind == PDMP_KIND_RFF && N > 0) return morph_rff_fast_workspace(d, M);
+  if (kind == PDMP_KIND_RFF && N > 0) {
+    const size_t a = morph_rff_fast_workspace(d, M), b = rff_mma(d) ? morph_rff_mma_workspace(M) : 0;
+    return a > b ? a : b;
+  }
   return 0;
 }
 
 cudaError_t morph_dispatch(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta,
                            float* xT, float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st) {
-  if (ws != nullptr && morph_workspace(kind, d, fa.M, N) > 0)
-    return kind == PDMP_KIND_RBF ? morph_rbf_fast(d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st)
-                                 : morph_rff_fast(d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
+  if (ws != nullptr && morph_workspace(kind, d, fa.M, N) > 0) {
+    if (kind == PDMP_KIND_RBF) return morph_rbf_fast(d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
+    if (rff_mma(d)) return morph_rff_mma(d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
+    return morph_rff_fast(d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
+  }
   return morph_direct(kind, d, fa, x0, N, T, eta, xT, ckpt, k, traj, steps, st);
 }
 }  // namespace pdmp

@@ -96,7 +96,13 @@ def test_morph_workspace_size_and_checks():
     f = fld()
     need = L.pdmp_morph_workspace(ctypes.byref(f), 1 << 20)
     assert need > (1 << 20) * 8                       # keys + permutation at least
-    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, phase=A)), 1 << 20) == 16 * 80   # RFF: pair table
+    # RFF, d = 8: the pair table (M records of 11 u64 pairs, padded to 16 bytes, 256 in all)
+    pair8 = L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=8, phase=A)), 1 << 20)
+    assert pair8 == (16 * 12 * 8 + 255) // 256 * 256
+    # RFF, d <= 7: the tensor-core table (k tiles of 8 features, 264 floats each, in whole stages of 16)
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, phase=A)), 1 << 20) == 16 * 264 * 4
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=3, phase=A)), 1 << 20) == 16 * 264 * 4
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, M=129, phase=A)), 1) == 32 * 264 * 4
     assert L.pdmp_morph_workspace(ctypes.byref(fld(d=1)), 1000) == 0
     assert morph_call(f, N=1 << 20, ws=A, ws_bytes=need - 1) == 3
     assert morph_call(f, N=1 << 20, ws=MIS, ws_bytes=need) == 1

@@ -75,7 +75,8 @@ def test_morph_config1_per_step_and_final(fast):
 @pytest.mark.parametrize("kind,d,M,N,T", [
     (wl.RBF, 1, 7, 37, 5), (wl.RBF, 2, 1, 1, 4), (wl.RBF, 2, 300, 1000, 6), (wl.RBF, 3, 513, 777, 5),
     (wl.RBF, 2, 257, 513, 3), (wl.RFF, 1, 33, 100, 5), (wl.RFF, 3, 129, 301, 4), (wl.RFF, 7, 300, 257, 5),
-    (wl.RFF, 8, 64, 65, 3),
+    (wl.RFF, 8, 64, 65, 3), (wl.RFF, 4, 17, 130, 3), (wl.RFF, 5, 1000, 700, 4), (wl.RFF, 6, 129, 128, 4),
+    (wl.RFF, 7, 2048, 1, 3),
 ])
 def test_morph_ragged_shapes(kind, d, M, N, T):
     if kind == wl.RBF:
