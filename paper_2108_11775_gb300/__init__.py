@@ -558,19 +558,30 @@ def morph_vjp_workspace(field: DeviceField, N: int, T: int, k: int, want_param_g
 
 
 def morph_vjp(field: DeviceField, x0: torch.Tensor, T: int, eta: float, k: int, gT: torch.Tensor,
-              ckpt: torch.Tensor | None = None, want_param_grad: bool = False, g0: torch.Tensor | None = None):
+              ckpt: torch.Tensor | None = None, want_param_grad: bool = False, g0: torch.Tensor | None = None,
+              fast: bool = True, ws: torch.Tensor | None = None):
     """g0 = (dx_T/dx_0)^T gT per sample; with want_param_grad also (gw, gbias)
-    = d/d(w, bias) of sum_n <gT[n], x_T[n]>."""
+    = d/d(w, bias) of sum_n <gT[n], x_T[n]>.  Without the parameter gradient,
+    ``fast`` gives the library a workspace (``ws`` or a fresh one) so that RFF
+    fields with d <= 7 and k <= 16 run on the tensor cores."""
     N, d = x0.shape[0], field.d
     if g0 is None:
         g0 = torch.empty_like(x0)
-    gw = gb = ws = None
+    gw = gb = None
     nbytes = 0
     if want_param_grad:
         gw = torch.empty(field.M, device=x0.device, dtype=torch.float32)
         gb = torch.empty(1, device=x0.device, dtype=torch.float32)
         nbytes = morph_vjp_workspace(field, N, T, k, True)
         ws = torch.empty(max(nbytes, 16), device=x0.device, dtype=torch.uint8)
+    elif fast:
+        nbytes = morph_vjp_workspace(field, N, T, k, False)
+        if nbytes == 0:
+            ws = None
+        elif ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, device=x0.device, dtype=torch.uint8)
+    else:
+        ws = None
     f = field.struct()
     st = lib().pdmp_morph_vjp(ctypes.byref(f), _ptr(x0, shape=(N, d), name="x0"), N, int(T), float(eta), int(k),
                               _ptr(ckpt, shape=(T // k, N, d), name="ckpt") if ckpt is not None else None,

@@ -489,11 +489,16 @@ pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int
   return cuda_status(pdmp::uniform_log_density(y, N, f->d, lo, hi, log_p, st));
 }
 
+// the tensor-core VJP: RFF fields with d <= 7, segments of at most 16 steps, no parameter gradient
+static bool vjp_mma_eligible(const pdmp_field* f, int32_t k) {
+  return f->kind == PDMP_KIND_RFF && f->d <= 7 && k >= 1 && k <= pdmp::kVjpMmaMaxSegment;
+}
+
 size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32_t k, int32_t want_param_grad) {
   (void)T;
-  (void)k;
-  if (f == nullptr || !want_param_grad || N <= 0 || f->M < 1) return 0;
-  return sizeof(float) * (size_t)pdmp::vjp_blocks(N) * (size_t)(f->M + 1);
+  if (f == nullptr || N <= 0 || f->M < 1) return 0;
+  if (want_param_grad) return sizeof(float) * (size_t)pdmp::vjp_blocks(N) * (size_t)(f->M + 1);
+  return vjp_mma_eligible(f, k) ? pdmp::morph_rff_mma_workspace(f->M) : 0;
 }
 
 pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, int32_t k,
@@ -510,6 +515,9 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
     size_t need = pdmp_morph_vjp_workspace(f, N, T, k, 1);
     if (need > 0 && (ws == nullptr || !aligned16(ws))) return PDMP_ERR_INVALID_ARG;
     if (ws_bytes < need) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  } else if (ws != nullptr) {
+    if (!aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+    if (ws_bytes < pdmp_morph_vjp_workspace(f, N, T, k, 0)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
   }
   cudaStream_t st = as_stream(stream);
   if (N > 0) {
@@ -524,6 +532,8 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
     if (gbias) cudaMemsetAsync(gbias, 0, sizeof(float), st);
     return launch_status();
   }
+  if (!want && ws != nullptr && N > 0 && vjp_mma_eligible(f, k))
+    return cuda_status(pdmp::vjp_rff_mma(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, ws, st));
   return cuda_status(pdmp::morph_vjp(f->kind, f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0,
                                      want ? (float*)ws : nullptr, gw, gbias, st));
 }

@@ -69,6 +69,10 @@ cudaError_t uniform_log_density(const float* y, int64_t N, int d, const double* 
                                 cudaStream_t st);
 
 int64_t vjp_blocks(int64_t N);
+// the tensor-core VJP for RFF fields (d <= 7, segments k <= kVjpMmaMaxSegment; ws: morph_rff_mma_workspace)
+constexpr int kVjpMmaMaxSegment = 16;
+cudaError_t vjp_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
+                        const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st);
 cudaError_t morph_vjp(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                       const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias,
                       cudaStream_t st);

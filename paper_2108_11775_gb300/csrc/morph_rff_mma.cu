@@ -104,6 +104,197 @@ __device__ __forceinline__ u64 rm_turns_to_rad(u64 tau) {
   return mul2(fma2(r, mone, tau), twopi);         // the difference is exact
 }
 
+// A fragments (hi, lo) of the warp's 32 rows of a [32][8] state array.
+__device__ __forceinline__ void rm_frags(const float* xs, int g, int t, uint32_t (&ah)[kRmRows][4],
+                                         uint32_t (&al)[kRmRows][4]) {
+#pragma unroll
+  for (int r = 0; r < kRmRows; ++r) {
+    const float* xr = xs + r * 16 * 8;
+    const float v[4] = {xr[g * 8 + t], xr[(g + 8) * 8 + t], xr[g * 8 + t + 4], xr[(g + 8) * 8 + t + 4]};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ah[r][q] = tf32_rna(v[q]);
+      al[r][q] = tf32_rna(v[q] - __uint_as_float(ah[r][q]));
+    }
+  }
+}
+
+// Veltkamp's split of a packed pair with the constant 2^13 + 1: hi keeps
+// 24 - 13 = 11 significant bits (an exact TF32 value, for any magnitude),
+// lo = a - hi exactly.
+__device__ __forceinline__ void rm_split(u64 a, u64& hi, u64& lo) {
+  const u64 c = pk(8193.0f, 8193.0f), mone = pk(-1.0f, -1.0f);
+  const u64 gm = mul2(a, c);
+  hi = fma2(fma2(a, mone, gm), mone, gm);   // gm - (gm - a)
+  lo = fma2(hi, mone, a);
+}
+
+// One pass over all features for the warp's 32 samples.  In:
+// A fragments of [x, 1] (ah, al) and, with HVP, of [v, 0] (vh, vl).  Out:
+// S (packed partial logits: row g / g + 8, features 2t / 2t + 1), G (D
+// fragments of grad s) and, with HVP, P (D fragments of
+// sum_m cos(theta_m) (omega_m . v / 2 pi) (-w_m omega_m) = (Hess s) v / 2 pi).
+// Block-wide: every warp of the block makes the same sequence of passes.
+template <bool HVP>
+__device__ __forceinline__ void rm_sweep(const float* __restrict__ tab, int nstage, float* sm,
+                                         const uint32_t (&ah)[kRmRows][4], const uint32_t (&al)[kRmRows][4],
+                                         const uint32_t (&vh)[kRmRows][4], const uint32_t (&vl)[kRmRows][4],
+                                         u64 (&S)[kRmRows][2], float (&G)[kRmRows][4], float (&P)[kRmRows][4]) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+#pragma unroll
+  for (int r = 0; r < kRmRows; ++r) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) G[r][q] = P[r][q] = 0.0f;
+    S[r][0] = S[r][1] = 0ull;
+  }
+  __syncthreads();   // every warp is done with the previous pass's stages
+  rm_stage_load(tab, sm);
+  for (int st = 0; st < nstage; ++st) {
+    cp_async_wait_all();
+    __syncthreads();   // stage st is visible; stage st - 1's buffer is free
+    if (st + 1 < nstage)
+      rm_stage_load(tab + (size_t)(st + 1) * kRmStageFloats, sm + ((st + 1) & 1) * kRmStageFloats);
+    const float* sb = sm + (st & 1) * kRmStageFloats;
+#pragma unroll kRmUnroll
+    for (int kt = 0; kt < kRmStageKT; ++kt) {
+      const float* rec = sb + kt * kRmKtFloats;
+      const float4 bt = reinterpret_cast<const float4*>(rec)[lane];
+      const float4 bg = reinterpret_cast<const float4*>(rec + 128)[lane];
+      const u64 wp = reinterpret_cast<const u64*>(rec + 256)[t];   // w of features 2t, 2t + 1
+      const uint32_t bth0 = __float_as_uint(bt.x), bth1 = __float_as_uint(bt.y);
+      const uint32_t btl0 = __float_as_uint(bt.z), btl1 = __float_as_uint(bt.w);
+      const uint32_t bgh0 = __float_as_uint(bg.x), bgh1 = __float_as_uint(bg.y);
+      const uint32_t bgl0 = __float_as_uint(bg.z), bgl1 = __float_as_uint(bg.w);
+#pragma unroll
+      for (int r = 0; r < kRmRows; ++r) {
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        mma_tf32(d, al[r][0], al[r][1], al[r][2], al[r][3], bth0, bth1);
+        mma_tf32(d, ah[r][0], ah[r][1], ah[r][2], ah[r][3], btl0, btl1);
+        mma_tf32(d, ah[r][0], ah[r][1], ah[r][2], ah[r][3], bth0, bth1);
+        float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // omega . v / 2 pi (the phase row meets v's zero)
+        if (HVP) {
+          mma_tf32(o, vl[r][0], vl[r][1], vl[r][2], vl[r][3], bth0, bth1);
+          mma_tf32(o, vh[r][0], vh[r][1], vh[r][2], vh[r][3], btl0, btl1);
+          mma_tf32(o, vh[r][0], vh[r][1], vh[r][2], vh[r][3], bth0, bth1);
+        }
+        float f0, f1, f2, f3;
+        upk(rm_turns_to_rad(pk(d[0], d[1])), f0, f1);   // sample g: features 2t, 2t + 1
+        upk(rm_turns_to_rad(pk(d[2], d[3])), f2, f3);   // sample g + 8
+        const float c0 = cos_approx(f0), c1 = cos_approx(f1), c2 = cos_approx(f2), c3 = cos_approx(f3);
+        S[r][0] = fma2(wp, pk(c0, c1), S[r][0]);
+        S[r][1] = fma2(wp, pk(c2, c3), S[r][1]);
+        // A of the products over features: k slot t <-> feature 2t, slot t + 4 <-> 2t + 1.
+        // |sin| <= 1: rounding to a multiple of 2^-11 (by adding and removing 1.5 * 2^12) leaves at
+        // most 11 significant bits, an exact TF32 value; the remainder (|lo| <= 2^-12) goes in as FP32
+        // bits, of which the tensor core takes the TF32 part (absolute error <= 2^-22).  All FP32-pipe
+        // work: rounding conversions here would load the ALU pipe instead.
+        const u64 c12 = pk(6144.0f, 6144.0f), nc12 = pk(-6144.0f, -6144.0f), mone = pk(-1.0f, -1.0f);
+        const u64 a01 = pk(sin_approx(f0), sin_approx(f2)), a23 = pk(sin_approx(f1), sin_approx(f3));
+        const u64 h01 = add2(add2(a01, c12), nc12), h23 = add2(add2(a23, c12), nc12);
+        const u64 l01 = fma2(h01, mone, a01), l23 = fma2(h23, mone, a23);
+        float h[4], l[4];
+        upk(h01, h[0], h[1]);
+        upk(h23, h[2], h[3]);
+        upk(l01, l[0], l[1]);
+        upk(l23, l[2], l[3]);
+        mma_tf32(G[r], __float_as_uint(l[0]), __float_as_uint(l[1]), __float_as_uint(l[2]), __float_as_uint(l[3]),
+                 bgh0, bgh1);
+        mma_tf32(G[r], __float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]),
+                 bgl0, bgl1);
+        mma_tf32(G[r], __float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]),
+                 bgh0, bgh1);
+        if (HVP) {
+          // cos(theta) (omega . v / 2 pi): unbounded, so Veltkamp's split
+          u64 ph01, pl01, ph23, pl23;
+          rm_split(mul2(pk(c0, c2), pk(o[0], o[2])), ph01, pl01);
+          rm_split(mul2(pk(c1, c3), pk(o[1], o[3])), ph23, pl23);
+          float ph[4], pl[4];
+          upk(ph01, ph[0], ph[1]);
+          upk(ph23, ph[2], ph[3]);
+          upk(pl01, pl[0], pl[1]);
+          upk(pl23, pl[2], pl[3]);
+          mma_tf32(P[r], __float_as_uint(pl[0]), __float_as_uint(pl[1]), __float_as_uint(pl[2]),
+                   __float_as_uint(pl[3]), bgh0, bgh1);
+          mma_tf32(P[r], __float_as_uint(ph[0]), __float_as_uint(ph[1]), __float_as_uint(ph[2]),
+                   __float_as_uint(ph[3]), bgl0, bgl1);
+          mma_tf32(P[r], __float_as_uint(ph[0]), __float_as_uint(ph[1]), __float_as_uint(ph[2]),
+                   __float_as_uint(ph[3]), bgh0, bgh1);
+        }
+      }
+    }
+  }
+}
+
+// the logit of rows g (hh = 0) and g + 8 (hh = 1) of row tile r: the quad's partial sums
+__device__ __forceinline__ float rm_logit(const u64 (&S)[kRmRows][2], int r, int hh) {
+  float sa, sb;
+  upk(S[r][hh], sa, sb);
+  float s = sa + sb;
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+
+// One Euler step of the warp's 32 samples held in xs ([32][8], column 7 = 1).
+template <int D, bool TRACE>
+__device__ __forceinline__ void rm_euler_step(const float* __restrict__ tab, int nstage, float* sm, float* xs,
+                                              float bias, float eta, int64_t s0, int64_t N, int step,
+                                              float* __restrict__ traj, float* __restrict__ steps) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t ah[kRmRows][4], al[kRmRows][4];
+  rm_frags(xs, g, t, ah, al);
+  float G[kRmRows][4], P[kRmRows][4];
+  u64 S[kRmRows][2];
+  rm_sweep<false>(tab, nstage, sm, ah, al, ah, al, S, G, P);
+#pragma unroll
+  for (int r = 0; r < kRmRows; ++r) {
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const float s = rm_logit(S, r, hh);
+      float d1, d2;
+      sigmoid_d12(s + bias, d1, d2);
+      const float c = -eta * d1;
+      const int row = r * 16 + g + 8 * hh;
+      const int64_t n = s0 + row;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int j = 2 * t + e;
+        if (j < D) {
+          const float inc = __fmul_rn(c, G[r][2 * hh + e]);
+          if (TRACE && n < N) {
+            traj[((int64_t)step * N + n) * D + j] = xs[row * 8 + j];
+            steps[((int64_t)step * N + n) * D + j] = inc;
+          }
+          xs[row * 8 + j] = __fadd_rn(xs[row * 8 + j], inc);
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// rows [s0, s0 + 32) of an N x D array into xs ([32][8]; column 7 = col7)
+template <int D>
+__device__ __forceinline__ void rm_load_rows(const float* __restrict__ src, int64_t s0, int64_t N, float col7,
+                                             float* xs) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < kRmWarpSamples * 8; i += 32) {
+    const int r = i >> 3, j = i & 7;
+    const int64_t n = s0 + r;
+    xs[i] = j < D ? (n < N ? src[n * D + j] : 0.0f) : (j == 7 ? col7 : 0.0f);
+  }
+  __syncwarp();
+}
+
+template <int D>
+__device__ __forceinline__ void rm_store_rows(const float* xs, int64_t s0, int64_t N, float* __restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < kRmWarpSamples * D; i += 32) {
+    const int r = i / D, j = i % D;
+    if (s0 + r < N) dst[(s0 + r) * D + j] = xs[r * 8 + j];
+  }
+}
+
 template <int D, bool TRACE>
 __global__ void __launch_bounds__(kRmWarps * 32, 4)
 k_morph_rff_mma(const float* __restrict__ tab, int nstage, float bias, const float* __restrict__ x0, int64_t N, int T,
@@ -112,135 +303,85 @@ k_morph_rff_mma(const float* __restrict__ tab, int nstage, float bias, const flo
   static_assert(D >= 1 && D <= 7, "dimensions and the phase share the 8 k slots");
   extern __shared__ __align__(16) float sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
   float* xs = sm + 2 * kRmStageFloats + warp * (kRmWarpSamples * 8);   // [32 samples][8]: x, 0 .., 1
   const int64_t s0 = (int64_t)blockIdx.x * kRmSamples + warp * kRmWarpSamples;
-  for (int i = lane; i < kRmWarpSamples * 8; i += 32) {
-    const int r = i >> 3, j = i & 7;
-    const int64_t n = s0 + r;
-    xs[i] = j < D ? (n < N ? x0[n * D + j] : 0.0f) : (j == 7 ? 1.0f : 0.0f);
-  }
-  __syncwarp();
-
+  rm_load_rows<D>(x0, s0, N, 1.0f, xs);
   for (int step = 0; step < T; ++step) {
-    // A fragments of [x, 1], hi and lo
-    uint32_t ah[kRmRows][4], al[kRmRows][4];
-#pragma unroll
-    for (int r = 0; r < kRmRows; ++r) {
-      const float* xr = xs + r * 16 * 8;
-      const float v[4] = {xr[g * 8 + t], xr[(g + 8) * 8 + t], xr[g * 8 + t + 4], xr[(g + 8) * 8 + t + 4]};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        ah[r][q] = tf32_rna(v[q]);
-        al[r][q] = tf32_rna(v[q] - __uint_as_float(ah[r][q]));
-      }
+    rm_euler_step<D, TRACE>(tab, nstage, sm, xs, bias, eta, s0, N, step, traj, steps);
+    if (ckpt != nullptr && (step + 1) % kck == 0)
+      rm_store_rows<D>(xs, s0, N, ckpt + (int64_t)((step + 1) / kck - 1) * N * D);
+  }
+  if (xT) rm_store_rows<D>(xs, s0, N, xT);
+  if (TRACE) rm_store_rows<D>(xs, s0, N, traj + (int64_t)T * N * D);
+  (void)lane;
+}
+
+// VJP of the T-step map (g_t = (I - eta Hess c(x_t)) g_{t+1}), segment by
+// segment from the checkpoints: the segment's states are recomputed into the
+// warp's shared memory (kseg x [32][8]), then each step back is one
+// Hessian-vector pass with v = g.
+template <int D>
+__global__ void __launch_bounds__(kRmWarps * 32, 3)
+k_vjp_rff_mma(const float* __restrict__ tab, int nstage, float bias, const float* __restrict__ x0, int64_t N, int T,
+              float eta, int kseg, const float* __restrict__ ckpt, const float* __restrict__ gT, float* __restrict__ g0) {
+  extern __shared__ __align__(16) float sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  float* gs = sm + 2 * kRmStageFloats + warp * (kseg + 1) * (kRmWarpSamples * 8);   // [32][8], column 7 = 0
+  float* seg = gs + kRmWarpSamples * 8;                                              // kseg x [32][8]
+  const int64_t s0 = (int64_t)blockIdx.x * kRmSamples + warp * kRmWarpSamples;
+  rm_load_rows<D>(gT, s0, N, 0.0f, gs);
+  const float twopi = k2PiHi;
+  const int nseg = T / kseg;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    if (sgi == 0 || ckpt == nullptr) {
+      rm_load_rows<D>(x0, s0, N, 1.0f, seg);
+      for (int q = 0; q < sgi * kseg; ++q)
+        rm_euler_step<D, false>(tab, nstage, sm, seg, bias, eta, s0, N, 0, nullptr, nullptr);
+    } else {
+      rm_load_rows<D>(ckpt + (int64_t)(sgi - 1) * N * D, s0, N, 1.0f, seg);
     }
-    float G[kRmRows][4];
-    u64 S[kRmRows][2];
-#pragma unroll
-    for (int r = 0; r < kRmRows; ++r) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) G[r][q] = 0.0f;
-      S[r][0] = S[r][1] = 0ull;
+    for (int i = 1; i < kseg; ++i) {
+      float* dst = seg + i * (kRmWarpSamples * 8);
+      for (int q = lane; q < kRmWarpSamples * 8; q += 32) dst[q] = dst[q - kRmWarpSamples * 8];
+      __syncwarp();
+      rm_euler_step<D, false>(tab, nstage, sm, dst, bias, eta, s0, N, 0, nullptr, nullptr);
     }
-    __syncthreads();   // every warp is done with the previous step's stages
-    rm_stage_load(tab, sm);
-    for (int st = 0; st < nstage; ++st) {
-      cp_async_wait_all();
-      __syncthreads();   // stage st is visible; stage st - 1's buffer is free
-      if (st + 1 < nstage)
-        rm_stage_load(tab + (size_t)(st + 1) * kRmStageFloats, sm + ((st + 1) & 1) * kRmStageFloats);
-      const float* sb = sm + (st & 1) * kRmStageFloats;
-#pragma unroll kRmUnroll
-      for (int kt = 0; kt < kRmStageKT; ++kt) {
-        const float* rec = sb + kt * kRmKtFloats;
-        const float4 bt = reinterpret_cast<const float4*>(rec)[lane];
-        const float4 bg = reinterpret_cast<const float4*>(rec + 128)[lane];
-        const u64 wp = reinterpret_cast<const u64*>(rec + 256)[t];   // w of features 2t, 2t + 1
-        const uint32_t bth0 = __float_as_uint(bt.x), bth1 = __float_as_uint(bt.y);
-        const uint32_t btl0 = __float_as_uint(bt.z), btl1 = __float_as_uint(bt.w);
-        const uint32_t bgh0 = __float_as_uint(bg.x), bgh1 = __float_as_uint(bg.y);
-        const uint32_t bgl0 = __float_as_uint(bg.z), bgl1 = __float_as_uint(bg.w);
+    for (int i = kseg - 1; i >= 0; --i) {
+      const float* xi = seg + i * (kRmWarpSamples * 8);
+      uint32_t ah[kRmRows][4], al[kRmRows][4], vh[kRmRows][4], vl[kRmRows][4];
+      rm_frags(xi, g, t, ah, al);
+      rm_frags(gs, g, t, vh, vl);
+      float G[kRmRows][4], P[kRmRows][4];
+      u64 S[kRmRows][2];
+      rm_sweep<true>(tab, nstage, sm, ah, al, vh, vl, S, G, P);
 #pragma unroll
-        for (int r = 0; r < kRmRows; ++r) {
-          float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          mma_tf32(d, al[r][0], al[r][1], al[r][2], al[r][3], bth0, bth1);
-          mma_tf32(d, ah[r][0], ah[r][1], ah[r][2], ah[r][3], btl0, btl1);
-          mma_tf32(d, ah[r][0], ah[r][1], ah[r][2], ah[r][3], bth0, bth1);
-          float f0, f1, f2, f3;
-          upk(rm_turns_to_rad(pk(d[0], d[1])), f0, f1);   // sample g: features 2t, 2t + 1
-          upk(rm_turns_to_rad(pk(d[2], d[3])), f2, f3);   // sample g + 8
-          S[r][0] = fma2(wp, pk(cos_approx(f0), cos_approx(f1)), S[r][0]);
-          S[r][1] = fma2(wp, pk(cos_approx(f2), cos_approx(f3)), S[r][1]);
-          // A of the gradient product: k slot t <-> feature 2t, slot t + 4 <-> 2t + 1
-          // |sin| <= 1: rounding to a multiple of 2^-11 (by adding and removing 1.5 * 2^12) leaves at
-          // most 11 significant bits, an exact TF32 value; the remainder (|lo| <= 2^-12) goes in as FP32
-          // bits, of which the tensor core takes the TF32 part (absolute error <= 2^-22).  All FP32-pipe
-          // work: rounding conversions here would load the ALU pipe instead.
-          const u64 c12 = pk(6144.0f, 6144.0f), nc12 = pk(-6144.0f, -6144.0f), mone = pk(-1.0f, -1.0f);
-          const u64 a01 = pk(sin_approx(f0), sin_approx(f2)), a23 = pk(sin_approx(f1), sin_approx(f3));
-          const u64 h01 = add2(add2(a01, c12), nc12), h23 = add2(add2(a23, c12), nc12);
-          const u64 l01 = fma2(h01, mone, a01), l23 = fma2(h23, mone, a23);
-          float h[4], l[4];
-          upk(h01, h[0], h[1]);
-          upk(h23, h[2], h[3]);
-          upk(l01, l[0], l[1]);
-          upk(l23, l[2], l[3]);
-          const uint32_t h0 = __float_as_uint(h[0]), h1 = __float_as_uint(h[1]);
-          const uint32_t h2 = __float_as_uint(h[2]), h3 = __float_as_uint(h[3]);
-          mma_tf32(G[r], __float_as_uint(l[0]), __float_as_uint(l[1]), __float_as_uint(l[2]), __float_as_uint(l[3]),
-                   bgh0, bgh1);
-          mma_tf32(G[r], h0, h1, h2, h3, bgl0, bgl1);
-          mma_tf32(G[r], h0, h1, h2, h3, bgh0, bgh1);
-        }
-      }
-    }
-    // logits: the quad's partial sums; then the Euler update of dimensions 2t, 2t + 1
+      for (int r = 0; r < kRmRows; ++r) {
 #pragma unroll
-    for (int r = 0; r < kRmRows; ++r) {
+        for (int hh = 0; hh < 2; ++hh) {
+          const int row = r * 16 + g + 8 * hh;
+          const float s = rm_logit(S, r, hh);
+          float d1, d2;
+          sigmoid_d12(s + bias, d1, d2);
+          // grad s . g over the quad (dimensions 2t, 2t + 1 per lane)
+          float gd = fmaf(G[r][2 * hh], gs[row * 8 + 2 * t], G[r][2 * hh + 1] * gs[row * 8 + 2 * t + 1]);
+          gd += __shfl_xor_sync(0xffffffffu, gd, 1);
+          gd += __shfl_xor_sync(0xffffffffu, gd, 2);
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        float sa, sb2;
-        upk(S[r][hh], sa, sb2);
-        float s = sa + sb2;
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        float d1, d2;
-        sigmoid_d12(s + bias, d1, d2);
-        const float c = -eta * d1;
-        const int row = r * 16 + g + 8 * hh;
-        const int64_t n = s0 + row;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int j = 2 * t + e;
-          if (j < D) {
-            const float inc = __fmul_rn(c, G[r][2 * hh + e]);
-            if (TRACE && n < N) {
-              traj[((int64_t)step * N + n) * D + j] = xs[row * 8 + j];
-              steps[((int64_t)step * N + n) * D + j] = inc;
+          for (int e = 0; e < 2; ++e) {
+            const int j = 2 * t + e;
+            if (j < D) {
+              const float hv = twopi * P[r][2 * hh + e];      // (Hess s) v
+              const float gj = gs[row * 8 + j];
+              gs[row * 8 + j] = gj - eta * fmaf(d1, hv, d2 * gd * G[r][2 * hh + e]);
             }
-            xs[row * 8 + j] = __fadd_rn(xs[row * 8 + j], inc);
           }
         }
       }
-    }
-    __syncwarp();
-    if (ckpt != nullptr && (step + 1) % kck == 0) {
-      float* dst = ckpt + (int64_t)((step + 1) / kck - 1) * N * D;
-      for (int i = lane; i < kRmWarpSamples * D; i += 32) {
-        const int r = i / D, j = i % D;
-        if (s0 + r < N) dst[(s0 + r) * D + j] = xs[r * 8 + j];
-      }
+      __syncwarp();
     }
   }
-  for (int i = lane; i < kRmWarpSamples * D; i += 32) {
-    const int r = i / D, j = i % D;
-    const int64_t n = s0 + r;
-    if (n < N) {
-      if (xT) xT[n * D + j] = xs[r * 8 + j];
-      if (TRACE) traj[((int64_t)T * N + n) * D + j] = xs[r * 8 + j];
-    }
-  }
+  rm_store_rows<D>(gs, s0, N, g0);
 }
 
 template <int D>
@@ -277,6 +418,40 @@ cudaError_t morph_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N
     case 5: return launch_rff_mma<5>(fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
     case 6: return launch_rff_mma<6>(fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
     case 7: return launch_rff_mma<7>(fa, x0, N, T, eta, xT, ckpt, k, traj, steps, ws, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// the tensor-core VJP keeps a segment of states in shared memory: k <= 16
+size_t vjp_rff_mma_smem(int k) {
+  return (2 * (size_t)kRmStageFloats + (size_t)kRmWarps * (k + 1) * kRmWarpSamples * 8) * sizeof(float);
+}
+
+template <int D>
+static cudaError_t launch_vjp_rff_mma(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
+                                      const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st) {
+  float* tab = reinterpret_cast<float*>(ws);
+  const int64_t n_kt = rm_tiles(fa.M);
+  k_rff_mma_table<D><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
+  const size_t smem = vjp_rff_mma_smem(k);
+  cudaError_t e = cudaFuncSetAttribute(k_vjp_rff_mma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((N + kRmSamples - 1) / kRmSamples);
+  k_vjp_rff_mma<D><<<blocks, kRmWarps * 32, smem, st>>>(tab, (int)(n_kt / kRmStageKT), fa.bias, x0, N, T, eta, k,
+                                                        ckpt, gT, g0);
+  return cudaGetLastError();
+}
+
+cudaError_t vjp_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
+                        const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st) {
+  switch (d) {
+    case 1: return launch_vjp_rff_mma<1>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
+    case 2: return launch_vjp_rff_mma<2>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
+    case 3: return launch_vjp_rff_mma<3>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
+    case 4: return launch_vjp_rff_mma<4>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
+    case 5: return launch_vjp_rff_mma<5>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
+    case 6: return launch_vjp_rff_mma<6>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
+    case 7: return launch_vjp_rff_mma<7>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -125,6 +125,15 @@ def test_vjp_validation():
     assert L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 0) == 0
     assert L.pdmp_morph_vjp(ctypes.byref(f), A, 1000, 10, 0.01, 5, None, A, A, A, None, A, need - 1, None) == 3
     assert L.pdmp_morph_vjp(ctypes.byref(f), A, 1000, 10, 0.01, 5, None, A, A, A, None, None, need, None) == 1
+    # RFF, d <= 7, k <= 16, no parameter gradient: the optional tensor-core table
+    fr = fld(kind=1, d=7, M=16, phase=A)
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fr), 1000, 10, 5, 0) == 16 * 264 * 4
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fr), 1000, 32, 32, 0) == 0         # segment too long
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fld(kind=1, d=8, phase=A)), 1000, 10, 5, 0) == 0
+    assert L.pdmp_morph_vjp(ctypes.byref(fr), A, 1000, 10, 0.01, 5, None, A, A, None, None, A,
+                            16 * 264 * 4 - 1, None) == 3
+    assert L.pdmp_morph_vjp(ctypes.byref(fr), A, 1000, 10, 0.01, 5, None, A, A, None, None, MIS,
+                            16 * 264 * 4, None) == 1
 
 
 @nogpu

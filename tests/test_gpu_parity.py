@@ -230,6 +230,35 @@ def test_vjp_matches_oracle(kind, use_ckpt):
     assert abs(gb - rb) <= 1e-4 * max(abs(rb), 1e-3)
 
 
+@pytest.mark.parametrize("d,N,T,k,use_ckpt", [(7, 300, 12, 4, True), (7, 129, 12, 12, False), (3, 97, 6, 1, True),
+                                              (5, 1, 4, 2, False)])
+def test_vjp_tensor_core_path(d, N, T, k, use_ckpt):
+    """RFF, d <= 7, no parameter gradient: the tensor-core VJP (ragged
+    blocks, with and without checkpoints, segments of 1 .. T steps, g0
+    written over gT) against the oracle and the direct kernel."""
+    f = wl.random_field(30 + d, wl.RFF, d, 300, wscale=6.0, bias=0.1)
+    lo, hi = np.full(d, -np.pi), np.full(d, np.pi)
+    eta, _ = rff_eta_sampled(f, lo, hi, n=600)
+    x0 = wl.uniform_box(31 + d, 3, N, lo, hi)
+    gT = wl.f32(wl.rng(32 + d, wl.S_COTANGENT).standard_normal((N, d)))
+    fld = pdmp.DeviceField.from_host(f)
+    assert pdmp.morph_vjp_workspace(fld, N, T, k, False) > 0
+    ck = None
+    if use_ckpt:
+        ck = torch.empty(T // k, N, d, device="cuda")
+        pdmp.morph(fld, dev(x0), T, eta, ckpt=ck, k=k)
+    g = dev(gT)
+    out = pdmp.morph_vjp(fld, dev(x0), T, eta, k, g, ckpt=ck, g0=g)
+    assert out.data_ptr() == g.data_ptr()
+    g0 = out.cpu().numpy()
+    r0 = oracle.morph_vjp(f, x0, T, eta, gT)
+    corr = r0 - gT
+    assert np.linalg.norm(g0 - r0) <= 1e-4 * np.linalg.norm(r0)
+    assert np.linalg.norm((g0 - gT) - corr) <= 1e-4 * np.linalg.norm(corr) + 1e-6
+    direct = pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck, fast=False).cpu().numpy()
+    assert np.linalg.norm(g0 - direct) <= 1e-4 * np.linalg.norm(direct)
+
+
 def test_vjp_rff_7d_certified_step_full_chain():
     wk = wl.config3(N=4096)
     eta, _ = rff_eta_certified(wk.field)
