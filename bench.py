@@ -511,7 +511,9 @@ def extra_rff(pdmp, torch, n_sms, pk):
     d = 7
     clk = n_sms * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     # FP32 / MUFU rooflines per feature (128 FP32 lanes, 15.6 sin or cos per SM per clock):
-    # forward 2d+2 FP32 + 2 MUFU; VJP pass 4d+3 FP32 + 2 MUFU; log-det 2d+2 + d(d+1)/2 FP32 + 2 MUFU
+    # forward 2d+2 FP32 + 2 MUFU; VJP pass 4d+3 FP32 + 2 MUFU; log-det 2d+2 + d(d+1)/2 FP32 + 2 MUFU.
+    # The forward and the VJP put their contractions on the tensor cores, so their FP32 counts no
+    # longer bind: the sin and cos of every feature (2 MUFU per feature and pass) do.
     mufu = MUFU_SINCOS_PER_SM / 2.0
     peaks = {"forward": clk * min(FP32_LANES_PER_SM / (2 * d + 2), mufu),
              "vjp_per_pass": clk * min(FP32_LANES_PER_SM / (4 * d + 3), mufu),
@@ -519,8 +521,11 @@ def extra_rff(pdmp, torch, n_sms, pk):
     rates = {"forward": work / t_fwd, "vjp_per_pass": 2 * work / t_vjp, "logdet": work / t_ld}
     return {**rates, "unit": "feature-evals/s",
             "roofline_frac": {k: rates[k] / peaks[k] for k in rates}, "roofline_peak": peaks,
+            "mufu_frac": {k: rates[k] / (clk * mufu) for k in rates}, "mufu_peak": clk * mufu,
             "ms": {"forward": 1e3 * t_fwd, "vjp": 1e3 * t_vjp, "logdet": 1e3 * t_ld},
-            "note": "VJP counts its recompute pass and its Hessian-vector pass (2 N T M)"}
+            "note": "VJP counts its recompute pass and its Hessian-vector pass (2 N T M); roofline_frac uses the "
+                    "FP32-operation count of each pass (above 1 where the tensor cores take that work), "
+                    "mufu_frac the sin/cos bound every pass shares"}
 
 
 def extra_surrogate(pdmp, torch, args):

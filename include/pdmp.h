@@ -444,7 +444,7 @@ pdmp_status pdmp_morph_inverse(const pdmp_field* f, const float* z, int64_t N, i
  *            = -inf                                otherwise,
  * with y = phi^{-1}(z) from pdmp_morph_inverse (tol, maxit, ws, ws_bytes as
  * there) written to y (N x d, must not alias z) and log det J as pdmp_logdet
- * computes it. */
+ * computes it (with the same workspace). */
 pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, const double* lo,
                              const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* ws,
                              size_t ws_bytes, void* stream);
@@ -476,9 +476,12 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
 /* logdet[n] = sum_t log det(I - eta Hess c(x_t)) for sample n; xT (N x d, may
  * be NULL) receives x_T.  I - eta Hess c is symmetric positive definite when
  * eta L < 1; a step where it is not records a device flag (read with
- * pdmp_stream_status) and that sample's logdet is NaN. */
+ * pdmp_stream_status) and that sample's logdet is NaN.  ws: NULL, or
+ * ws_bytes >= pdmp_morph_workspace(f, N) bytes; with it, RFF fields with
+ * d <= 7 run on the tensor cores (theta, grad s and the d(d+1)/2 Hessian
+ * entries as TF32 MMAs with hi/lo splits; a d x d Cholesky per sample). */
 pdmp_status pdmp_logdet(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta,
-                        float* logdet, float* xT, void* stream);
+                        float* logdet, float* xT, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Sec. 3.1: occupancy queries and ground-truth labels.                     */

@@ -98,7 +98,7 @@ def lib():
                 "pdmp_morph": [_FP, _P, _i64, _i32, _f32, _P, _P, _i32, _P, _sz, _P],
                 "pdmp_morph_trace": [_FP, _P, _i64, _i32, _f32, _P, _P, _P, _sz, _P],
                 "pdmp_morph_vjp": [_FP, _P, _i64, _i32, _f32, _i32, _P, _P, _P, _P, _P, _P, _sz, _P],
-                "pdmp_logdet": [_FP, _P, _i64, _i32, _f32, _P, _P, _P],
+                "pdmp_logdet": [_FP, _P, _i64, _i32, _f32, _P, _P, _P, _sz, _P],
                 "pdmp_queue_create": [_i32, _i64, ctypes.POINTER(_P)],
                 "pdmp_queue_push": [_P, _P, _i64, _i32, ctypes.POINTER(_i64)],
                 "pdmp_queue_pop": [_P, _P, _i64, ctypes.POINTER(_i64)],
@@ -594,13 +594,18 @@ def morph_vjp(field: DeviceField, x0: torch.Tensor, T: int, eta: float, k: int, 
     return g0
 
 
-def logdet(field: DeviceField, x0: torch.Tensor, T: int, eta: float, want_xT: bool = False):
+def logdet(field: DeviceField, x0: torch.Tensor, T: int, eta: float, want_xT: bool = False, fast: bool = True,
+           ws: torch.Tensor | None = None):
+    """sum_t log det(I - eta Hess c(x_t)) per sample (and x_T); ``fast`` gives
+    the library the morph's workspace, with which RFF fields with d <= 7 run
+    on the tensor cores."""
     N, d = x0.shape[0], field.d
     ld = torch.empty(N, device=x0.device, dtype=torch.float32)
     xT = torch.empty_like(x0) if want_xT else None
+    wp, wb, _keep = _workspace(field, N, fast, ws)
     f = field.struct()
     st = lib().pdmp_logdet(ctypes.byref(f), _ptr(x0, shape=(N, d), name="x0"), N, int(T), float(eta),
-                           _ptr(ld, name="logdet"), _ptr(xT, name="xT"), _stream())
+                           _ptr(ld, name="logdet"), _ptr(xT, name="xT"), wp, wb, _stream())
     _check(st, "pdmp_logdet")
     return (ld, xT) if want_xT else ld
 

@@ -484,7 +484,7 @@ pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int
   cudaStream_t st = as_stream(stream);
   if ((s = pdmp_morph_inverse(f, z, N, T, eta, tol, maxit, y, nullptr, ws, ws_bytes, nullptr, stream)) != PDMP_OK)
     return s;
-  if ((s = cuda_status(pdmp::logdet(f->kind, f->d, field_args(f), y, N, T, eta, log_p, nullptr, st))) != PDMP_OK)
+  if ((s = cuda_status(pdmp::logdet(f->kind, f->d, field_args(f), y, N, T, eta, log_p, nullptr, ws, st))) != PDMP_OK)
     return s;
   return cuda_status(pdmp::uniform_log_density(y, N, f->d, lo, hi, log_p, st));
 }
@@ -539,7 +539,7 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
 }
 
 pdmp_status pdmp_logdet(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* logdet,
-                        float* xT, void* stream) {
+                        float* xT, void* ws, size_t ws_bytes, void* stream) {
   NvtxRange nvtx_range("pdmp_logdet");
   pdmp_status s = check_field(f);
   if (s != PDMP_OK) return s;
@@ -547,7 +547,9 @@ pdmp_status pdmp_logdet(const pdmp_field* f, const float* x0, int64_t N, int32_t
   if (N < 0 || T < 0) return PDMP_ERR_INVALID_ARG;
   if (N == 0) return PDMP_OK;
   if (!ok_ptr(x0, true) || !ok_ptr(logdet, true) || !ok_ptr(xT, false)) return PDMP_ERR_INVALID_ARG;
-  return cuda_status(pdmp::logdet(f->kind, f->d, field_args(f), x0, N, T, eta, logdet, xT, as_stream(stream)));
+  if ((s = check_ws(f, N, ws, ws_bytes)) != PDMP_OK) return s;
+  return cuda_status(
+      pdmp::logdet(f->kind, f->d, field_args(f), x0, N, T, eta, logdet, xT, ws, as_stream(stream)));
 }
 
 pdmp_status pdmp_occupancy_query(const pdmp_field* f, const float* x, int64_t N, float* c, float* s_out, float* grad,

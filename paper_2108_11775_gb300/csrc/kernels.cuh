@@ -76,8 +76,11 @@ cudaError_t vjp_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, 
 cudaError_t morph_vjp(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                       const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias,
                       cudaStream_t st);
+// ws: NULL or the morph's workspace (RFF, d <= 7: the tensor-core kernel)
 cudaError_t logdet(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
-                   float* xT, cudaStream_t st);
+                   float* xT, void* ws, cudaStream_t st);
+cudaError_t logdet_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
+                           float* xT, void* ws, cudaStream_t st);
 
 cudaError_t occupancy_query(int kind, int d, const FieldArgs& fa, const float* x, int64_t N, float* c, float* s,
                             float* grad, cudaStream_t st);

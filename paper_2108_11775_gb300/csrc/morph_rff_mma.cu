@@ -51,19 +51,30 @@ static int64_t rm_tiles(int64_t M) {   // k tiles, padded to whole stages
   return (kt + kRmStageKT - 1) / kRmStageKT * kRmStageKT;
 }
 
+// Log-det records: the morph's 264 floats per k tile, then the B fragments of
+// the Hessian contraction, kLdNT n tiles of 8 lower-triangle entries (hi, lo).
+constexpr int kLdNT = 4;                                // 28 entries of a 7 x 7 symmetric matrix
+constexpr int kLdKtFloats = kRmKtFloats + kLdNT * 128;
+constexpr int kLdStageKT = 8;                           // k tiles per log-det stage
+constexpr int kLdStageFloats = kLdStageKT * kLdKtFloats;
+static_assert(kRmStageKT % kLdStageKT == 0, "the table is padded to whole stages of both kernels");
+
 size_t morph_rff_mma_workspace(int64_t M) {
-  return ((size_t)rm_tiles(M) * kRmKtFloats * sizeof(float) + 255) & ~size_t(255);
+  return ((size_t)rm_tiles(M) * kLdKtFloats * sizeof(float) + 255) & ~size_t(255);
 }
 
 // Table of B fragments, one thread per (k tile, lane).  Features past M are
 // zero (w = 0 and omega = 0: cos = 1 and sin = 0 add nothing).
-template <int D>
+// With HESS, also B[k][n] = -w omega_a omega_b for the lower-triangle entry
+// n = a (a + 1) / 2 + b of feature 2t (k = t) and 2t + 1 (k = t + 4), so
+// that sum_m cos(theta_m) B gives Hess s; the record stride is then kLdKtFloats.
+template <int D, bool HESS>
 __global__ void k_rff_mma_table(FieldArgs fa, int64_t n_kt, float* __restrict__ tab) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_kt * 32) return;
   const int64_t kt = i >> 5;
   const int lane = (int)(i & 31), g = lane >> 2, t = lane & 3;
-  float* rec = tab + kt * kRmKtFloats;
+  float* rec = tab + kt * (HESS ? kLdKtFloats : kRmKtFloats);
   // theta: B[k = dimension][n = feature] = omega / 2 pi, the phase in row 7
   const int64_t m = kt * 8 + g;
   float p[2];
@@ -88,10 +99,30 @@ __global__ void k_rff_mma_table(FieldArgs fa, int64_t n_kt, float* __restrict__ 
   reinterpret_cast<float4*>(rec + 128)[lane] = make_float4(e0, e1, __uint_as_float(tf32_rna(q[0] - e0)),
                                                            __uint_as_float(tf32_rna(q[1] - e1)));
   if (lane < 8) rec[256 + lane] = kt * 8 + lane < fa.M ? fa.w[kt * 8 + lane] : 0.0f;
+  if (HESS) {
+#pragma unroll
+    for (int nt = 0; nt < kLdNT; ++nt) {
+      const int n = 8 * nt + g;
+      int a = 0;
+      while (a < 7 && (a + 1) * (a + 2) / 2 <= n) ++a;   // row of entry n
+      const int b = n - a * (a + 1) / 2;
+      float q2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t mm = kt * 8 + 2 * t + h;
+        q2[h] = (mm < fa.M && a < D && n < D * (D + 1) / 2)
+                    ? -fa.w[mm] * fa.centres[mm * D + a] * fa.centres[mm * D + b] : 0.0f;
+      }
+      const float u0 = __uint_as_float(tf32_rna(q2[0])), u1 = __uint_as_float(tf32_rna(q2[1]));
+      reinterpret_cast<float4*>(rec + kRmKtFloats + 128 * nt)[lane] =
+          make_float4(u0, u1, __uint_as_float(tf32_rna(q2[0] - u0)), __uint_as_float(tf32_rna(q2[1] - u1)));
+    }
+  }
 }
 
+template <int kFloats = kRmStageFloats>
 __device__ __forceinline__ void rm_stage_load(const float* __restrict__ src, float* dst) {
-  constexpr int kChunks = kRmStageFloats / 4;
+  constexpr int kChunks = kFloats / 4;
   for (int i = threadIdx.x; i < kChunks; i += kRmWarps * 32) cp_async16(dst + 4 * i, src + 4 * i);
   cp_async_commit();
 }
@@ -389,7 +420,7 @@ static cudaError_t launch_rff_mma(const FieldArgs& fa, const float* x0, int64_t 
                                   float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st) {
   float* tab = reinterpret_cast<float*>(ws);
   const int64_t n_kt = rm_tiles(fa.M);
-  k_rff_mma_table<D><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
+  k_rff_mma_table<D, false><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
   const int nstage = (int)(n_kt / kRmStageKT);
   constexpr size_t smem = rm_smem_bytes();
   const unsigned blocks = (unsigned)((N + kRmSamples - 1) / kRmSamples);
@@ -422,6 +453,198 @@ cudaError_t morph_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N
   return cudaErrorInvalidValue;
 }
 
+// Log-det of the T-step map (Sec. 3.2, "Drawing Samples"): per step
+// log det(I - eta Hess c(x_t)) with Hess c = sigma'(s) Hess s + sigma''(s)
+// grad s grad s^T.  The sweep adds to the forward's two products the
+// Hessian contraction Hess s = sum_m cos(theta_m) (-w_m omega_m omega_m^T) over
+// the 28 lower-triangle entries (4 n tiles, TF32 with hi/lo splits; cos split
+// like the sines).  At the step end each sample's s, grad s and Hess s are
+// gathered through shared memory to one lane, which forms I - eta Hess c, its
+// Cholesky log-det and the Euler update.
+constexpr int kLdGather = 40;   // per sample: Hess s (32 slots), s, grad s (7)
+
+__host__ __device__ constexpr size_t ld_rff_smem_bytes() {
+  return (2 * (size_t)kLdStageFloats + (size_t)kRmWarps * kRmWarpSamples * (8 + kLdGather)) * sizeof(float);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kRmWarps * 32, 3)
+k_logdet_rff_mma(const float* __restrict__ tab, int nstage, float bias, const float* __restrict__ x0, int64_t N,
+                 int T, float eta, float* __restrict__ logdet, float* __restrict__ xT) {
+  static_assert(D >= 1 && D <= 7, "dimensions and the phase share the 8 k slots");
+  extern __shared__ __align__(16) float sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  float* xs = sm + 2 * kLdStageFloats + warp * kRmWarpSamples * (8 + kLdGather);
+  float* gat = xs + kRmWarpSamples * 8;
+  const int64_t s0 = (int64_t)blockIdx.x * kRmSamples + warp * kRmWarpSamples;
+  rm_load_rows<D>(x0, s0, N, 1.0f, xs);
+  float total = 0.0f;
+  bool bad = false;
+  const u64 c12 = pk(6144.0f, 6144.0f), nc12 = pk(-6144.0f, -6144.0f), mone = pk(-1.0f, -1.0f);
+
+  for (int step = 0; step < T; ++step) {
+    uint32_t ah[kRmRows][4], al[kRmRows][4];
+    rm_frags(xs, g, t, ah, al);
+    float G[kRmRows][4], Q[kRmRows][kLdNT][4];
+    u64 S[kRmRows][2];
+#pragma unroll
+    for (int r = 0; r < kRmRows; ++r) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        G[r][q] = 0.0f;
+#pragma unroll
+        for (int nt = 0; nt < kLdNT; ++nt) Q[r][nt][q] = 0.0f;
+      }
+      S[r][0] = S[r][1] = 0ull;
+    }
+    __syncthreads();   // every warp is done with the previous step's stages
+    rm_stage_load<kLdStageFloats>(tab, sm);
+    for (int st = 0; st < nstage; ++st) {
+      cp_async_wait_all();
+      __syncthreads();
+      if (st + 1 < nstage)
+        rm_stage_load<kLdStageFloats>(tab + (size_t)(st + 1) * kLdStageFloats,
+                                      sm + ((st + 1) & 1) * kLdStageFloats);
+      const float* sb = sm + (st & 1) * kLdStageFloats;
+#pragma unroll 1
+      for (int kt = 0; kt < kLdStageKT; ++kt) {
+        const float* rec = sb + kt * kLdKtFloats;
+        const float4 bt = reinterpret_cast<const float4*>(rec)[lane];
+        const float4 bg = reinterpret_cast<const float4*>(rec + 128)[lane];
+        const u64 wp = reinterpret_cast<const u64*>(rec + 256)[t];
+        float4 bh[kLdNT];
+#pragma unroll
+        for (int nt = 0; nt < kLdNT; ++nt) bh[nt] = reinterpret_cast<const float4*>(rec + kRmKtFloats + 128 * nt)[lane];
+#pragma unroll
+        for (int r = 0; r < kRmRows; ++r) {
+          float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          mma_tf32(d, al[r][0], al[r][1], al[r][2], al[r][3], __float_as_uint(bt.x), __float_as_uint(bt.y));
+          mma_tf32(d, ah[r][0], ah[r][1], ah[r][2], ah[r][3], __float_as_uint(bt.z), __float_as_uint(bt.w));
+          mma_tf32(d, ah[r][0], ah[r][1], ah[r][2], ah[r][3], __float_as_uint(bt.x), __float_as_uint(bt.y));
+          float f0, f1, f2, f3;
+          upk(rm_turns_to_rad(pk(d[0], d[1])), f0, f1);
+          upk(rm_turns_to_rad(pk(d[2], d[3])), f2, f3);
+          const float c0 = cos_approx(f0), c1 = cos_approx(f1), c2 = cos_approx(f2), c3 = cos_approx(f3);
+          S[r][0] = fma2(wp, pk(c0, c1), S[r][0]);
+          S[r][1] = fma2(wp, pk(c2, c3), S[r][1]);
+          // sines (gradient) and cosines (Hessian), each split by the 1.5 * 2^12 shift
+          const u64 s01 = pk(sin_approx(f0), sin_approx(f2)), s23 = pk(sin_approx(f1), sin_approx(f3));
+          const u64 sh01 = add2(add2(s01, c12), nc12), sh23 = add2(add2(s23, c12), nc12);
+          const u64 sl01 = fma2(sh01, mone, s01), sl23 = fma2(sh23, mone, s23);
+          const u64 k01 = pk(c0, c2), k23 = pk(c1, c3);
+          const u64 kh01 = add2(add2(k01, c12), nc12), kh23 = add2(add2(k23, c12), nc12);
+          const u64 kl01 = fma2(kh01, mone, k01), kl23 = fma2(kh23, mone, k23);
+          float sh[4], sl[4], kh[4], kl[4];
+          upk(sh01, sh[0], sh[1]);
+          upk(sh23, sh[2], sh[3]);
+          upk(sl01, sl[0], sl[1]);
+          upk(sl23, sl[2], sl[3]);
+          upk(kh01, kh[0], kh[1]);
+          upk(kh23, kh[2], kh[3]);
+          upk(kl01, kl[0], kl[1]);
+          upk(kl23, kl[2], kl[3]);
+#define PDMP_U(x) __float_as_uint(x)
+          mma_tf32(G[r], PDMP_U(sl[0]), PDMP_U(sl[1]), PDMP_U(sl[2]), PDMP_U(sl[3]), PDMP_U(bg.x), PDMP_U(bg.y));
+          mma_tf32(G[r], PDMP_U(sh[0]), PDMP_U(sh[1]), PDMP_U(sh[2]), PDMP_U(sh[3]), PDMP_U(bg.z), PDMP_U(bg.w));
+          mma_tf32(G[r], PDMP_U(sh[0]), PDMP_U(sh[1]), PDMP_U(sh[2]), PDMP_U(sh[3]), PDMP_U(bg.x), PDMP_U(bg.y));
+#pragma unroll
+          for (int nt = 0; nt < kLdNT; ++nt) {
+            mma_tf32(Q[r][nt], PDMP_U(kl[0]), PDMP_U(kl[1]), PDMP_U(kl[2]), PDMP_U(kl[3]), PDMP_U(bh[nt].x),
+                     PDMP_U(bh[nt].y));
+            mma_tf32(Q[r][nt], PDMP_U(kh[0]), PDMP_U(kh[1]), PDMP_U(kh[2]), PDMP_U(kh[3]), PDMP_U(bh[nt].z),
+                     PDMP_U(bh[nt].w));
+            mma_tf32(Q[r][nt], PDMP_U(kh[0]), PDMP_U(kh[1]), PDMP_U(kh[2]), PDMP_U(kh[3]), PDMP_U(bh[nt].x),
+                     PDMP_U(bh[nt].y));
+          }
+#undef PDMP_U
+        }
+      }
+    }
+    // gather each sample's sums: Hess s columns from the quad, s and grad s
+#pragma unroll
+    for (int r = 0; r < kRmRows; ++r)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const float s = rm_logit(S, r, hh);
+        float* row = gat + (r * 16 + g + 8 * hh) * kLdGather;
+#pragma unroll
+        for (int nt = 0; nt < kLdNT; ++nt) {
+          row[nt * 8 + 2 * t] = Q[r][nt][2 * hh];
+          row[nt * 8 + 2 * t + 1] = Q[r][nt][2 * hh + 1];
+        }
+        if (t == 0) row[32] = s;
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          if (2 * t + e < D) row[33 + 2 * t + e] = G[r][2 * hh + e];
+      }
+    __syncwarp();
+    {
+      // lane = sample: I - eta Hess c, its Cholesky log-det, the Euler update
+      const float* row = gat + lane * kLdGather;
+      float gsv[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) gsv[j] = row[33 + j];
+      float d1, d2;
+      sigmoid_d12(row[32] + bias, d1, d2);
+      float A[D][D];
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          if (b <= a) {
+            const float hc = fmaf(d1, row[a * (a + 1) / 2 + b], d2 * gsv[a] * gsv[b]);
+            A[a][b] = (a == b ? 1.0f : 0.0f) - eta * hc;
+          } else {
+            A[a][b] = 0.0f;
+          }
+        }
+      const float ld = chol_logdet<D>(A);
+      if (!(ld == ld)) bad = true;
+      total += ld;
+      const float c = -eta * d1;
+#pragma unroll
+      for (int j = 0; j < D; ++j) xs[lane * 8 + j] = __fadd_rn(xs[lane * 8 + j], __fmul_rn(c, gsv[j]));
+    }
+    __syncwarp();
+  }
+  const int64_t own = s0 + lane;
+  if (own < N) {
+    if (bad) raise_flag(FLAG_NONPOSITIVE_PIVOT);
+    logdet[own] = bad ? nanf("") : total;
+  }
+  if (xT) rm_store_rows<D>(xs, s0, N, xT);
+}
+
+template <int D>
+static cudaError_t launch_logdet_rff_mma(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta,
+                                         float* ld, float* xT, void* ws, cudaStream_t st) {
+  float* tab = reinterpret_cast<float*>(ws);
+  const int64_t n_kt = rm_tiles(fa.M);
+  k_rff_mma_table<D, true><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
+  constexpr size_t smem = ld_rff_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_logdet_rff_mma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((N + kRmSamples - 1) / kRmSamples);
+  k_logdet_rff_mma<D><<<blocks, kRmWarps * 32, smem, st>>>(tab, (int)(n_kt / kLdStageKT), fa.bias, x0, N, T, eta,
+                                                           ld, xT);
+  return cudaGetLastError();
+}
+
+cudaError_t logdet_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
+                           float* xT, void* ws, cudaStream_t st) {
+  switch (d) {
+    case 1: return launch_logdet_rff_mma<1>(fa, x0, N, T, eta, ld, xT, ws, st);
+    case 2: return launch_logdet_rff_mma<2>(fa, x0, N, T, eta, ld, xT, ws, st);
+    case 3: return launch_logdet_rff_mma<3>(fa, x0, N, T, eta, ld, xT, ws, st);
+    case 4: return launch_logdet_rff_mma<4>(fa, x0, N, T, eta, ld, xT, ws, st);
+    case 5: return launch_logdet_rff_mma<5>(fa, x0, N, T, eta, ld, xT, ws, st);
+    case 6: return launch_logdet_rff_mma<6>(fa, x0, N, T, eta, ld, xT, ws, st);
+    case 7: return launch_logdet_rff_mma<7>(fa, x0, N, T, eta, ld, xT, ws, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 // the tensor-core VJP keeps a segment of states in shared memory: k <= 16
 size_t vjp_rff_mma_smem(int k) {
   return (2 * (size_t)kRmStageFloats + (size_t)kRmWarps * (k + 1) * kRmWarpSamples * 8) * sizeof(float);
@@ -432,7 +655,7 @@ static cudaError_t launch_vjp_rff_mma(const FieldArgs& fa, const float* x0, int6
                                       const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st) {
   float* tab = reinterpret_cast<float*>(ws);
   const int64_t n_kt = rm_tiles(fa.M);
-  k_rff_mma_table<D><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
+  k_rff_mma_table<D, false><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
   const size_t smem = vjp_rff_mma_smem(k);
   cudaError_t e = cudaFuncSetAttribute(k_vjp_rff_mma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -99,10 +99,10 @@ def test_morph_workspace_size_and_checks():
     # RFF, d = 8: the pair table (M records of 11 u64 pairs, padded to 16 bytes, 256 in all)
     pair8 = L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=8, phase=A)), 1 << 20)
     assert pair8 == (16 * 12 * 8 + 255) // 256 * 256
-    # RFF, d <= 7: the tensor-core table (k tiles of 8 features, 264 floats each, in whole stages of 16)
-    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, phase=A)), 1 << 20) == 16 * 264 * 4
-    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=3, phase=A)), 1 << 20) == 16 * 264 * 4
-    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, M=129, phase=A)), 1) == 32 * 264 * 4
+    # RFF, d <= 7: the tensor-core table (k tiles of 8 features, 776 floats each, whole stages of 16)
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, phase=A)), 1 << 20) == 16 * 776 * 4
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=3, phase=A)), 1 << 20) == 16 * 776 * 4
+    assert L.pdmp_morph_workspace(ctypes.byref(fld(kind=1, d=7, M=129, phase=A)), 1) == 32 * 776 * 4
     assert L.pdmp_morph_workspace(ctypes.byref(fld(d=1)), 1000) == 0
     assert morph_call(f, N=1 << 20, ws=A, ws_bytes=need - 1) == 3
     assert morph_call(f, N=1 << 20, ws=MIS, ws_bytes=need) == 1
@@ -127,13 +127,13 @@ def test_vjp_validation():
     assert L.pdmp_morph_vjp(ctypes.byref(f), A, 1000, 10, 0.01, 5, None, A, A, A, None, None, need, None) == 1
     # RFF, d <= 7, k <= 16, no parameter gradient: the optional tensor-core table
     fr = fld(kind=1, d=7, M=16, phase=A)
-    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fr), 1000, 10, 5, 0) == 16 * 264 * 4
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fr), 1000, 10, 5, 0) == 16 * 776 * 4
     assert L.pdmp_morph_vjp_workspace(ctypes.byref(fr), 1000, 32, 32, 0) == 0         # segment too long
     assert L.pdmp_morph_vjp_workspace(ctypes.byref(fld(kind=1, d=8, phase=A)), 1000, 10, 5, 0) == 0
     assert L.pdmp_morph_vjp(ctypes.byref(fr), A, 1000, 10, 0.01, 5, None, A, A, None, None, A,
-                            16 * 264 * 4 - 1, None) == 3
+                            16 * 776 * 4 - 1, None) == 3
     assert L.pdmp_morph_vjp(ctypes.byref(fr), A, 1000, 10, 0.01, 5, None, A, A, None, None, MIS,
-                            16 * 264 * 4, None) == 1
+                            16 * 776 * 4, None) == 1
 
 
 @nogpu

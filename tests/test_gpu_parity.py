@@ -286,6 +286,40 @@ def test_logdet_matches_oracle_and_is_diffeomorphic(kind):
     assert pdmp.stream_status()[0] == 0
 
 
+@pytest.mark.parametrize("d,N,T,M", [(7, 300, 6, 300), (3, 131, 5, 1000), (1, 64, 4, 17), (5, 129, 3, 260)])
+def test_logdet_tensor_core_path(d, N, T, M):
+    """RFF, d <= 7, with the workspace: the tensor-core log-det (ragged blocks,
+    several stages, the Hessian's d(d+1)/2 entries) against the oracle and
+    the direct kernel."""
+    f = wl.random_field(60 + d, wl.RFF, d, M, wscale=6.0, bias=0.1)
+    lo, hi = np.full(d, -np.pi), np.full(d, np.pi)
+    eta, _ = rff_eta_sampled(f, lo, hi, n=600)
+    x0 = wl.uniform_box(61 + d, 3, N, lo, hi)
+    fld = pdmp.DeviceField.from_host(f)
+    ld, xT = pdmp.logdet(fld, dev(x0), T, eta, want_xT=True)
+    ld, xT = ld.cpu().numpy(), xT.cpu().numpy()
+    ref, xref, mindet = oracle.logdet(f, x0, T, eta)
+    assert np.all(mindet > 0)
+    assert max_abs(ld, ref) <= 1e-4 * T
+    assert max_abs(xT, xref) <= 1e-4
+    assert np.abs(ref).max() > 1e-3                       # the steps change volume measurably
+    direct = pdmp.logdet(fld, dev(x0), T, eta, fast=False).cpu().numpy()
+    assert max_abs(ld, direct) <= 1e-4 * T
+    assert pdmp.stream_status()[0] == 0
+
+
+def test_logdet_flags_a_non_diffeomorphic_step_on_the_tensor_cores():
+    f = wl.random_field(66, wl.RFF, 7, 256, wscale=6.0, bias=0.1)
+    lo, hi = np.full(7, -np.pi), np.full(7, np.pi)
+    eta, _ = rff_eta_sampled(f, lo, hi, n=600)
+    fld = pdmp.DeviceField.from_host(f)                   # carries no bound: the call is accepted
+    ld = pdmp.logdet(fld, dev(wl.uniform_box(67, 3, 256, lo, hi)), 3, 400.0 * eta).cpu().numpy()
+    st, detail = pdmp.stream_status()
+    assert st == 7 and detail & 1
+    assert np.isnan(ld).any()
+    assert pdmp.stream_status()[0] == 0
+
+
 def test_logdet_flags_a_non_diffeomorphic_step():
     w1 = wl.config1(N=128)
     _, L = rbf_eta(w1.field, w1.lo, w1.hi)
