@@ -461,7 +461,9 @@ cudaError_t morph_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N
 // like the sines).  At the step end each sample's s, grad s and Hess s are
 // gathered through shared memory to one lane, which forms I - eta Hess c, its
 // Cholesky log-det and the Euler update.
-constexpr int kLdGather = 40;   // per sample: Hess s (32 slots), s, grad s (7)
+// per sample: Hess s (32 slots), s, grad s (7); 41 floats a row so that the
+// lanes reading one row each (stride 41, odd) hit distinct banks
+constexpr int kLdGather = 41;
 
 __host__ __device__ constexpr size_t ld_rff_smem_bytes() {
   return (2 * (size_t)kLdStageFloats + (size_t)kRmWarps * kRmWarpSamples * (8 + kLdGather)) * sizeof(float);
