@@ -333,7 +333,7 @@ k_morph_rff_mma(const float* __restrict__ tab, int nstage, float bias, const flo
                 float* __restrict__ steps) {
   static_assert(D >= 1 && D <= 7, "dimensions and the phase share the 8 k slots");
   extern __shared__ __align__(16) float sm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   float* xs = sm + 2 * kRmStageFloats + warp * (kRmWarpSamples * 8);   // [32 samples][8]: x, 0 .., 1
   const int64_t s0 = (int64_t)blockIdx.x * kRmSamples + warp * kRmWarpSamples;
   rm_load_rows<D>(x0, s0, N, 1.0f, xs);
@@ -344,7 +344,6 @@ k_morph_rff_mma(const float* __restrict__ tab, int nstage, float bias, const flo
   }
   if (xT) rm_store_rows<D>(xs, s0, N, xT);
   if (TRACE) rm_store_rows<D>(xs, s0, N, traj + (int64_t)T * N * D);
-  (void)lane;
 }
 
 // VJP of the T-step map (g_t = (I - eta Hess c(x_t)) g_{t+1}), segment by

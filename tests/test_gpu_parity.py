@@ -259,6 +259,30 @@ def test_vjp_tensor_core_path(d, N, T, k, use_ckpt):
     assert np.linalg.norm(g0 - direct) <= 1e-4 * np.linalg.norm(direct)
 
 
+def test_vjp_and_logdet_rff_7d_full_size_sampled():
+    """The differentiation workload as the benchmark runs it (N = 2^20,
+    M = 4096, T = 20, k = 5, tensor-core kernels): the VJP from the forward's
+    checkpoints and the log-det, on sampled samples against the oracle."""
+    wk = wl.config3()
+    eta, L = rff_eta_certified(wk.field)
+    fld = pdmp.DeviceField.from_host(wk.field, lipschitz=L)
+    N, T, k = wk.x0.shape[0], wk.T, wk.extra["k"]
+    x0 = dev(wk.x0)
+    gT = wk.extra["gT"]
+    ck = torch.empty(T // k, N, 7, device="cuda")
+    pdmp.morph(fld, x0, T, eta, ckpt=ck, k=k)
+    g0 = pdmp.morph_vjp(fld, x0, T, eta, k, dev(gT), ckpt=ck).cpu().numpy()
+    ld = pdmp.logdet(fld, x0, T, eta).cpu().numpy()
+    assert np.isfinite(g0).all() and np.isfinite(ld).all()
+    idx = np.concatenate([np.sort(wl.rng(10, 1).choice(N, 20, replace=False)), [0, N - 1]])
+    r0 = oracle.morph_vjp(wk.field, wk.x0[idx], T, eta, gT[idx])
+    corr = r0 - gT[idx]
+    assert np.linalg.norm((g0[idx] - gT[idx]) - corr) <= 1e-4 * np.linalg.norm(corr)
+    rl, _, mindet = oracle.logdet(wk.field, wk.x0[idx], T, eta)
+    assert np.all(mindet > 0)
+    assert max_abs(ld[idx], rl) <= 1e-4 * T
+
+
 def test_vjp_rff_7d_certified_step_full_chain():
     wk = wl.config3(N=4096)
     eta, _ = rff_eta_certified(wk.field)
