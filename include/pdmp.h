@@ -479,7 +479,9 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
  * pdmp_stream_status) and that sample's logdet is NaN.  ws: NULL, or
  * ws_bytes >= pdmp_morph_workspace(f, N) bytes; with it, RFF fields with
  * d <= 7 run on the tensor cores (theta, grad s and the d(d+1)/2 Hessian
- * entries as TF32 MMAs with hi/lo splits; a d x d Cholesky per sample). */
+ * entries as TF32 MMAs with hi/lo splits; a d x d Cholesky per sample), and
+ * RBF fields in d = 2, 3 on the morph's sorted tiles (expanded exponent, the
+ * Hessian from the moments sum e' c c^T; N < 2^31). */
 pdmp_status pdmp_logdet(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta,
                         float* logdet, float* xT, void* ws, size_t ws_bytes, void* stream);
 

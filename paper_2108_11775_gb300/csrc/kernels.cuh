@@ -81,6 +81,9 @@ cudaError_t logdet(int kind, int d, const FieldArgs& fa, const float* x0, int64_
                    float* xT, void* ws, cudaStream_t st);
 cudaError_t logdet_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
                            float* xT, void* ws, cudaStream_t st);
+// RBF, d = 2, 3 on sorted tiles (ws: morph_rbf_fast_workspace)
+cudaError_t logdet_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
+                            float* xT, void* ws, cudaStream_t st);
 
 cudaError_t occupancy_query(int kind, int d, const FieldArgs& fa, const float* x, int64_t N, float* c, float* s,
                             float* grad, cudaStream_t st);

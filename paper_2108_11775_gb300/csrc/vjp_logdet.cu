@@ -436,6 +436,8 @@ cudaError_t morph_vjp(int kind, int d, const FieldArgs& fa, const float* x0, int
 cudaError_t logdet(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
                    float* xT, void* ws, cudaStream_t st) {
   if (kind == PDMP_KIND_RFF && d <= 7 && ws != nullptr) return logdet_rff_mma(d, fa, x0, N, T, eta, ld, xT, ws, st);
+  if (kind == PDMP_KIND_RBF && (d == 2 || d == 3) && ws != nullptr)
+    return logdet_rbf_fast(d, fa, x0, N, T, eta, ld, xT, ws, st);
   if (kind == PDMP_KIND_RFF && d == 7) return logdet_rff7_mma(fa, x0, N, T, eta, ld, xT, st);
   PDMP_DISPATCH(launch_logdet, fa, x0, N, T, eta, ld, xT, st);
 }

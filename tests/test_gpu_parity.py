@@ -332,6 +332,35 @@ def test_logdet_tensor_core_path(d, N, T, M):
     assert pdmp.stream_status()[0] == 0
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_logdet_sorted_tiles_rbf(d):
+    """RBF, d = 2, 3 with the workspace: the log-det on the morph's sorted
+    tiles (enough samples that tiles are compact and take the expanded form,
+    plus a ragged last tile) against the oracle on sampled samples and the
+    direct kernel on all."""
+    if d == 2:
+        f = wl.config1().field
+        lo, hi, N, T = np.zeros(2), np.full(2, 10.0), (1 << 15) + 77, 6
+        eta, L = rbf_eta(f, lo, hi)
+    else:
+        f = wl.random_field(78, wl.RBF, 3, 4096, lo=0, hi=5, gamma=8.0, wscale=2.0, bias=-0.2)
+        lo, hi, N, T = np.zeros(3), np.full(3, 5.0), (1 << 15) + 5, 5
+        eta, L = rbf_eta(f, lo - 0.5, hi + 0.5, cells=16)
+    x0 = wl.uniform_box(90 + d, 3, N, lo, hi)
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    ld, xT = pdmp.logdet(fld, dev(x0), T, eta, want_xT=True)
+    ld, xT = ld.cpu().numpy(), xT.cpu().numpy()
+    idx = np.concatenate([np.sort(wl.rng(d, 11).choice(N, 64, replace=False)), [N - 1]])
+    ref, xref, mindet = oracle.logdet(f, x0[idx], T, eta)
+    assert np.all(mindet > 0)
+    assert max_abs(ld[idx], ref) <= 1e-4 * T
+    assert max_abs(xT[idx], xref) <= 1e-4
+    assert np.abs(ref).max() > 1e-3
+    direct = pdmp.logdet(fld, dev(x0), T, eta, fast=False).cpu().numpy()
+    assert max_abs(ld, direct) <= 1e-4 * T
+    assert pdmp.stream_status()[0] == 0
+
+
 def test_logdet_flags_a_non_diffeomorphic_step_on_the_tensor_cores():
     f = wl.random_field(66, wl.RFF, 7, 256, wscale=6.0, bias=0.1)
     lo, hi = np.full(7, -np.pi), np.full(7, np.pi)
