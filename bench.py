@@ -594,7 +594,22 @@ def cpu_baseline(wk, fld, eta, target_s=12.0):
     oracle.morph(f, wk.x0[probe:probe + n], T, eta)
     dt = time.perf_counter() - t0
     return {"value": n * T * M / dt, "unit": "feature-evals/s", "cores": ncores, "kind": "oracle",
-            "sample": f"{n} of the {N} samples, full M={M} and T={T}, FP64 C oracle, {dt:.1f} s"}
+            "sample": f"{n} of the {N} samples, full M={M} and T={T}, FP64 C oracle, {dt:.1f} s",
+            "per_core": n * T * M / dt / ncores, "cpu": host_cpu()}
+
+
+def host_cpu() -> str:
+    """The host CPU's model line from /proc/cpuinfo (or the platform's name)."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    return f"{platform.machine()} {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return platform.machine() or "unknown"
 
 
 def run_reference(args, world, rank, local):
