@@ -461,10 +461,11 @@ pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int
  * (overwritten, not accumulated); gbias: NULL or one float, likewise for the
  * bias.  Both need the workspace: ws must hold pdmp_morph_vjp_workspace(...,
  * want_param_grad = 1) bytes.  Without them ws is optional: NULL, or at least
- * pdmp_morph_vjp_workspace(..., 0) bytes; with it, RFF fields with d <= 7 and
- * k <= 16 run on the tensor cores (theta, grad s, omega . g and the
- * Hessian-vector sum as TF32 MMAs with hi/lo splits; the segment's states in
- * shared memory).  gT may alias g0. */
+ * pdmp_morph_vjp_workspace(..., 0) bytes; with it (k <= 16), RFF fields with
+ * d <= 7 run on the tensor cores (theta, grad s, omega . g and the
+ * Hessian-vector sum as TF32 MMAs with hi/lo splits) and RBF fields in
+ * d = 2, 3 on the morph's sorted tiles (expanded exponent; N < 2^31), the
+ * segment's states in shared memory.  gT may alias g0. */
 size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32_t k, int32_t want_param_grad);
 pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, int32_t k,
                            const float* ckpt, const float* gT, float* g0, float* gw, float* gbias,

@@ -494,11 +494,19 @@ static bool vjp_mma_eligible(const pdmp_field* f, int32_t k) {
   return f->kind == PDMP_KIND_RFF && f->d <= 7 && k >= 1 && k <= pdmp::kVjpMmaMaxSegment;
 }
 
+// the sorted-tile VJP: RBF fields in d = 2, 3, segments of at most 16 steps, no parameter gradient
+static bool vjp_tiles_eligible(const pdmp_field* f, int64_t N, int32_t k) {
+  return f->kind == PDMP_KIND_RBF && (f->d == 2 || f->d == 3) && k >= 1 && k <= pdmp::kVjpMmaMaxSegment &&
+         N <= (int64_t)INT32_MAX;
+}
+
 size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32_t k, int32_t want_param_grad) {
   (void)T;
   if (f == nullptr || N <= 0 || f->M < 1) return 0;
   if (want_param_grad) return sizeof(float) * (size_t)pdmp::vjp_blocks(N) * (size_t)(f->M + 1);
-  return vjp_mma_eligible(f, k) ? pdmp::morph_rff_mma_workspace(f->M) : 0;
+  if (vjp_mma_eligible(f, k)) return pdmp::morph_rff_mma_workspace(f->M);
+  if (vjp_tiles_eligible(f, N, k)) return pdmp::morph_rbf_fast_workspace(f->d, f->M, N);
+  return 0;
 }
 
 pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, int32_t k,
@@ -534,6 +542,8 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
   }
   if (!want && ws != nullptr && N > 0 && vjp_mma_eligible(f, k))
     return cuda_status(pdmp::vjp_rff_mma(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, ws, st));
+  if (!want && ws != nullptr && N > 0 && vjp_tiles_eligible(f, N, k))
+    return cuda_status(pdmp::vjp_rbf_fast(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, ws, st));
   return cuda_status(pdmp::morph_vjp(f->kind, f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0,
                                      want ? (float*)ws : nullptr, gw, gbias, st));
 }

@@ -73,6 +73,9 @@ int64_t vjp_blocks(int64_t N);
 constexpr int kVjpMmaMaxSegment = 16;
 cudaError_t vjp_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                         const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st);
+// the sorted-tile VJP for RBF fields (d = 2, 3, k <= kVjpMmaMaxSegment; ws: morph_rbf_fast_workspace)
+cudaError_t vjp_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
+                         const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st);
 cudaError_t morph_vjp(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                       const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias,
                       cudaStream_t st);

@@ -122,7 +122,9 @@ def test_vjp_validation():
     assert L.pdmp_morph_vjp(ctypes.byref(f), A, 8, 64, 0.01, 64, None, A, A, None, None, None, 0, None) == 1
     need = L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 1)
     assert need > 0
-    assert L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 0) == 0
+    # RBF, d = 2, no parameter gradient: the optional sorted-tile workspace (the morph's)
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 0) == L.pdmp_morph_workspace(ctypes.byref(f), 1000)
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fld(d=1)), 1000, 10, 5, 0) == 0
     assert L.pdmp_morph_vjp(ctypes.byref(f), A, 1000, 10, 0.01, 5, None, A, A, A, None, A, need - 1, None) == 3
     assert L.pdmp_morph_vjp(ctypes.byref(f), A, 1000, 10, 0.01, 5, None, A, A, A, None, None, need, None) == 1
     # RFF, d <= 7, k <= 16, no parameter gradient: the optional tensor-core table
