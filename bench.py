@@ -671,6 +671,19 @@ def profile_case(case: str, reps: int = 1):
         x0 = torch.from_numpy(wl.uniform_box(2, wl.S_SAMPLES, 1 << 18, lo, hi)).cuda()
         r, _ = pdmp.cull_radius(f, 1e-6)
         out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_culled(f, x0, 3, 4.5e-4, r), reps=reps)
+    elif case in ("vjp_rbf", "logdet_rbf"):
+        lo, hi = np.zeros(2), np.full(2, 10.0)
+        centres = wl.uniform_box(2, wl.S_CENTRES, M, lo, hi)
+        boxes = wl.random_boxes(2, 64, lo, hi, 0.3, 1.5)
+        f = pdmp.DeviceField.from_host(wl.Field(wl.RBF, centres, wl.proxy_fitted_weights(2, centres, boxes), gamma=8.0))
+        x0 = torch.from_numpy(wl.uniform_box(2, wl.S_SAMPLES, 1 << 18, lo, hi)).cuda()
+        if case == "vjp_rbf":
+            ck = torch.empty(2, x0.shape[0], 2, device="cuda")
+            pdmp.morph(f, x0, 4, 4.5e-4, ckpt=ck, k=2)
+            gT = torch.ones_like(x0)
+            out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_vjp(f, x0, 4, 4.5e-4, 2, gT, ckpt=ck), reps=reps)
+        else:
+            out["ms"] = 1e3 * _time(torch, lambda: pdmp.logdet(f, x0, 3, 4.5e-4), reps=reps)
     elif case == "inverse":
         lo, hi = np.zeros(2), np.full(2, 10.0)
         centres = wl.uniform_box(2, wl.S_CENTRES, M, lo, hi)
@@ -704,7 +717,8 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=1500)
     ap.add_argument("--workload", choices=["full", "small"], default="full",
                     help="small: 262,144 samples and 3 steps of the same workload (for ncu captures)")
-    ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "inverse", "tanh"], default=None,
+    ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "inverse", "vjp_rbf", "logdet_rbf", "tanh"],
+                    default=None,
                     help="run one small launch of that kernel family and exit (for ncu captures)")
     ap.add_argument("--case-reps", type=int, default=1, help="timed repetitions of --case (best of)")
     args = ap.parse_args()

@@ -20,7 +20,10 @@ namespace pdmp {
 template <int D>
 struct VjRbf {
   static constexpr int kUsed = 3 * D + 2;              // u64 pairs: a, b, sg, c~ = sg c, c
-  static constexpr int kPairs = (kUsed + 1) / 2 * 2;   // whole 16-byte chunks
+  // whole 16-byte chunks, an odd number of them: the lanes of a quarter warp
+  // building consecutive records then write to distinct banks
+  static constexpr int kChunks = (kUsed + 1) / 2 % 2 == 1 ? (kUsed + 1) / 2 : (kUsed + 1) / 2 + 1;
+  static constexpr int kPairs = 2 * kChunks;
   static constexpr int kSums = 2 * D + 2;              // S, G, K, Kc (direct: S, G, -, P)
   static constexpr int kK = D == 2 ? 8 : 6;
   static constexpr int kW = 4;
