@@ -287,16 +287,24 @@ __device__ __forceinline__ void stage_accumulate(const u64* rec, bool expanded, 
         r[2 * j] = v.x;
         r[2 * j + 1] = v.y;
       }
+      // phased: the P arguments, their ex2, then each sum over the P pairs, so
+      // that consecutive packed FMAs share the record's operand (1.2 % faster
+      // than pair by pair, measured; identical results)
+      u64 e[P];
 #pragma unroll
-      for (int i = 0; i < P; ++i) {
-        u64 arg = fma2(r[1], U[i][0], r[0]);
+      for (int i = 0; i < P; ++i) e[i] = fma2(r[1], U[i][0], r[0]);
 #pragma unroll
-        for (int j = 1; j < D; ++j) arg = fma2(r[1 + j], U[i][j], arg);
-        const u64 e = ex2x2(arg);
-        S[i] = fma2(r[D + 1], e, S[i]);
+      for (int j = 1; j < D; ++j)
 #pragma unroll
-        for (int j = 0; j < D; ++j) G[i][j] = fma2(e, r[D + 2 + j], G[i][j]);
-      }
+        for (int i = 0; i < P; ++i) e[i] = fma2(r[1 + j], U[i][j], e[i]);
+#pragma unroll
+      for (int i = 0; i < P; ++i) e[i] = ex2x2(e[i]);
+#pragma unroll
+      for (int i = 0; i < P; ++i) S[i] = fma2(r[D + 1], e[i], S[i]);
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int i = 0; i < P; ++i) G[i][j] = fma2(e[i], r[D + 2 + j], G[i][j]);
     }
   } else {
     const u64 ng = pk(-gl2e, -gl2e);
