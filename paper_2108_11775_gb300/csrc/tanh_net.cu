@@ -6,18 +6,12 @@
 // backward pass  v2 = w3 (.) (1 - h2^2),  u1 = W2^T v2,  g1 = u1 (.) (1 - h1^2),
 // grad s = W1^T g1.
 //
-// Kernel.  A persistent block of 128 threads owns tiles of 64 samples and keeps
-// their state in shared memory across all T steps.  Both dense H x H products
-// of a step (W2 h1 forward, W2^T v2 backward) run as register tiles: a thread
-// computes 4 samples x 8 units, with packed f32x2 FMAs over pairs of units
-// (the weight pair from shared memory, the activation duplicated), reading
-// per inner step one 16-byte activation vector and two 16-byte weight pairs.
-// W2 is staged once per block in both layouts (unit pairs of a column for the
-// forward product, of a row for the backward one); the activation tile holds
-// h1 for the forward product and then v2 for the backward one, and each
-// thread keeps 1 - h1^2 of its own units in registers (62.6 KB of shared
-// memory a block for H = 64: three blocks per SM).  Partial sums over the
-// 8 unit groups are added in a fixed order, so results are deterministic.
+// Kernel.  A persistent block of 128 threads owns tiles of 64 samples and
+// keeps their state in shared memory across all T steps; both dense H x H
+// products of a step run on the tensor cores (below).  An earlier FP32 kernel
+// (4-sample x 8-unit register tiles of packed f32x2 FMAs) ran at 0.58 of the
+// FP32 roofline on the d = 2, H = 64 workload; this one at 0.70 (1.21x), and
+// 1.53x for d = 3, H = 32.
 #include "fast_tile.cuh"
 #include "kernels.cuh"
 
@@ -25,199 +19,222 @@ namespace pdmp {
 
 constexpr int kNetThreads = 128;
 constexpr int kNetTile = 64;     // samples per tile
-constexpr int kNetSG = 16;       // sample groups of 4
-constexpr int kNetUG = 8;        // unit groups of 8 (for H = 64; of 4 for H = 32)
 
+// Both H x H products on the tensor cores (m16n8k8 TF32,
+// hi/lo splits of both operands, three MMAs each).  A warp owns 16 samples
+// (one MMA row tile) and needs no other warp within a step.
+//   forward   A2 = H1 W2^T + b2:  A = h1 (rows: samples, k: units j),
+//             B[k = j][n = i] = W2[i][j]
+//   backward  U1 = V2 W2:         A = v2 = w3 (.) (1 - h2^2), B = W2
+// Lane (g, t) evaluates layer 1 exactly at its A-fragment positions (units
+// 8kk + t and 8kk + t + 4 of samples g and g + 8).  The forward D fragment
+// (units 8n + 2t, 8n + 2t + 1) is the backward A fragment once k slot t holds
+// unit 8kk + 2t and slot t + 4 unit 8kk + 2t + 1; the backward's output
+// columns are permuted (column 8n + 2t + e <-> unit 8n + t + 4e) so that u1
+// arrives at the lane's own layer-1 units, where 1 - h1^2 waits in registers.
+// The B fragments of both products (hi, lo) are built once per block.
 template <int H>
-struct NetSmem {
-  static constexpr int kUnitsPerThread = H / kNetUG;             // 8 (H = 64) or 4 (H = 32)
-  static constexpr int kPairsPerThread = kUnitsPerThread / 2;
-  // offsets in floats
-  static constexpr int kW2f = 0;                                  // forward pairs: [j][i/2] (W2[i][j], W2[i+1][j])
-  static constexpr int kW2b = kW2f + H * H;                       // backward pairs: [i][j/2] = W2 row-major
-  static constexpr int kH1 = kW2b + H * H;                        // h1 [j][sample], then v2 [i][sample]
-  static constexpr int kV2 = kH1;
-  static constexpr int kW1 = kH1 + H * kNetTile;                  // W1: H x d (d <= 4)
+struct NetMma {
+  static constexpr int kNT = H / 8;                          // n tiles = k steps
+  static constexpr int kFrag = kNT * kNT * 32;               // float4 fragments (hi, lo) per product
+  static constexpr int kW1 = 2 * kFrag * 4;                  // floats: W1 (H x 4)
   static constexpr int kB1 = kW1 + H * 4;
   static constexpr int kB2 = kB1 + H;
   static constexpr int kW3 = kB2 + H;
-  static constexpr int kX = kW3 + H;                              // x: [sample][4]
-  static constexpr int kSP = kX + kNetTile * 4;                   // s partials: [ug][sample]
-  static constexpr int kGP = kSP + kNetUG * kNetTile;             // grad partials: [ug][sample][4]
-  static constexpr int kEnd = kGP + kNetUG * kNetTile * 4;
+  static constexpr int kX = kW3 + H;                         // [64 samples][4]
+  static constexpr int kT1Row = H + 4;                       // padded: rows 4 banks apart
+  static constexpr int kT1 = kX + kNetTile * 4;              // 1 - h1^2: [64 samples][H + 4]
+  static constexpr int kEnd = kT1 + kNetTile * kT1Row;
   static constexpr size_t bytes() { return (size_t)kEnd * sizeof(float); }
 };
 
-__device__ __forceinline__ u64 dup2(float v) { return pk(v, v); }
+__device__ __forceinline__ float4 tf32_pair_split(float a, float b) {
+  const float ha = __uint_as_float(tf32_rna(a)), hb = __uint_as_float(tf32_rna(b));
+  return make_float4(ha, hb, __uint_as_float(tf32_rna(a - ha)), __uint_as_float(tf32_rna(b - hb)));
+}
 
 template <int D, int H>
 __global__ void __launch_bounds__(kNetThreads, 3)
-k_tanh_net_morph(TanhNetArgs net, const float* __restrict__ x0, int64_t N, int T, float eta, float* __restrict__ xT,
-                 float* __restrict__ ckpt, int kck) {
-  using L = NetSmem<H>;
-  constexpr int UP = L::kUnitsPerThread, PP = L::kPairsPerThread;
+k_tanh_net_mma(TanhNetArgs net, const float* __restrict__ x0, int64_t N, int T, float eta, float* __restrict__ xT,
+               float* __restrict__ ckpt, int kck) {
+  using L = NetMma<H>;
+  constexpr int NT = L::kNT;
   extern __shared__ __align__(16) float sm[];
-  const int tid = threadIdx.x;
-  const int sg = tid & (kNetSG - 1), ug = tid >> 4;   // 16 sample groups x 8 unit groups
-  // stage the weights once
-  for (int e = tid; e < H * H; e += kNetThreads) {
-    const int i = e / H, j = e % H;                    // W2[i][j]
-    const float w = net.W2[e];
-    sm[L::kW2f + j * H + i] = w;                       // transposed: units (i, i+1) of column j adjacent
-    sm[L::kW2b + e] = w;                               // row-major: (j, j+1) adjacent
+  float4* w2f = reinterpret_cast<float4*>(sm);
+  float4* w2b = w2f + L::kFrag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  for (int e = tid; e < L::kFrag; e += kNetThreads) {
+    const int kk = e / (NT * 32), nt = (e / 32) % NT, l = e & 31, gg = l >> 2, tt = l & 3;
+    // forward: b0 = W2[8nt + gg][8kk + tt], b1 = W2[8nt + gg][8kk + tt + 4]
+    const float f0 = net.W2[(8 * nt + gg) * H + 8 * kk + tt], f1 = net.W2[(8 * nt + gg) * H + 8 * kk + tt + 4];
+    // backward: rows (units i) 8kk + 2tt, 8kk + 2tt + 1; column gg <-> unit j = 8nt + gg / 2 + 4 (gg % 2)
+    const int j = 8 * nt + (gg >> 1) + 4 * (gg & 1);
+    const float q0 = net.W2[(8 * kk + 2 * tt) * H + j], q1 = net.W2[(8 * kk + 2 * tt + 1) * H + j];
+    w2f[e] = tf32_pair_split(f0, f1);
+    w2b[e] = tf32_pair_split(q0, q1);
   }
-  for (int e = tid; e < H * D; e += kNetThreads) sm[L::kW1 + e] = net.W1[e];
+  for (int e = tid; e < H * D; e += kNetThreads) sm[L::kW1 + (e / D) * 4 + e % D] = net.W1[e];
   for (int e = tid; e < H; e += kNetThreads) {
     sm[L::kB1 + e] = net.b1[e];
     sm[L::kB2 + e] = net.b2[e];
     sm[L::kW3 + e] = net.w3[e];
   }
   __syncthreads();
+  const u64 c12 = pk(6144.0f, 6144.0f), nc12 = pk(-6144.0f, -6144.0f), mone = pk(-1.0f, -1.0f);
+  const u64 c13 = pk(8193.0f, 8193.0f);
+  const int r0 = warp * 16 + g, r1 = r0 + 8;                 // this lane's two samples in the tile
   const int64_t ntiles = (N + kNetTile - 1) / kNetTile;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t n0 = tile * kNetTile;
-    const int nt = (int)min64(kNetTile, N - n0);
+    const int nt_s = (int)min64(kNetTile, N - n0);
     for (int e = tid; e < kNetTile * D; e += kNetThreads) {
       const int s = e / D;
-      sm[L::kX + s * 4 + e % D] = s < nt ? x0[n0 * D + e] : 0.0f;
+      sm[L::kX + s * 4 + e % D] = s < nt_s ? x0[n0 * D + e] : 0.0f;
     }
     __syncthreads();
-    for (int t = 0; t < T; ++t) {
-      // layer 1 (h1 for this thread's 4 samples x UP units); the thread keeps
-      // 1 - h1^2 of exactly the units whose backward it computes
-      float t1[4][UP];
+    for (int step = 0; step < T; ++step) {
+      float xr[2][D];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int s = sg * 4 + q;
-        float xs[D];
+      for (int k = 0; k < D; ++k) {
+        xr[0][k] = sm[L::kX + r0 * 4 + k];
+        xr[1][k] = sm[L::kX + r1 * 4 + k];
+      }
+      // forward product, layer 1 evaluated per k step at the A-fragment positions
+      // (1 - h1^2 kept in shared memory at the same positions for the backward)
+      float acc[NT][4];
 #pragma unroll
-        for (int k = 0; k < D; ++k) xs[k] = sm[L::kX + s * 4 + k];
+      for (int nt = 0; nt < NT; ++nt) {
+        const float ba = sm[L::kB2 + 8 * nt + 2 * t], bb = sm[L::kB2 + 8 * nt + 2 * t + 1];
+        acc[nt][0] = ba;
+        acc[nt][1] = bb;
+        acc[nt][2] = ba;
+        acc[nt][3] = bb;
+      }
+#pragma unroll 1
+      for (int kk = 0; kk < NT; ++kk) {
+        float h[4];
 #pragma unroll
-        for (int u = 0; u < UP; ++u) {
-          const int i = ug * UP + u;
-          float a = sm[L::kB1 + i];
+        for (int q = 0; q < 4; ++q) {
+          const int unit = 8 * kk + t + 4 * (q >> 1);
+          float a = sm[L::kB1 + unit];
 #pragma unroll
-          for (int k = 0; k < D; ++k) a = fmaf(sm[L::kW1 + i * D + k], xs[k], a);
-          const float h = tanhf(a);
-          sm[L::kH1 + i * kNetTile + s] = h;
-          t1[q][u] = fmaf(-h, h, 1.0f);
+          for (int k = 0; k < D; ++k) a = fmaf(sm[L::kW1 + unit * 4 + k], xr[q & 1][k], a);
+          h[q] = tanhf(a);
+          sm[L::kT1 + ((q & 1) ? r1 : r0) * L::kT1Row + unit] = fmaf(-h[q], h[q], 1.0f);
+        }
+        // |h| <= 1: the shift split (exact TF32 head, the tail read as TF32)
+        const u64 a01 = pk(h[0], h[1]), a23 = pk(h[2], h[3]);
+        const u64 h01 = add2(add2(a01, c12), nc12), h23 = add2(add2(a23, c12), nc12);
+        const u64 l01 = fma2(h01, mone, a01), l23 = fma2(h23, mone, a23);
+        float ah[4], al[4];
+        upk(h01, ah[0], ah[1]);
+        upk(h23, ah[2], ah[3]);
+        upk(l01, al[0], al[1]);
+        upk(l23, al[2], al[3]);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const float4 b = w2f[(kk * NT + nt) * 32 + lane];
+          mma_tf32(acc[nt], __float_as_uint(al[0]), __float_as_uint(al[1]), __float_as_uint(al[2]),
+                   __float_as_uint(al[3]), __float_as_uint(b.x), __float_as_uint(b.y));
+          mma_tf32(acc[nt], __float_as_uint(ah[0]), __float_as_uint(ah[1]), __float_as_uint(ah[2]),
+                   __float_as_uint(ah[3]), __float_as_uint(b.z), __float_as_uint(b.w));
+          mma_tf32(acc[nt], __float_as_uint(ah[0]), __float_as_uint(ah[1]), __float_as_uint(ah[2]),
+                   __float_as_uint(ah[3]), __float_as_uint(b.x), __float_as_uint(b.y));
         }
       }
-      __syncthreads();
-      // layer 2: a2 = W2 h1 + b2 as a 4 x UP register tile
-      u64 acc[4][PP];
+      // h2 = tanh(a2); the logit's partial sums; v2 = w3 (.) (1 - h2^2) in place
+      float sp0 = 0.0f, sp1 = 0.0f;
 #pragma unroll
-      for (int p = 0; p < PP; ++p) {
-        const u64 b = pk(sm[L::kB2 + ug * UP + 2 * p], sm[L::kB2 + ug * UP + 2 * p + 1]);
+      for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q][p] = b;
-      }
-#pragma unroll 4
-      for (int j = 0; j < H; ++j) {
-        const float4 h = *reinterpret_cast<const float4*>(sm + L::kH1 + j * kNetTile + sg * 4);
-        const ulonglong2* wp = reinterpret_cast<const ulonglong2*>(sm + L::kW2f + j * H + ug * UP);
-        u64 w[PP];
-#pragma unroll
-        for (int p = 0; p < PP / 2; ++p) {
-          const ulonglong2 v2w = wp[p];
-          w[2 * p] = v2w.x;
-          w[2 * p + 1] = v2w.y;
+        for (int e = 0; e < 2; ++e) {
+          const float w = sm[L::kW3 + 8 * nt + 2 * t + e];
+          const float ha = tanhf(acc[nt][e]), hb = tanhf(acc[nt][2 + e]);
+          sp0 = fmaf(w, ha, sp0);
+          sp1 = fmaf(w, hb, sp1);
+          acc[nt][e] = w * fmaf(-ha, ha, 1.0f);
+          acc[nt][2 + e] = w * fmaf(-hb, hb, 1.0f);
         }
-        const u64 hv[4] = {dup2(h.x), dup2(h.y), dup2(h.z), dup2(h.w)};
+      sp0 += __shfl_xor_sync(0xffffffffu, sp0, 1);
+      sp0 += __shfl_xor_sync(0xffffffffu, sp0, 2);
+      sp1 += __shfl_xor_sync(0xffffffffu, sp1, 1);
+      sp1 += __shfl_xor_sync(0xffffffffu, sp1, 2);
+      // backward product: k slot t <-> unit 8kk + 2t, slot t + 4 <-> 8kk + 2t + 1
+      float u[NT][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+      for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-          for (int p = 0; p < PP; ++p) acc[q][p] = fma2(w[p], hv[q], acc[q][p]);
-      }
-      __syncthreads();   // every thread has read h1 before v2 takes its place
-      // h2 = tanh(a2); s partial over this thread's units; v2 = w3 (.) (1 - h2^2)
+        for (int q = 0; q < 4; ++q) u[nt][q] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int s = sg * 4 + q;
-        float sp = 0.0f;
+      for (int kk = 0; kk < NT; ++kk) {
+        // v2 has no bound: Veltkamp's split (2^13 + 1: an 11-bit head)
+        const u64 a01 = pk(acc[kk][0], acc[kk][2]), a23 = pk(acc[kk][1], acc[kk][3]);
+        const u64 g01 = mul2(a01, c13), g23 = mul2(a23, c13);
+        const u64 h01 = fma2(fma2(a01, mone, g01), mone, g01), h23 = fma2(fma2(a23, mone, g23), mone, g23);
+        const u64 l01 = fma2(h01, mone, a01), l23 = fma2(h23, mone, a23);
+        float vh[4], vl[4];
+        upk(h01, vh[0], vh[1]);
+        upk(h23, vh[2], vh[3]);
+        upk(l01, vl[0], vl[1]);
+        upk(l23, vl[2], vl[3]);
 #pragma unroll
-        for (int p = 0; p < PP; ++p) {
-          float a0, a1;
-          upk(acc[q][p], a0, a1);
-          const int i = ug * UP + 2 * p;
-          const float h0 = tanhf(a0), h1 = tanhf(a1);
-          const float w0 = sm[L::kW3 + i], w1 = sm[L::kW3 + i + 1];
-          sp = fmaf(w0, h0, sp);
-          sp = fmaf(w1, h1, sp);
-          sm[L::kV2 + i * kNetTile + s] = w0 * fmaf(-h0, h0, 1.0f);
-          sm[L::kV2 + (i + 1) * kNetTile + s] = w1 * fmaf(-h1, h1, 1.0f);
+        for (int nt = 0; nt < NT; ++nt) {
+          const float4 b = w2b[(kk * NT + nt) * 32 + lane];
+          mma_tf32(u[nt], __float_as_uint(vl[0]), __float_as_uint(vl[1]), __float_as_uint(vl[2]),
+                   __float_as_uint(vl[3]), __float_as_uint(b.x), __float_as_uint(b.y));
+          mma_tf32(u[nt], __float_as_uint(vh[0]), __float_as_uint(vh[1]), __float_as_uint(vh[2]),
+                   __float_as_uint(vh[3]), __float_as_uint(b.z), __float_as_uint(b.w));
+          mma_tf32(u[nt], __float_as_uint(vh[0]), __float_as_uint(vh[1]), __float_as_uint(vh[2]),
+                   __float_as_uint(vh[3]), __float_as_uint(b.x), __float_as_uint(b.y));
         }
-        sm[L::kSP + ug * kNetTile + s] = sp;
       }
-      __syncthreads();
-      // backward: u1 = W2^T v2 as a 4 x UP register tile over units j
+      // u[nt]: (r0, unit 8nt+t), (r0, 8nt+t+4), (r1, 8nt+t), (r1, 8nt+t+4); g1 = u1 (.) (1 - h1^2); grad = W1^T g1
+      float gp0[D], gp1[D];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int k = 0; k < D; ++k) gp0[k] = gp1[k] = 0.0f;
 #pragma unroll
-        for (int p = 0; p < PP; ++p) acc[q][p] = 0ull;
-#pragma unroll 4
-      for (int i = 0; i < H; ++i) {
-        const float4 v = *reinterpret_cast<const float4*>(sm + L::kV2 + i * kNetTile + sg * 4);
-        const ulonglong2* wp = reinterpret_cast<const ulonglong2*>(sm + L::kW2b + i * H + ug * UP);
-        u64 w[PP];
+      for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-        for (int p = 0; p < PP / 2; ++p) {
-          const ulonglong2 v2w = wp[p];
-          w[2 * p] = v2w.x;
-          w[2 * p + 1] = v2w.y;
-        }
-        const u64 vv[4] = {dup2(v.x), dup2(v.y), dup2(v.z), dup2(v.w)};
+        for (int e = 0; e < 2; ++e) {
+          const int unit = 8 * nt + t + 4 * e;
+          const float ga = u[nt][e] * sm[L::kT1 + r0 * L::kT1Row + unit];
+          const float gb = u[nt][2 + e] * sm[L::kT1 + r1 * L::kT1Row + unit];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int p = 0; p < PP; ++p) acc[q][p] = fma2(w[p], vv[q], acc[q][p]);
-      }
-      // g1 = u1 (.) (1 - h1^2); grad s partial = W1^T g1 over this thread's units
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int s = sg * 4 + q;
-        float gp[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) gp[k] = 0.0f;
-#pragma unroll
-        for (int p = 0; p < PP; ++p) {
-          float u0, u1;
-          upk(acc[q][p], u0, u1);
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int j = ug * UP + 2 * p + r;
-            const float g = (r ? u1 : u0) * t1[q][2 * p + r];
-#pragma unroll
-            for (int k = 0; k < D; ++k) gp[k] = fmaf(sm[L::kW1 + j * D + k], g, gp[k]);
+          for (int k = 0; k < D; ++k) {
+            const float w = sm[L::kW1 + unit * 4 + k];
+            gp0[k] = fmaf(w, ga, gp0[k]);
+            gp1[k] = fmaf(w, gb, gp1[k]);
           }
         }
 #pragma unroll
-        for (int k = 0; k < D; ++k) sm[L::kGP + (ug * kNetTile + s) * 4 + k] = gp[k];
+      for (int k = 0; k < D; ++k) {
+        gp0[k] += __shfl_xor_sync(0xffffffffu, gp0[k], 1);
+        gp0[k] += __shfl_xor_sync(0xffffffffu, gp0[k], 2);
+        gp1[k] += __shfl_xor_sync(0xffffffffu, gp1[k], 1);
+        gp1[k] += __shfl_xor_sync(0xffffffffu, gp1[k], 2);
       }
-      __syncthreads();
-      // Euler step of Eq. (1): partial sums over the unit groups in a fixed order
-      if (tid < kNetTile) {
-        const int s = tid;
-        float sv = net.b3, g[D];
+      // Euler step of Eq. (1) for the lane's two samples (lane t = 0 of the quad writes)
+      if (t == 0) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) g[k] = 0.0f;
-        for (int u = 0; u < kNetUG; ++u) {
-          sv += sm[L::kSP + u * kNetTile + s];
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int r = h2 ? r1 : r0;
+          float d1, d2;
+          sigmoid_d12((h2 ? sp1 : sp0) + net.b3, d1, d2);
+          const float c = -eta * d1;
 #pragma unroll
-          for (int k = 0; k < D; ++k) g[k] += sm[L::kGP + (u * kNetTile + s) * 4 + k];
+          for (int k = 0; k < D; ++k)
+            sm[L::kX + r * 4 + k] = __fadd_rn(xr[h2][k], __fmul_rn(c, h2 ? gp1[k] : gp0[k]));
+          if (ckpt != nullptr && (step + 1) % kck == 0 && r < nt_s)
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+              ckpt[((int64_t)((step + 1) / kck - 1) * N + n0 + r) * D + k] = sm[L::kX + r * 4 + k];
         }
-        float d1, d2;
-        sigmoid_d12(sv, d1, d2);
-        const float c = -eta * d1;
-#pragma unroll
-        for (int k = 0; k < D; ++k) sm[L::kX + s * 4 + k] = __fadd_rn(sm[L::kX + s * 4 + k], __fmul_rn(c, g[k]));
-        if (ckpt != nullptr && (t + 1) % kck == 0 && s < nt)
-#pragma unroll
-          for (int k = 0; k < D; ++k) ckpt[((int64_t)((t + 1) / kck - 1) * N + n0 + s) * D + k] = sm[L::kX + s * 4 + k];
       }
-      __syncthreads();
+      __syncwarp();
     }
-    for (int e = tid; e < nt * D; e += kNetThreads) xT[n0 * D + e] = sm[L::kX + (e / D) * 4 + e % D];
+    __syncthreads();
+    for (int e = tid; e < nt_s * D; e += kNetThreads) xT[n0 * D + e] = sm[L::kX + (e / D) * 4 + e % D];
     __syncthreads();
   }
 }
@@ -268,16 +285,16 @@ __global__ void k_tanh_net_query(TanhNetArgs net, const float* __restrict__ x, i
 template <int D, int H>
 static cudaError_t launch_net(const TanhNetArgs& net, const float* x0, int64_t N, int T, float eta, float* xT,
                               float* ckpt, int k, cudaStream_t st) {
-  constexpr size_t smem = NetSmem<H>::bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_tanh_net_morph<D, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr size_t smem = NetMma<H>::bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_tanh_net_mma<D, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tanh_net_morph<D, H>, kNetThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tanh_net_mma<D, H>, kNetThreads, smem);
   const int64_t ntiles = (N + kNetTile - 1) / kNetTile;
   const int64_t grid = min64(ntiles, (int64_t)sms * (per_sm > 0 ? per_sm : 1));
-  k_tanh_net_morph<D, H><<<(unsigned)grid, kNetThreads, smem, st>>>(net, x0, N, T, eta, xT, ckpt, k);
+  k_tanh_net_mma<D, H><<<(unsigned)grid, kNetThreads, smem, st>>>(net, x0, N, T, eta, xT, ckpt, k);
   return cudaGetLastError();
 }
 
