@@ -507,6 +507,12 @@ def extra_rff(pdmp, torch, n_sms, pk):
     g0 = torch.empty_like(x0)
     t_vjp = _time(torch, lambda: pdmp.morph_vjp(f, x0, T, eta, k, gT, ckpt=ck, g0=g0), reps=2)
     t_ld = _time(torch, lambda: pdmp.logdet(f, x0, T, eta), reps=1)
+    # the inverse of the forward's output (Eq. 2), on the tensor cores
+    y = torch.empty_like(x0)
+    wk_inv = torch.zeros(1, dtype=torch.int64, device="cuda")
+    t_inv = _time(torch, lambda: pdmp.morph_inverse(f, out, T, eta, out=y), reps=1)
+    pdmp.morph_inverse(f, out, T, eta, out=y, work=wk_inv)
+    inv_rt = float((y - x0).abs().max())
     work = float(N) * T * M
     d = 7
     clk = n_sms * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
@@ -522,7 +528,9 @@ def extra_rff(pdmp, torch, n_sms, pk):
     return {**rates, "unit": "feature-evals/s",
             "roofline_frac": {k: rates[k] / peaks[k] for k in rates}, "roofline_peak": peaks,
             "mufu_frac": {k: rates[k] / (clk * mufu) for k in rates}, "mufu_peak": clk * mufu,
-            "ms": {"forward": 1e3 * t_fwd, "vjp": 1e3 * t_vjp, "logdet": 1e3 * t_ld},
+            "ms": {"forward": 1e3 * t_fwd, "vjp": 1e3 * t_vjp, "logdet": 1e3 * t_ld, "inverse": 1e3 * t_inv},
+            "inverse": {"value": float(wk_inv.item()) / t_inv, "unit": "feature-evals/s performed",
+                        "mean_iterations_per_step": float(wk_inv.item()) / work, "round_trip_max_abs": inv_rt},
             "note": "VJP counts its recompute pass and its Hessian-vector pass (2 N T M); roofline_frac uses the "
                     "FP32-operation count of each pass (above 1 where the tensor cores take that work), "
                     "mufu_frac the sin/cos bound every pass shares"}

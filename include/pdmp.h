@@ -428,8 +428,10 @@ pdmp_status pdmp_cull_radius(const pdmp_field* f, float eps, float* r_cut, doubl
  * ws: NULL, or ws_bytes >= pdmp_morph_workspace(f, N) bytes of device
  * scratch.  With a workspace, RBF fields in d = 2 or 3 run on the forward's
  * spatially sorted tiles (blocks of 320 samples in Hilbert order, the
- * expanded exponent about the tile's current centre; N < 2^31); other fields
- * and ws = NULL use blocks of 256 samples in input order, every feature
+ * expanded exponent about the tile's current centre; N < 2^31) and RFF
+ * fields with d <= 7 on the tensor cores (blocks of 128 samples, each
+ * iteration one pass of the morph's tensor-core sweep); other fields and
+ * ws = NULL use blocks of 256 samples in input order, every feature
  * evaluated directly.  work (device, 8-byte aligned, may be NULL) is
  * incremented by the feature evaluations performed (per block, its
  * iterations summed over the steps times its samples times M). */

@@ -308,6 +308,8 @@ cudaError_t morph_inverse(int kind, int d, const FieldArgs& fa, const float* z, 
     if (d == 2) return launch_inverse_fast<2>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
     return launch_inverse_fast<3>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
   }
+  if (ws != nullptr && kind == PDMP_KIND_RFF && d <= 7)
+    return inverse_rff_mma(d, fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
 #define PDMP_CASE(KD, DD) \
   if (kind == KD && d == DD) return launch_inverse<KD, DD>(fa, z, N, T, eta, tol, maxit, y, iters, work, st);
   PDMP_CASE(PDMP_KIND_RBF, 1) PDMP_CASE(PDMP_KIND_RBF, 2) PDMP_CASE(PDMP_KIND_RBF, 3)

@@ -84,6 +84,9 @@ cudaError_t logdet(int kind, int d, const FieldArgs& fa, const float* x0, int64_
                    float* xT, void* ws, cudaStream_t st);
 cudaError_t logdet_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
                            float* xT, void* ws, cudaStream_t st);
+// the inverse map for RFF fields (d <= 7) on the tensor cores (ws: morph_rff_mma_workspace)
+cudaError_t inverse_rff_mma(int d, const FieldArgs& fa, const float* z, int64_t N, int T, float eta, float tol,
+                            int maxit, float* y, int32_t* iters, unsigned long long* work, void* ws, cudaStream_t st);
 // RBF, d = 2, 3 on sorted tiles (ws: morph_rbf_fast_workspace)
 cudaError_t logdet_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
                             float* xT, void* ws, cudaStream_t st);

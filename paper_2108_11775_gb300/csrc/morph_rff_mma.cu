@@ -646,6 +646,108 @@ cudaError_t logdet_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t 
   return cudaErrorInvalidValue;
 }
 
+// Inverse of the T-step map (Eq. 2) for RFF fields, d <= 7: each Euler step,
+// last first, undone by the fixed point y = z + eta grad c(y), every
+// iteration one pass of the forward's tensor-core sweep.  The block iterates
+// until none of its samples moves by more than tol (1 + |y|) per coordinate,
+// or maxit times (the sweep synchronises the block, so the stopping test is
+// block-wide).
+template <int D>
+__global__ void __launch_bounds__(kRmWarps * 32, 4)
+k_inverse_rff_mma(const float* __restrict__ tab, int nstage, float bias, const float* __restrict__ z0, int64_t N,
+                  int T, float eta, float tol, int maxit, float* __restrict__ y_out, int32_t* __restrict__ iters,
+                  unsigned long long* __restrict__ work, int64_t M) {
+  extern __shared__ __align__(16) float sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  float* ys = sm + 2 * kRmStageFloats + warp * (2 * kRmWarpSamples * 8);   // iterate [32][8], column 7 = 1
+  float* zs = ys + kRmWarpSamples * 8;                                     // target  [32][8]
+  const int64_t s0 = (int64_t)blockIdx.x * kRmSamples + warp * kRmWarpSamples;
+  rm_load_rows<D>(z0, s0, N, 1.0f, zs);
+  int worst = 0;
+  long long total = 0;
+  for (int step = T - 1; step >= 0; --step) {
+    for (int i = lane; i < kRmWarpSamples * 8; i += 32) ys[i] = zs[i];
+    __syncwarp();
+    int it = 0;
+    bool moving = true;
+    while (moving && it < maxit) {
+      uint32_t ah[kRmRows][4], al[kRmRows][4];
+      rm_frags(ys, g, t, ah, al);
+      float G[kRmRows][4], P[kRmRows][4];
+      u64 S[kRmRows][2];
+      rm_sweep<false>(tab, nstage, sm, ah, al, ah, al, S, G, P);
+      bool mv = false;
+#pragma unroll
+      for (int r = 0; r < kRmRows; ++r)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const float s = rm_logit(S, r, hh);
+          float d1, d2;
+          sigmoid_d12(s + bias, d1, d2);
+          const float c = eta * d1;
+          const int row = r * 16 + g + 8 * hh;
+          const bool act = s0 + row < N;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int j = 2 * t + e;
+            if (j < D) {
+              const float yn = fmaf(c, G[r][2 * hh + e], zs[row * 8 + j]);   // z + eta sigma'(s) grad s(y)
+              if (act && fabsf(yn - ys[row * 8 + j]) > tol * (1.0f + fabsf(yn))) mv = true;
+              ys[row * 8 + j] = yn;
+            }
+          }
+        }
+      __syncwarp();
+      ++it;
+      moving = __syncthreads_or(mv) != 0;
+    }
+    worst = it > worst ? it : worst;
+    total += it;
+    for (int i = lane; i < kRmWarpSamples * 8; i += 32) zs[i] = ys[i];
+    __syncwarp();
+  }
+  rm_store_rows<D>(zs, s0, N, y_out);
+  if (iters)
+    for (int r = lane; r < kRmWarpSamples; r += 32)
+      if (s0 + r < N) iters[s0 + r] = worst;
+  if (work != nullptr && threadIdx.x == 0) {
+    const int64_t first = (int64_t)blockIdx.x * kRmSamples;
+    const int64_t cnt = min64((int64_t)kRmSamples, N - first);
+    atomicAdd(work, (unsigned long long)total * (unsigned long long)cnt * (unsigned long long)M);
+  }
+}
+
+template <int D>
+static cudaError_t launch_inverse_rff_mma(const FieldArgs& fa, const float* z, int64_t N, int T, float eta, float tol,
+                                          int maxit, float* y, int32_t* iters, unsigned long long* work, void* ws,
+                                          cudaStream_t st) {
+  float* tab = reinterpret_cast<float*>(ws);
+  const int64_t n_kt = rm_tiles(fa.M);
+  k_rff_mma_table<D, false><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
+  constexpr size_t smem = (2 * (size_t)kRmStageFloats + (size_t)kRmWarps * 2 * kRmWarpSamples * 8) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_inverse_rff_mma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((N + kRmSamples - 1) / kRmSamples);
+  k_inverse_rff_mma<D><<<blocks, kRmWarps * 32, smem, st>>>(tab, (int)(n_kt / kRmStageKT), fa.bias, z, N, T, eta, tol,
+                                                            maxit, y, iters, work, fa.M);
+  return cudaGetLastError();
+}
+
+cudaError_t inverse_rff_mma(int d, const FieldArgs& fa, const float* z, int64_t N, int T, float eta, float tol,
+                            int maxit, float* y, int32_t* iters, unsigned long long* work, void* ws, cudaStream_t st) {
+  switch (d) {
+    case 1: return launch_inverse_rff_mma<1>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
+    case 2: return launch_inverse_rff_mma<2>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
+    case 3: return launch_inverse_rff_mma<3>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
+    case 4: return launch_inverse_rff_mma<4>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
+    case 5: return launch_inverse_rff_mma<5>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
+    case 6: return launch_inverse_rff_mma<6>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
+    case 7: return launch_inverse_rff_mma<7>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 // the tensor-core VJP keeps a segment of states in shared memory: k <= 16
 size_t vjp_rff_mma_smem(int k) {
   return (2 * (size_t)kRmStageFloats + (size_t)kRmWarps * (k + 1) * kRmWarpSamples * 8) * sizeof(float);

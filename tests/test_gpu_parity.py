@@ -580,6 +580,34 @@ def test_inverse_sorted_tiles_ragged_in_place_and_work(d, N):
     assert np.abs(zc.cpu().numpy() - x0).max() > 1e-3
 
 
+@pytest.mark.parametrize("d,N", [(7, 257), (3, 300)])
+def test_inverse_tensor_cores_rff(d, N):
+    """RFF, d <= 7, with the workspace: the inverse on the tensor cores
+    (ragged blocks, in place, the work counter) against the oracle, the round
+    trip and the direct kernel."""
+    f = wl.random_field(44 + d, wl.RFF, d, 300, wscale=6.0, bias=0.1)
+    lo, hi = np.full(d, -np.pi), np.full(d, np.pi)
+    eta, _ = rff_eta_sampled(f, lo, hi, n=600)
+    T = 10
+    x0 = wl.uniform_box(45 + d, 3, N, lo, hi)
+    fld = pdmp.DeviceField.from_host(f)
+    z = pdmp.morph(fld, dev(x0), T, eta)
+    zc = z.clone()
+    work = torch.zeros(1, dtype=torch.int64, device="cuda")
+    y, its = pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=60, want_iters=True, out=z, work=work)
+    assert y.data_ptr() == z.data_ptr()
+    y, its = y.cpu().numpy(), its.cpu().numpy()
+    ref, _ = oracle.morph_inverse(f, zc.cpu().numpy(), T, eta, tol=1e-13, maxit=200)
+    assert max_abs(y, ref) <= 1e-4
+    assert max_abs(y, x0) <= 1e-4
+    assert 1 <= its.min() and its.max() < 60
+    wv = int(work.item())
+    assert wv % f.M == 0 and T * N * f.M <= wv <= T * 60 * N * f.M
+    yd = pdmp.morph_inverse(fld, zc, T, eta, tol=1e-6, maxit=60, fast=False).cpu().numpy()
+    assert max_abs(y, yd) <= 1e-4
+    assert np.abs(zc.cpu().numpy() - x0).max() > 1e-3
+
+
 def test_inverse_fitted_2d_sampled_at_the_bench_size():
     """The inverse as the benchmark runs it: the first 2^18 samples of the
     2-D fitted workload morphed through T = 50 steps, then inverted on sorted
