@@ -76,3 +76,58 @@ def test_non_finite_samples_stay_local():
         ref = oracle.morph(w1.field, x0[idx], w1.T, eta)
         assert max_abs(out[idx], ref) <= 1e-4
         assert np.isfinite(out[good]).all()
+
+
+def test_rff_tensor_cores_many_features():
+    """7-D random Fourier field with M = 2^17 features on the tensor-core
+    kernels (a 50 MB fragment table, 1024 stages): the morph, the log-det and
+    the VJP on sampled samples against the oracle."""
+    M = 1 << 17
+    f = wl.random_field(63, wl.RFF, 7, M, wscale=6.0, bias=0.1)
+    lo, hi = np.full(7, -np.pi), np.full(7, np.pi)
+    L, _ = oracle.lipschitz(f)
+    eta = float(np.float32(0.5 / L))
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    N, T = 4096, 2
+    x0 = wl.uniform_box(63, 3, N, lo, hi)
+    gT = wl.f32(wl.rng(63, wl.S_COTANGENT).standard_normal((N, 7)))
+    idx = np.arange(0, N, 171)
+    xT = pdmp.morph(fld, dev(x0), T, eta).cpu().numpy()
+    assert max_abs(xT[idx], oracle.morph(f, x0[idx], T, eta)) <= 1e-4
+    ld = pdmp.logdet(fld, dev(x0), T, eta).cpu().numpy()
+    ref_ld, _, _ = oracle.logdet(f, x0[idx], T, eta)
+    assert max_abs(ld[idx], ref_ld) <= 1e-4 * T
+    g0 = pdmp.morph_vjp(fld, dev(x0), T, eta, T, dev(gT)).cpu().numpy()
+    r0 = oracle.morph_vjp(f, x0[idx], T, eta, gT[idx])
+    assert np.linalg.norm(g0[idx] - r0) <= 1e-4 * np.linalg.norm(r0)
+    assert pdmp.stream_status()[0] == 0
+
+
+def test_rff_non_finite_samples_stay_local():
+    """On the tensor-core kernels a NaN or infinite sample sits in one row of
+    its 16 x 8 tiles: its own outputs are non-finite, every other sample's
+    (also in its tiles and quads) match the oracle."""
+    f = wl.random_field(64, wl.RFF, 7, 300, wscale=6.0, bias=0.1)
+    lo, hi = np.full(7, -np.pi), np.full(7, np.pi)
+    L, _ = oracle.lipschitz(f)
+    eta = float(np.float32(0.5 / L))
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    N, T = 512, 4
+    x0 = wl.uniform_box(64, 3, N, lo, hi)
+    bad = np.array([3, 11, 200, 511])
+    x0[bad[0], 0] = np.nan
+    x0[bad[1], 6] = np.inf
+    x0[bad[2]] = -np.inf
+    x0[bad[3], 3] = np.nan
+    good = np.setdiff1d(np.arange(N), bad)
+    out = pdmp.morph(fld, dev(x0), T, eta).cpu().numpy()
+    assert not np.isfinite(out[bad]).all(axis=1).any()
+    assert np.isfinite(out[good]).all()
+    idx = good[::29]
+    assert max_abs(out[idx], oracle.morph(f, x0[idx], T, eta)) <= 1e-4
+    gT = np.ones((N, 7), np.float32)
+    g0 = pdmp.morph_vjp(fld, dev(x0), T, eta, 2, dev(gT)).cpu().numpy()
+    assert np.isfinite(g0[good]).all()
+    r0 = oracle.morph_vjp(f, x0[idx], T, eta, gT[idx])
+    assert np.linalg.norm(g0[idx] - r0) <= 1e-4 * np.linalg.norm(r0)
+    assert pdmp.stream_status()[0] == 0
