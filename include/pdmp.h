@@ -55,6 +55,11 @@ typedef int32_t pdmp_status;
 #define PDMP_ERR_DEVICE_FLAG          7  /* a kernel recorded a numerical failure */
 #define PDMP_ERR_UNSUPPORTED          8  /* valid request this build does not handle */
 
+/* Bits of the device flag (the detail of PDMP_ERR_DEVICE_FLAG). */
+#define PDMP_FLAG_NONPOSITIVE_PIVOT   1  /* log-det: I - eta Hess c not positive definite at some step */
+#define PDMP_FLAG_FIT_NONFINITE       2  /* fit: the loss became NaN or infinite */
+#define PDMP_FLAG_NOT_CONVERGED       4  /* inverse: a block stopped at maxit iterations */
+
 #define PDMP_KIND_RBF 0
 #define PDMP_KIND_RFF 1
 
@@ -424,7 +429,8 @@ pdmp_status pdmp_cull_radius(const pdmp_field* f, float eps, float* r_cut, doubl
  * eta L < 1), iterated until every sample of a block moves by at most
  * tol * (1 + |y|) per coordinate, or maxit times.  iters (N, may be NULL)
  * receives, per sample, the largest number of iterations any step of its
- * block used (maxit means the tolerance was not reached).  y may alias z.
+ * block used; a block that stops at maxit without reaching the tolerance
+ * raises PDMP_FLAG_NOT_CONVERGED in the device flag.  y may alias z.
  * ws: NULL, or ws_bytes >= pdmp_morph_workspace(f, N) bytes of device
  * scratch.  With a workspace, RBF fields in d = 2 or 3 run on the forward's
  * spatially sorted tiles (blocks of 320 samples in Hilbert order, the

@@ -15,10 +15,9 @@ __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return
 // log-det Cholesky) are OR-ed into this word; pdmp_stream_status reads and
 // clears it.
 enum : int32_t {
-  FLAG_NONPOSITIVE_PIVOT = 1,
-  FLAG_FIT_NONFINITE = 2,
-  FLAG_BATCH_QUEUE = 4,
-  FLAG_SURROGATE = 8,
+  FLAG_NONPOSITIVE_PIVOT = PDMP_FLAG_NONPOSITIVE_PIVOT,
+  FLAG_FIT_NONFINITE = PDMP_FLAG_FIT_NONFINITE,
+  FLAG_NOT_CONVERGED = PDMP_FLAG_NOT_CONVERGED,
 };
 extern __device__ int32_t g_device_flag;
 

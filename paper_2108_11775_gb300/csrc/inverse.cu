@@ -43,6 +43,7 @@ k_morph_inverse(FieldArgs fa, const float* __restrict__ z0, int64_t N, int T, fl
 #pragma unroll
       for (int j = 0; j < D; ++j) y[k][j] = z[k][j];
     int it = 0;
+    bool converged = false;
     for (; it < maxit; ++it) {
       float s[K], gs[K][D];
 #pragma unroll
@@ -79,9 +80,11 @@ k_morph_inverse(FieldArgs fa, const float* __restrict__ z0, int64_t N, int T, fl
       }
       if (!__syncthreads_or(moving)) {
         ++it;
+        converged = true;
         break;
       }
     }
+    if (!converged && threadIdx.x == 0) raise_flag(FLAG_NOT_CONVERGED);
     worst = it > worst ? it : worst;
     total += it;
 #pragma unroll
@@ -223,6 +226,7 @@ __device__ __forceinline__ void inverse_tile(const TileArgs& a, float tol, int m
       // every warp has read the reduction buffer before the next iteration rebuilds the stages
       moving = __syncthreads_or(mv) != 0;
     }
+    if (moving && threadIdx.x == 0) raise_flag(FLAG_NOT_CONVERGED);
     worst = it > worst ? it : worst;
     total += it;
     // the converged y is the next (earlier) step's target; every warp has

@@ -702,6 +702,7 @@ k_inverse_rff_mma(const float* __restrict__ tab, int nstage, float bias, const f
       ++it;
       moving = __syncthreads_or(mv) != 0;
     }
+    if (moving && threadIdx.x == 0) raise_flag(FLAG_NOT_CONVERGED);
     worst = it > worst ? it : worst;
     total += it;
     for (int i = lane; i < kRmWarpSamples * 8; i += 32) zs[i] = ys[i];

@@ -608,6 +608,26 @@ def test_inverse_tensor_cores_rff(d, N):
     assert np.abs(zc.cpu().numpy() - x0).max() > 1e-3
 
 
+@pytest.mark.parametrize("kind,fast", [(wl.RBF, True), (wl.RBF, False), (wl.RFF, True)])
+def test_inverse_reports_non_convergence(kind, fast):
+    """An iteration cap too small for the tolerance raises the not-converged
+    bit of the device flag (and the result is still the capped iterate);
+    enough iterations leave the flag clear."""
+    if kind == wl.RBF:
+        f, x0, T, _, eta = _vjp_case(wl.RBF)
+        x0 = np.tile(x0, (4, 1))[:1000]                    # several sorted tiles
+    else:
+        f, x0, T, _, eta = _vjp_case(wl.RFF)
+    fld = pdmp.DeviceField.from_host(f)
+    z = pdmp.morph(fld, dev(x0), T, eta)
+    assert pdmp.stream_status()[0] == 0
+    pdmp.morph_inverse(fld, z, T, eta, tol=0.0, maxit=1, fast=fast)
+    st, detail = pdmp.stream_status()
+    assert st == 7 and detail & 4
+    pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=80, fast=fast)
+    assert pdmp.stream_status()[0] == 0
+
+
 def test_inverse_fitted_2d_sampled_at_the_bench_size():
     """The inverse as the benchmark runs it: the first 2^18 samples of the
     2-D fitted workload morphed through T = 50 steps, then inverted on sorted
