@@ -88,7 +88,7 @@ const char* pdmp_status_string(pdmp_status s) {
   }
 }
 
-int32_t pdmp_version(void) { return 100; }
+int32_t pdmp_version(void) { return 200; }   // 0.2.0: the inverse, log-density and log-det take a workspace
 
 pdmp_status pdmp_stream_status(void* stream, int32_t* detail) {
   cudaStream_t st = as_stream(stream);

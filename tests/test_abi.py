@@ -35,7 +35,7 @@ def test_status_strings():
     for s in range(0, 9):
         assert L.pdmp_status_string(s)
     assert L.pdmp_status_string(12345) == b"unknown status"
-    assert L.pdmp_version() >= 100
+    assert L.pdmp_version() >= 200
 
 
 # Fake, never-dereferenced device addresses: every call below fails host
