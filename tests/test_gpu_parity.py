@@ -310,6 +310,36 @@ def test_vjp_sorted_tiles_rbf(d, N, T, k, use_ckpt):
     assert np.linalg.norm(g0 - direct) <= 1e-4 * np.linalg.norm(direct)
 
 
+def test_vjp_and_inverse_sorted_tiles_dense_3d():
+    """3-D samples dense enough (2^17 in [0,5]^3, gamma = 8: tiles of 192 or
+    320 samples span g' R^2 of about 3 to 4) that the sorted tiles take the
+    expanded form: the VJP and the inverse on sampled samples against the
+    oracle, and against the direct kernels on all."""
+    f = wl.random_field(79, wl.RBF, 3, 2048, lo=0, hi=5, gamma=8.0, wscale=2.0, bias=-0.2)
+    lo, hi = np.zeros(3), np.full(3, 5.0)
+    eta, L = rbf_eta(f, lo - 0.5, hi + 0.5, cells=16)
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    N, T, k = 1 << 17, 4, 2
+    x0 = wl.uniform_box(80, 3, N, lo, hi)
+    gT = wl.f32(wl.rng(81, wl.S_COTANGENT).standard_normal((N, 3)))
+    ck = torch.empty(T // k, N, 3, device="cuda")
+    z = pdmp.morph(fld, dev(x0), T, eta, ckpt=ck, k=k)
+    g0 = pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck).cpu().numpy()
+    y = pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=60).cpu().numpy()
+    idx = np.concatenate([np.sort(wl.rng(82, 1).choice(N, 48, replace=False)), [N - 1]])
+    r0 = oracle.morph_vjp(f, x0[idx], T, eta, gT[idx])
+    assert np.linalg.norm(g0[idx] - r0) <= 1e-4 * np.linalg.norm(r0)
+    corr = r0 - gT[idx]
+    assert np.linalg.norm((g0[idx] - gT[idx]) - corr) <= 1e-4 * np.linalg.norm(corr) + 1e-6
+    ry, _ = oracle.morph_inverse(f, z.cpu().numpy()[idx], T, eta, tol=1e-13, maxit=200)
+    assert max_abs(y[idx], ry) <= 1e-4
+    assert max_abs(y, x0) <= 1e-4
+    gd = pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck, fast=False).cpu().numpy()
+    assert np.linalg.norm(g0 - gd) <= 1e-4 * np.linalg.norm(gd)
+    yd = pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=60, fast=False).cpu().numpy()
+    assert max_abs(y, yd) <= 1e-4
+
+
 def test_vjp_fitted_2d_full_size_sampled():
     """The 2-D VJP as the benchmark runs it (N = 2^20, T = 50, k = 5, sorted
     tiles): sampled samples against the oracle at the VJP tolerance (g0 to
