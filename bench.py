@@ -700,6 +700,13 @@ def profile_case(case: str, reps: int = 1):
         x0 = torch.from_numpy(wl.uniform_box(2, wl.S_SAMPLES, 1 << 18, lo, hi)).cuda()
         z = pdmp.morph(f, x0, 2, 4.5e-4)
         out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_inverse(f, z, 2, 4.5e-4), reps=reps)
+    elif case == "inverse_rff":
+        wk = wl.config3(N=1 << 17)
+        f = pdmp.DeviceField.from_host(wk.field)
+        L, _ = pdmp.lipschitz_bound(f)
+        eta = float(np.float32(0.5 / L))
+        z = pdmp.morph(f, torch.from_numpy(wk.x0).cuda(), 4, eta)
+        out["ms"] = 1e3 * _time(torch, lambda: pdmp.morph_inverse(f, z, 4, eta), reps=reps)
     elif case == "tanh":
         net = pdmp.DeviceTanhNet.from_host(wl.tanh_net(7, 2, 64))
         L, _ = pdmp.tanh_net_lipschitz(net)
@@ -725,7 +732,8 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=1500)
     ap.add_argument("--workload", choices=["full", "small"], default="full",
                     help="small: 262,144 samples and 3 steps of the same workload (for ncu captures)")
-    ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "inverse", "vjp_rbf", "logdet_rbf", "tanh"],
+    ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "inverse", "inverse_rff", "vjp_rbf", "logdet_rbf",
+                                       "tanh"],
                     default=None,
                     help="run one small launch of that kernel family and exit (for ncu captures)")
     ap.add_argument("--case-reps", type=int, default=1, help="timed repetitions of --case (best of)")
