@@ -506,6 +506,10 @@ def extra_rff(pdmp, torch, n_sms, pk):
     t_fwd = _time(torch, lambda: pdmp.morph(f, x0, T, eta, out=out, ckpt=ck, k=k), reps=2)
     g0 = torch.empty_like(x0)
     t_vjp = _time(torch, lambda: pdmp.morph_vjp(f, x0, T, eta, k, gT, ckpt=ck, g0=g0), reps=2)
+    # with d/dw and d/dbias: a third pass per step (the weight terms) on the same tensor-core kernel
+    ws_pg = torch.empty(pdmp.morph_vjp_workspace(f, N, T, k, 1), dtype=torch.uint8, device="cuda")
+    t_pg = _time(torch, lambda: pdmp.morph_vjp(f, x0, T, eta, k, gT, ckpt=ck, g0=g0, want_param_grad=True,
+                                               ws=ws_pg), reps=1)
     t_ld = _time(torch, lambda: pdmp.logdet(f, x0, T, eta), reps=1)
     # the inverse of the forward's output (Eq. 2), on the tensor cores
     y = torch.empty_like(x0)
@@ -524,14 +528,18 @@ def extra_rff(pdmp, torch, n_sms, pk):
     peaks = {"forward": clk * min(FP32_LANES_PER_SM / (2 * d + 2), mufu),
              "vjp_per_pass": clk * min(FP32_LANES_PER_SM / (4 * d + 3), mufu),
              "logdet": clk * min(FP32_LANES_PER_SM / (2 * d + 2 + d * (d + 1) // 2), mufu)}
-    rates = {"forward": work / t_fwd, "vjp_per_pass": 2 * work / t_vjp, "logdet": work / t_ld}
+    rates = {"forward": work / t_fwd, "vjp_per_pass": 2 * work / t_vjp, "logdet": work / t_ld,
+             "vjp_param_grad_per_pass": 3 * work / t_pg}
+    peaks["vjp_param_grad_per_pass"] = peaks["vjp_per_pass"]
     return {**rates, "unit": "feature-evals/s",
             "roofline_frac": {k: rates[k] / peaks[k] for k in rates}, "roofline_peak": peaks,
             "mufu_frac": {k: rates[k] / (clk * mufu) for k in rates}, "mufu_peak": clk * mufu,
-            "ms": {"forward": 1e3 * t_fwd, "vjp": 1e3 * t_vjp, "logdet": 1e3 * t_ld, "inverse": 1e3 * t_inv},
+            "ms": {"forward": 1e3 * t_fwd, "vjp": 1e3 * t_vjp, "vjp_param_grad": 1e3 * t_pg, "logdet": 1e3 * t_ld,
+                   "inverse": 1e3 * t_inv},
             "inverse": {"value": float(wk_inv.item()) / t_inv, "unit": "feature-evals/s performed",
                         "mean_iterations_per_step": float(wk_inv.item()) / work, "round_trip_max_abs": inv_rt},
-            "note": "VJP counts its recompute pass and its Hessian-vector pass (2 N T M); roofline_frac uses the "
+            "note": "VJP counts its recompute pass and its Hessian-vector pass (2 N T M), with the parameter "
+                    "gradient also its weight pass (3 N T M); roofline_frac uses the "
                     "FP32-operation count of each pass (above 1 where the tensor cores take that work), "
                     "mufu_frac the sin/cos bound every pass shares"}
 

@@ -467,8 +467,13 @@ pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int
  * NULL to recompute each segment from x0.  k >= 1 must divide T.
  * gw: NULL, or an M vector that receives d/dw of sum_n <gT[n], x_T[n]>
  * (overwritten, not accumulated); gbias: NULL or one float, likewise for the
- * bias.  Both need the workspace: ws must hold pdmp_morph_vjp_workspace(...,
- * want_param_grad = 1) bytes.  Without them ws is optional: NULL, or at least
+ * bias.  Both need the workspace (16-byte aligned): at least the per-block
+ * rows of the sums, the size pdmp_morph_vjp_workspace(..., want_param_grad =
+ * 2) returns (else PDMP_ERR_WORKSPACE_TOO_SMALL); with the
+ * pdmp_morph_vjp_workspace(..., want_param_grad = 1) bytes and k <= 16, RFF
+ * fields with d <= 7 also run on the tensor cores (the weight terms in a
+ * second MMA pass per step; the query gives the rows alone otherwise).
+ * Without them ws is optional: NULL, or at least
  * pdmp_morph_vjp_workspace(..., 0) bytes; with it (k <= 16), RFF fields with
  * d <= 7 run on the tensor cores (theta, grad s, omega . g and the
  * Hessian-vector sum as TF32 MMAs with hi/lo splits) and RBF fields in

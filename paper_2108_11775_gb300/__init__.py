@@ -552,9 +552,11 @@ def log_density(field: DeviceField, z: torch.Tensor, T: int, eta: float, lo, hi,
     return lp, y
 
 
-def morph_vjp_workspace(field: DeviceField, N: int, T: int, k: int, want_param_grad: bool) -> int:
+def morph_vjp_workspace(field: DeviceField, N: int, T: int, k: int, want_param_grad: bool | int) -> int:
+    """Bytes of workspace for pdmp_morph_vjp; want_param_grad 1 (True) sizes it
+    for the fastest kernel, 2 for the parameter gradient's rows alone."""
     f = field.struct()
-    return int(lib().pdmp_morph_vjp_workspace(ctypes.byref(f), int(N), int(T), int(k), int(bool(want_param_grad))))
+    return int(lib().pdmp_morph_vjp_workspace(ctypes.byref(f), int(N), int(T), int(k), int(want_param_grad)))
 
 
 def morph_vjp(field: DeviceField, x0: torch.Tensor, T: int, eta: float, k: int, gT: torch.Tensor,
@@ -563,7 +565,8 @@ def morph_vjp(field: DeviceField, x0: torch.Tensor, T: int, eta: float, k: int, 
     """g0 = (dx_T/dx_0)^T gT per sample; with want_param_grad also (gw, gbias)
     = d/d(w, bias) of sum_n <gT[n], x_T[n]>.  Without the parameter gradient,
     ``fast`` gives the library a workspace (``ws`` or a fresh one) so that RFF
-    fields with d <= 7 and k <= 16 run on the tensor cores."""
+    fields with d <= 7 and k <= 16 run on the tensor cores; with it, the
+    parameter gradient does too (``fast=False``: the direct kernel)."""
     N, d = x0.shape[0], field.d
     if g0 is None:
         g0 = torch.empty_like(x0)
@@ -572,8 +575,9 @@ def morph_vjp(field: DeviceField, x0: torch.Tensor, T: int, eta: float, k: int, 
     if want_param_grad:
         gw = torch.empty(field.M, device=x0.device, dtype=torch.float32)
         gb = torch.empty(1, device=x0.device, dtype=torch.float32)
-        nbytes = morph_vjp_workspace(field, N, T, k, True)
-        ws = torch.empty(max(nbytes, 16), device=x0.device, dtype=torch.uint8)
+        nbytes = morph_vjp_workspace(field, N, T, k, 1 if fast else 2)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(max(nbytes, 16), device=x0.device, dtype=torch.uint8)
     elif fast:
         nbytes = morph_vjp_workspace(field, N, T, k, False)
         if nbytes == 0:

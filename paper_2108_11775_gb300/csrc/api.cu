@@ -489,7 +489,7 @@ pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int
   return cuda_status(pdmp::uniform_log_density(y, N, f->d, lo, hi, log_p, st));
 }
 
-// the tensor-core VJP: RFF fields with d <= 7, segments of at most 16 steps, no parameter gradient
+// the tensor-core VJP: RFF fields with d <= 7, segments of at most 16 steps
 static bool vjp_mma_eligible(const pdmp_field* f, int32_t k) {
   return f->kind == PDMP_KIND_RFF && f->d <= 7 && k >= 1 && k <= pdmp::kVjpMmaMaxSegment;
 }
@@ -500,10 +500,19 @@ static bool vjp_tiles_eligible(const pdmp_field* f, int64_t N, int32_t k) {
          N <= (int64_t)INT32_MAX;
 }
 
+// the per-block rows of the parameter gradient (either VJP kernel's blocks), rounded to 256 bytes
+static size_t vjp_rows_bytes(const pdmp_field* f, int64_t N) {
+  const int64_t blocks = std::max(pdmp::vjp_blocks(N), pdmp::vjp_rff_mma_blocks(N));
+  return (sizeof(float) * (size_t)blocks * (size_t)(f->M + 1) + 255) & ~size_t(255);
+}
+
 size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32_t k, int32_t want_param_grad) {
   (void)T;
   if (f == nullptr || N <= 0 || f->M < 1) return 0;
-  if (want_param_grad) return sizeof(float) * (size_t)pdmp::vjp_blocks(N) * (size_t)(f->M + 1);
+  if (want_param_grad) {
+    if (want_param_grad == 1 && vjp_mma_eligible(f, k)) return vjp_rows_bytes(f, N) + pdmp::morph_rff_mma_workspace(f->M);
+    return vjp_rows_bytes(f, N);
+  }
   if (vjp_mma_eligible(f, k)) return pdmp::morph_rff_mma_workspace(f->M);
   if (vjp_tiles_eligible(f, N, k)) return pdmp::morph_rbf_fast_workspace(f->d, f->M, N);
   return 0;
@@ -520,7 +529,8 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
   if (!ok_ptr(ckpt, false) || !ok_ptr(gw, false) || !ok_ptr(gbias, false)) return PDMP_ERR_INVALID_ARG;
   const bool want = gw != nullptr || gbias != nullptr;
   if (want) {
-    size_t need = pdmp_morph_vjp_workspace(f, N, T, k, 1);
+    // the rows are required; the tensor-core kernel also wants its table after them
+    size_t need = N > 0 && f->M >= 1 ? vjp_rows_bytes(f, N) : 0;
     if (need > 0 && (ws == nullptr || !aligned16(ws))) return PDMP_ERR_INVALID_ARG;
     if (ws_bytes < need) return PDMP_ERR_WORKSPACE_TOO_SMALL;
   } else if (ws != nullptr) {
@@ -541,7 +551,13 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
     return launch_status();
   }
   if (!want && ws != nullptr && N > 0 && vjp_mma_eligible(f, k))
-    return cuda_status(pdmp::vjp_rff_mma(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, ws, st));
+    return cuda_status(pdmp::vjp_rff_mma(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, nullptr, nullptr,
+                                         nullptr, ws, st));
+  if (want && N > 0 && vjp_mma_eligible(f, k) && ws_bytes >= pdmp_morph_vjp_workspace(f, N, T, k, 1)) {
+    const size_t rows_bytes = vjp_rows_bytes(f, N);
+    return cuda_status(pdmp::vjp_rff_mma(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, (float*)ws, gw, gbias,
+                                         (char*)ws + rows_bytes, st));
+  }
   if (!want && ws != nullptr && N > 0 && vjp_tiles_eligible(f, N, k))
     return cuda_status(pdmp::vjp_rbf_fast(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, ws, st));
   return cuda_status(pdmp::morph_vjp(f->kind, f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0,

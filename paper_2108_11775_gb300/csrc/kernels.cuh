@@ -69,10 +69,15 @@ cudaError_t uniform_log_density(const float* y, int64_t N, int d, const double* 
                                 cudaStream_t st);
 
 int64_t vjp_blocks(int64_t N);
-// the tensor-core VJP for RFF fields (d <= 7, segments k <= kVjpMmaMaxSegment; ws: morph_rff_mma_workspace)
+// gw[m] = sum_b rows[b][m] (m < width - 1), *gbias = sum_b rows[b][width - 1], in block order
+cudaError_t sum_vjp_rows(const float* rows, int64_t nrows, int64_t width, float* gw, float* gbias, cudaStream_t st);
+// the tensor-core VJP for RFF fields (d <= 7, segments k <= kVjpMmaMaxSegment; ws: morph_rff_mma_workspace).
+// rows: nullptr, or vjp_rff_mma_blocks(N) x (M + 1) floats for the weight and bias gradient (gw, gbias)
 constexpr int kVjpMmaMaxSegment = 16;
+int64_t vjp_rff_mma_blocks(int64_t N);
 cudaError_t vjp_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
-                        const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st);
+                        const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias, void* ws,
+                        cudaStream_t st);
 // the sorted-tile VJP for RBF fields (d = 2, 3, k <= kVjpMmaMaxSegment; ws: morph_rbf_fast_workspace)
 cudaError_t vjp_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                          const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st);

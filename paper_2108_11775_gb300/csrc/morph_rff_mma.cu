@@ -346,6 +346,77 @@ k_morph_rff_mma(const float* __restrict__ tab, int nstage, float bias, const flo
   if (TRACE) rm_store_rows<D>(xs, s0, N, traj + (int64_t)T * N * D);
 }
 
+// Weight-gradient pass at x (A fragments ah, al) with v = g (vh, vl), both
+// before the step's update of g: adds to row[m], for every feature m, the
+// block's sum over its samples of
+//   cA_n cos(theta_nm) + cB_n (grad phi_m . g_n),   grad phi_m . g = -sin(theta_m) omega_m . g,
+// with cA_n = -eta sigma''(s_n) (grad s_n . g_n) and cB_n = -eta sigma'(s_n)
+// (per lane, for its rows g and g + 8 of each row tile).  Per k tile the
+// lanes sharing t add their rows (shuffles over g), the warps' partials go
+// through shared memory and are added to the block's row in a fixed order.
+__device__ __forceinline__ void rm_gw_sweep(const float* __restrict__ tab, int nstage, float* sm, float* part,
+                                            const uint32_t (&ah)[kRmRows][4], const uint32_t (&al)[kRmRows][4],
+                                            const uint32_t (&vh)[kRmRows][4], const uint32_t (&vl)[kRmRows][4],
+                                            const float (&cA)[kRmRows][2], const float (&cB)[kRmRows][2],
+                                            float* __restrict__ row, int64_t M) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const float twopi = k2PiHi;
+  __syncthreads();   // every warp is done with the previous pass's stages
+  rm_stage_load(tab, sm);
+  for (int st = 0; st < nstage; ++st) {
+    cp_async_wait_all();
+    __syncthreads();   // stage st is visible; stage st - 1's buffer and the partials are free
+    if (st + 1 < nstage)
+      rm_stage_load(tab + (size_t)(st + 1) * kRmStageFloats, sm + ((st + 1) & 1) * kRmStageFloats);
+    const float* sb = sm + (st & 1) * kRmStageFloats;
+#pragma unroll 1
+    for (int kt = 0; kt < kRmStageKT; ++kt) {
+      const float4 bt = reinterpret_cast<const float4*>(sb + kt * kRmKtFloats)[lane];
+      const uint32_t bth0 = __float_as_uint(bt.x), bth1 = __float_as_uint(bt.y);
+      const uint32_t btl0 = __float_as_uint(bt.z), btl1 = __float_as_uint(bt.w);
+      float p0 = 0.0f, p1 = 0.0f;   // features 2t and 2t + 1 of the k tile
+#pragma unroll
+      for (int r = 0; r < kRmRows; ++r) {
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f}, o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        mma_tf32(d, al[r][0], al[r][1], al[r][2], al[r][3], bth0, bth1);
+        mma_tf32(d, ah[r][0], ah[r][1], ah[r][2], ah[r][3], btl0, btl1);
+        mma_tf32(d, ah[r][0], ah[r][1], ah[r][2], ah[r][3], bth0, bth1);
+        mma_tf32(o, vl[r][0], vl[r][1], vl[r][2], vl[r][3], bth0, bth1);
+        mma_tf32(o, vh[r][0], vh[r][1], vh[r][2], vh[r][3], btl0, btl1);
+        mma_tf32(o, vh[r][0], vh[r][1], vh[r][2], vh[r][3], bth0, bth1);
+        float f[4];
+        upk(rm_turns_to_rad(pk(d[0], d[1])), f[0], f[1]);
+        upk(rm_turns_to_rad(pk(d[2], d[3])), f[2], f[3]);
+        // element q: row g + 8 (q >> 1), feature 2t + (q & 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float c = fmaf(-cB[r][q >> 1] * twopi * sin_approx(f[q]), o[q], cA[r][q >> 1] * cos_approx(f[q]));
+          if (q & 1) p1 += c; else p0 += c;
+        }
+      }
+#pragma unroll
+      for (int off = 4; off < 32; off <<= 1) {
+        p0 += __shfl_xor_sync(0xffffffffu, p0, off);
+        p1 += __shfl_xor_sync(0xffffffffu, p1, off);
+      }
+      if (g == 0) {
+        part[warp * (kRmStageKT * 8) + kt * 8 + 2 * t] = p0;
+        part[warp * (kRmStageKT * 8) + kt * 8 + 2 * t + 1] = p1;
+      }
+    }
+    __syncthreads();   // every warp's partials of this stage
+    for (int fi = threadIdx.x; fi < kRmStageKT * 8; fi += kRmWarps * 32) {
+      const int64_t m = (int64_t)st * (kRmStageKT * 8) + fi;
+      if (m < M) {
+        float a = part[fi];
+#pragma unroll
+        for (int w = 1; w < kRmWarps; ++w) a += part[w * (kRmStageKT * 8) + fi];
+        row[m] += a;
+      }
+    }
+  }
+}
+
 // VJP of the T-step map (g_t = (I - eta Hess c(x_t)) g_{t+1}), segment by
 // segment from the checkpoints: the segment's states are recomputed into the
 // warp's shared memory (kseg x [32][8]), then each step back is one
@@ -353,12 +424,20 @@ k_morph_rff_mma(const float* __restrict__ tab, int nstage, float bias, const flo
 template <int D>
 __global__ void __launch_bounds__(kRmWarps * 32, 3)
 k_vjp_rff_mma(const float* __restrict__ tab, int nstage, float bias, const float* __restrict__ x0, int64_t N, int T,
-              float eta, int kseg, const float* __restrict__ ckpt, const float* __restrict__ gT, float* __restrict__ g0) {
+              float eta, int kseg, const float* __restrict__ ckpt, const float* __restrict__ gT, float* __restrict__ g0,
+              float* __restrict__ rows, int64_t M) {
   extern __shared__ __align__(16) float sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   float* gs = sm + 2 * kRmStageFloats + warp * (kseg + 1) * (kRmWarpSamples * 8);   // [32][8], column 7 = 0
   float* seg = gs + kRmWarpSamples * 8;                                              // kseg x [32][8]
+  // weight gradient (rows != nullptr): this block's row of rows_[blocks][M + 1], warp partials, bias partials
+  float* part = sm + 2 * kRmStageFloats + kRmWarps * (kseg + 1) * (kRmWarpSamples * 8);   // [4][128]
+  float* gbw = part + kRmWarps * kRmStageKT * 8;                                        // [4]
+  float* row = rows ? rows + (int64_t)blockIdx.x * (M + 1) : nullptr;
+  if (row)
+    for (int64_t m = threadIdx.x; m <= M; m += blockDim.x) row[m] = 0.0f;
+  float gb_acc = 0.0f;
   const int64_t s0 = (int64_t)blockIdx.x * kRmSamples + warp * kRmWarpSamples;
   rm_load_rows<D>(gT, s0, N, 0.0f, gs);
   const float twopi = k2PiHi;
@@ -385,25 +464,43 @@ k_vjp_rff_mma(const float* __restrict__ tab, int nstage, float bias, const float
       float G[kRmRows][4], P[kRmRows][4];
       u64 S[kRmRows][2];
       rm_sweep<true>(tab, nstage, sm, ah, al, vh, vl, S, G, P);
+      float D1[kRmRows][2], D2[kRmRows][2], GD[kRmRows][2];
+#pragma unroll
+      for (int r = 0; r < kRmRows; ++r)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int rw = r * 16 + g + 8 * hh;
+          sigmoid_d12(rm_logit(S, r, hh) + bias, D1[r][hh], D2[r][hh]);
+          // grad s . g over the quad (dimensions 2t, 2t + 1 per lane)
+          float gd = fmaf(G[r][2 * hh], gs[rw * 8 + 2 * t], G[r][2 * hh + 1] * gs[rw * 8 + 2 * t + 1]);
+          gd += __shfl_xor_sync(0xffffffffu, gd, 1);
+          gd += __shfl_xor_sync(0xffffffffu, gd, 2);
+          GD[r][hh] = gd;
+        }
+      if (row) {   // d/dw with g_{t+1}, before the update
+        float cA[kRmRows][2], cB[kRmRows][2];
+#pragma unroll
+        for (int r = 0; r < kRmRows; ++r)
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            cA[r][hh] = -eta * D2[r][hh] * GD[r][hh];
+            cB[r][hh] = -eta * D1[r][hh];
+            if (t == 0) gb_acc += cA[r][hh];
+          }
+        rm_gw_sweep(tab, nstage, sm, part, ah, al, vh, vl, cA, cB, row, M);
+      }
 #pragma unroll
       for (int r = 0; r < kRmRows; ++r) {
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-          const int row = r * 16 + g + 8 * hh;
-          const float s = rm_logit(S, r, hh);
-          float d1, d2;
-          sigmoid_d12(s + bias, d1, d2);
-          // grad s . g over the quad (dimensions 2t, 2t + 1 per lane)
-          float gd = fmaf(G[r][2 * hh], gs[row * 8 + 2 * t], G[r][2 * hh + 1] * gs[row * 8 + 2 * t + 1]);
-          gd += __shfl_xor_sync(0xffffffffu, gd, 1);
-          gd += __shfl_xor_sync(0xffffffffu, gd, 2);
+          const int rw = r * 16 + g + 8 * hh;
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const int j = 2 * t + e;
             if (j < D) {
               const float hv = twopi * P[r][2 * hh + e];      // (Hess s) v
-              const float gj = gs[row * 8 + j];
-              gs[row * 8 + j] = gj - eta * fmaf(d1, hv, d2 * gd * G[r][2 * hh + e]);
+              const float gj = gs[rw * 8 + j];
+              gs[rw * 8 + j] = gj - eta * fmaf(D1[r][hh], hv, D2[r][hh] * GD[r][hh] * G[r][2 * hh + e]);
             }
           }
         }
@@ -412,6 +509,18 @@ k_vjp_rff_mma(const float* __restrict__ tab, int nstage, float bias, const float
     }
   }
   rm_store_rows<D>(gs, s0, N, g0);
+  if (row) {
+    // the bias term: lanes t = 0 hold their rows' sums; warp totals, then the block's in a fixed order
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) gb_acc += __shfl_xor_sync(0xffffffffu, gb_acc, off);
+    if (lane == 0) gbw[warp] = gb_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float a = gbw[0];
+      for (int w = 1; w < kRmWarps; ++w) a += gbw[w];
+      row[M] = a;
+    }
+  }
 }
 
 template <int D>
@@ -749,36 +858,43 @@ cudaError_t inverse_rff_mma(int d, const FieldArgs& fa, const float* z, int64_t 
   return cudaErrorInvalidValue;
 }
 
+int64_t vjp_rff_mma_blocks(int64_t N) { return (N + kRmSamples - 1) / kRmSamples; }
+
 // the tensor-core VJP keeps a segment of states in shared memory: k <= 16
 size_t vjp_rff_mma_smem(int k) {
-  return (2 * (size_t)kRmStageFloats + (size_t)kRmWarps * (k + 1) * kRmWarpSamples * 8) * sizeof(float);
+  return (2 * (size_t)kRmStageFloats + (size_t)kRmWarps * (k + 1) * kRmWarpSamples * 8 +
+          (size_t)kRmWarps * kRmStageKT * 8 + kRmWarps) * sizeof(float);
 }
 
 template <int D>
 static cudaError_t launch_vjp_rff_mma(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
-                                      const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st) {
+                                      const float* ckpt, const float* gT, float* g0, float* rows, float* gw,
+                                      float* gbias, void* ws, cudaStream_t st) {
   float* tab = reinterpret_cast<float*>(ws);
   const int64_t n_kt = rm_tiles(fa.M);
   k_rff_mma_table<D, false><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
   const size_t smem = vjp_rff_mma_smem(k);
   cudaError_t e = cudaFuncSetAttribute(k_vjp_rff_mma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((N + kRmSamples - 1) / kRmSamples);
+  const unsigned blocks = (unsigned)vjp_rff_mma_blocks(N);
   k_vjp_rff_mma<D><<<blocks, kRmWarps * 32, smem, st>>>(tab, (int)(n_kt / kRmStageKT), fa.bias, x0, N, T, eta, k,
-                                                        ckpt, gT, g0);
-  return cudaGetLastError();
+                                                        ckpt, gT, g0, rows, fa.M);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || rows == nullptr) return e;
+  return sum_vjp_rows(rows, (int64_t)blocks, fa.M + 1, gw, gbias, st);
 }
 
 cudaError_t vjp_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
-                        const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st) {
+                        const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias, void* ws,
+                        cudaStream_t st) {
   switch (d) {
-    case 1: return launch_vjp_rff_mma<1>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
-    case 2: return launch_vjp_rff_mma<2>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
-    case 3: return launch_vjp_rff_mma<3>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
-    case 4: return launch_vjp_rff_mma<4>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
-    case 5: return launch_vjp_rff_mma<5>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
-    case 6: return launch_vjp_rff_mma<6>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
-    case 7: return launch_vjp_rff_mma<7>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
+    case 1: return launch_vjp_rff_mma<1>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
+    case 2: return launch_vjp_rff_mma<2>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
+    case 3: return launch_vjp_rff_mma<3>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
+    case 4: return launch_vjp_rff_mma<4>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
+    case 5: return launch_vjp_rff_mma<5>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
+    case 6: return launch_vjp_rff_mma<6>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
+    case 7: return launch_vjp_rff_mma<7>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
   }
   return cudaErrorInvalidValue;
 }

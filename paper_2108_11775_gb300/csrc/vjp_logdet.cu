@@ -263,6 +263,11 @@ __global__ void k_sum_rows(const float* __restrict__ rows, int64_t nrows, int64_
   }
 }
 
+cudaError_t sum_vjp_rows(const float* rows, int64_t nrows, int64_t width, float* gw, float* gbias, cudaStream_t st) {
+  k_sum_rows<<<(unsigned)((width + 255) / 256), 256, 0, st>>>(rows, nrows, width, gw, gbias);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ log-det
 // Cholesky of the SPD d x d matrix a (row-major, lower triangle used);
 // returns sum log diag(L)^2, or NaN after raising the flag if a pivot <= 0.
@@ -392,9 +397,7 @@ static cudaError_t launch_vjp(const FieldArgs& fa, const float* x0, int64_t N, i
   k_morph_vjp<KIND, D><<<(unsigned)blocks, kVjpThreads, 0, st>>>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || rows == nullptr) return e;
-  int64_t width = fa.M + 1;
-  k_sum_rows<<<(unsigned)((width + 255) / 256), 256, 0, st>>>(rows, blocks, width, gw, gbias);
-  return cudaGetLastError();
+  return sum_vjp_rows(rows, blocks, fa.M + 1, gw, gbias, st);
 }
 
 template <int KIND, int D>

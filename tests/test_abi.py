@@ -136,6 +136,14 @@ def test_vjp_validation():
                             16 * 776 * 4 - 1, None) == 3
     assert L.pdmp_morph_vjp(ctypes.byref(fr), A, 1000, 10, 0.01, 5, None, A, A, None, None, MIS,
                             16 * 776 * 4, None) == 1
+    # with the parameter gradient: the per-block rows (8 blocks of 128 samples x (M + 1) floats, rounded
+    # to 256 bytes), then the tensor-core table; the rows alone are the minimum
+    rows = 256 * ((8 * 17 * 4 + 255) // 256)
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fr), 1000, 10, 5, 1) == rows + 16 * 776 * 4
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fr), 1000, 32, 32, 1) == rows
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(fr), 1000, 10, 5, 2) == rows
+    assert L.pdmp_morph_vjp(ctypes.byref(fr), A, 1000, 10, 0.01, 5, None, A, A, A, None, A, rows - 1, None) == 3
+    assert L.pdmp_morph_vjp(ctypes.byref(fr), A, 1000, 10, 0.01, 5, None, A, A, None, A, MIS, rows, None) == 1
 
 
 @nogpu

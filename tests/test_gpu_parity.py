@@ -259,6 +259,35 @@ def test_vjp_tensor_core_path(d, N, T, k, use_ckpt):
     assert np.linalg.norm(g0 - direct) <= 1e-4 * np.linalg.norm(direct)
 
 
+@pytest.mark.parametrize("d,N,M,T,k,use_ckpt", [(7, 300, 300, 12, 4, True), (3, 129, 77, 6, 6, False),
+                                                (5, 1, 130, 4, 2, True)])
+def test_vjp_param_grad_tensor_core_path(d, N, M, T, k, use_ckpt):
+    """RFF, d <= 7, with the weight and bias gradient: the tensor-core VJP's
+    second pass per step (ragged sample blocks, M past one stage of 128
+    features and below it) against the oracle's d/dw, d/dbias and the direct
+    kernel's."""
+    f = wl.random_field(40 + d, wl.RFF, d, M, wscale=6.0, bias=0.1)
+    lo, hi = np.full(d, -np.pi), np.full(d, np.pi)
+    eta, _ = rff_eta_sampled(f, lo, hi, n=600)
+    x0 = wl.uniform_box(41 + d, 3, N, lo, hi)
+    gT = wl.f32(wl.rng(42 + d, wl.S_COTANGENT).standard_normal((N, d)))
+    fld = pdmp.DeviceField.from_host(f)
+    assert pdmp.morph_vjp_workspace(fld, N, T, k, 1) > pdmp.morph_vjp_workspace(fld, N, T, k, 2) > 0
+    ck = None
+    if use_ckpt:
+        ck = torch.empty(T // k, N, d, device="cuda")
+        pdmp.morph(fld, dev(x0), T, eta, ckpt=ck, k=k)
+    g0, gw, gb = pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck, want_param_grad=True)
+    g0, gw, gb = g0.cpu().numpy(), gw.cpu().numpy(), float(gb.cpu().numpy()[0])
+    r0, rw, rb = oracle.morph_vjp(f, x0, T, eta, gT, want_gw=True)
+    assert np.linalg.norm(g0 - r0) <= 1e-4 * np.linalg.norm(r0)
+    assert np.linalg.norm(gw - rw) <= 1e-4 * np.linalg.norm(rw)
+    assert abs(gb - rb) <= 1e-4 * max(abs(rb), 1e-3)
+    d0, dw, db = pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck, want_param_grad=True, fast=False)
+    assert np.linalg.norm(gw - dw.cpu().numpy()) <= 1e-4 * np.linalg.norm(rw)
+    assert np.array_equal(g0, pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck).cpu().numpy())
+
+
 def test_vjp_and_logdet_rff_7d_full_size_sampled():
     """The differentiation workload as the benchmark runs it (N = 2^20,
     M = 4096, T = 20, k = 5, tensor-core kernels): the VJP from the forward's
