@@ -59,6 +59,7 @@ typedef int32_t pdmp_status;
 #define PDMP_FLAG_NONPOSITIVE_PIVOT   1  /* log-det: I - eta Hess c not positive definite at some step */
 #define PDMP_FLAG_FIT_NONFINITE       2  /* fit: the loss became NaN or infinite */
 #define PDMP_FLAG_NOT_CONVERGED       4  /* inverse: a block stopped at maxit iterations */
+#define PDMP_FLAG_STAGE_TIMEOUT       8  /* a bounded wait for a shared-memory stage copy gave up (results invalid) */
 
 #define PDMP_KIND_RBF 0
 #define PDMP_KIND_RFF 1
@@ -98,6 +99,18 @@ pdmp_status pdmp_stream_status(void* stream, int32_t* detail);
  * the work has not finished by then (it keeps running; call again to keep
  * waiting); otherwise as pdmp_stream_status. */
 pdmp_status pdmp_stream_wait(void* stream, int32_t timeout_ms, int32_t* detail);
+
+/* Self-test of the kernels' bounded wait for a shared-memory stage copy (the
+ * bulk copies that stage the random Fourier tables).  One block initialises
+ * a stage barrier; with with_copy != 0 it copies the 16 floats at src
+ * (device, 16-byte aligned) into shared memory by the staging path and then
+ * to dst (device, 16 floats); one thread waits for the barrier at most
+ * limit_clocks (1 .. 2^31) SM clocks.  Without the copy nothing completes
+ * the barrier, the wait runs out and the kernel raises
+ * PDMP_FLAG_STAGE_TIMEOUT, which pdmp_stream_status then reports; nothing
+ * hangs and nothing is left in flight. */
+pdmp_status pdmp_selftest_stage_wait(const float* src, float* dst, int64_t limit_clocks, int32_t with_copy,
+                                     void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Sec. 3.2 (Eq. 1, "Drawing Samples"): morph a batch of base samples.      */

@@ -95,6 +95,7 @@ def lib():
             sigs = {
                 "pdmp_stream_status": [_P, ctypes.POINTER(_i32)],
                 "pdmp_stream_wait": [_P, _i32, ctypes.POINTER(_i32)],
+                "pdmp_selftest_stage_wait": [_P, _P, _i64, _i32, _P],
                 "pdmp_morph": [_FP, _P, _i64, _i32, _f32, _P, _P, _i32, _P, _sz, _P],
                 "pdmp_morph_trace": [_FP, _P, _i64, _i32, _f32, _P, _P, _P, _sz, _P],
                 "pdmp_morph_vjp": [_FP, _P, _i64, _i32, _f32, _i32, _P, _P, _P, _P, _P, _P, _sz, _P],
@@ -235,6 +236,18 @@ def stream_wait(timeout_ms: int):
     d = ctypes.c_int32(0)
     st = lib().pdmp_stream_wait(_stream(), int(timeout_ms), ctypes.byref(d))
     return int(st), int(d.value)
+
+def selftest_stage_wait(limit_clocks: int, src: torch.Tensor | None = None, dst: torch.Tensor | None = None):
+    """Runs the kernels' bounded stage-copy wait once: with src and dst (16
+    float32 each on the device) the copy completes and dst receives src;
+    without them the wait runs out after limit_clocks SM clocks and raises
+    PDMP_FLAG_STAGE_TIMEOUT.  Returns stream_status()."""
+    with_copy = src is not None
+    _check(lib().pdmp_selftest_stage_wait(_ptr(src, shape=(16,), name="src") if with_copy else None,
+                                          _ptr(dst, shape=(16,), name="dst") if with_copy else None,
+                                          int(limit_clocks), int(with_copy), _stream()), "pdmp_selftest_stage_wait")
+    return stream_status()
+
 
 def morph_workspace(field: DeviceField, N: int) -> int:
     f = field.struct()

@@ -110,6 +110,14 @@ pdmp_status pdmp_stream_status(void* stream, int32_t* detail) {
   return flag ? PDMP_ERR_DEVICE_FLAG : PDMP_OK;
 }
 
+pdmp_status pdmp_selftest_stage_wait(const float* src, float* dst, int64_t limit_clocks, int32_t with_copy,
+                                     void* stream) {
+  if (limit_clocks < 1 || limit_clocks > (int64_t(1) << 31)) return PDMP_ERR_INVALID_ARG;
+  if (with_copy && (!ok_ptr(src, true) || !ok_ptr(dst, true) || !aligned16(src))) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::stage_wait_selftest(with_copy ? src : nullptr, with_copy ? dst : nullptr,
+                                               (long long)limit_clocks, with_copy ? 1 : 0, as_stream(stream)));
+}
+
 pdmp_status pdmp_stream_wait(void* stream, int32_t timeout_ms, int32_t* detail) {
   if (timeout_ms < 0) return PDMP_ERR_INVALID_ARG;
   cudaStream_t st = as_stream(stream);

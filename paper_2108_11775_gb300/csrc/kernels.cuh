@@ -75,6 +75,8 @@ cudaError_t sum_vjp_rows(const float* rows, int64_t nrows, int64_t width, float*
 // rows: nullptr, or vjp_rff_mma_blocks(N) x (M + 1) floats for the weight and bias gradient (gw, gbias)
 constexpr int kVjpMmaMaxSegment = 16;
 int64_t vjp_rff_mma_blocks(int64_t N);
+// the staging wait's self-test (src, dst: 16 floats, 16-byte aligned; limit in clocks)
+cudaError_t stage_wait_selftest(const float* src, float* dst, long long limit, int with_copy, cudaStream_t st);
 cudaError_t vjp_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                         const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias, void* ws,
                         cudaStream_t st);

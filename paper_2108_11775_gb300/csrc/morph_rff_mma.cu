@@ -120,11 +120,83 @@ __global__ void k_rff_mma_table(FieldArgs fa, int64_t n_kt, float* __restrict__ 
   }
 }
 
+// Staging of the B-fragment table (TMA bulk copies).  A stage is one
+// contiguous run of the table, so thread 0 moves it with a single
+// cp.async.bulk (both ends 16-byte aligned, a multiple of 16 bytes long) that
+// completes on the block's mbarrier; thread 0 waits for it and the block
+// barrier that follows publishes the stage to every thread.  The wait is
+// bounded (kRmWaitClocks, about a second): past it the block raises
+// FLAG_STAGE_TIMEOUT and then issues and waits for no further copies, so the
+// kernel ends (with results the flag marks as invalid).
+constexpr long long kRmWaitClocks = 1ll << 31;
+
+struct RmStageState {
+  unsigned long long bar;   // the mbarrier
+  uint32_t phase;           // parity of the next completion
+  uint32_t failed;          // a wait gave up
+};
+
+// The block's staging state (static shared memory; only thread 0 touches it).
+__device__ __forceinline__ RmStageState* rm_stage_state() {
+  __shared__ RmStageState st;
+  return &st;
+}
+
+// Once per kernel, before the first stage load.
+__device__ __forceinline__ void rm_stage_init() {
+  if (threadIdx.x == 0) {
+    RmStageState* s = rm_stage_state();
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&s->bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s->phase = 0u;
+    s->failed = 0u;
+  }
+}
+
+// Thread 0 starts the copy of kFloats floats from src to dst; the caller has
+// passed a block barrier since dst was last read.
 template <int kFloats = kRmStageFloats>
 __device__ __forceinline__ void rm_stage_load(const float* __restrict__ src, float* dst) {
-  constexpr int kChunks = kFloats / 4;
-  for (int i = threadIdx.x; i < kChunks; i += kRmWarps * 32) cp_async16(dst + 4 * i, src + 4 * i);
-  cp_async_commit();
+  static_assert((kFloats * sizeof(float)) % 16 == 0, "bulk copies move multiples of 16 bytes");
+  if (threadIdx.x != 0) return;
+  RmStageState* s = rm_stage_state();
+  if (s->failed) return;
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s->bar);
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const uint32_t bytes = (uint32_t)(kFloats * sizeof(float));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(d), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Thread 0 waits for the copy in flight; the caller's block barrier follows.
+__device__ __forceinline__ void rm_stage_wait(long long limit = kRmWaitClocks) {
+  if (threadIdx.x != 0) return;
+  RmStageState* s = rm_stage_state();
+  if (s->failed) return;
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&s->bar);
+  const uint32_t parity = s->phase;
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) {
+      s->phase = parity ^ 1u;
+      return;
+    }
+    if (clock64() - t0 > limit) {
+      s->failed = 1u;
+      raise_flag(FLAG_STAGE_TIMEOUT);
+      return;
+    }
+  }
 }
 
 // tau (turns, a packed pair) -> 2 pi (tau - rint(tau)) in [-pi, pi]
@@ -181,7 +253,7 @@ __device__ __forceinline__ void rm_sweep(const float* __restrict__ tab, int nsta
   __syncthreads();   // every warp is done with the previous pass's stages
   rm_stage_load(tab, sm);
   for (int st = 0; st < nstage; ++st) {
-    cp_async_wait_all();
+    rm_stage_wait();
     __syncthreads();   // stage st is visible; stage st - 1's buffer is free
     if (st + 1 < nstage)
       rm_stage_load(tab + (size_t)(st + 1) * kRmStageFloats, sm + ((st + 1) & 1) * kRmStageFloats);
@@ -333,6 +405,7 @@ k_morph_rff_mma(const float* __restrict__ tab, int nstage, float bias, const flo
                 float* __restrict__ steps) {
   static_assert(D >= 1 && D <= 7, "dimensions and the phase share the 8 k slots");
   extern __shared__ __align__(16) float sm[];
+  rm_stage_init();
   const int warp = threadIdx.x >> 5;
   float* xs = sm + 2 * kRmStageFloats + warp * (kRmWarpSamples * 8);   // [32 samples][8]: x, 0 .., 1
   const int64_t s0 = (int64_t)blockIdx.x * kRmSamples + warp * kRmWarpSamples;
@@ -364,7 +437,7 @@ __device__ __forceinline__ void rm_gw_sweep(const float* __restrict__ tab, int n
   __syncthreads();   // every warp is done with the previous pass's stages
   rm_stage_load(tab, sm);
   for (int st = 0; st < nstage; ++st) {
-    cp_async_wait_all();
+    rm_stage_wait();
     __syncthreads();   // stage st is visible; stage st - 1's buffer and the partials are free
     if (st + 1 < nstage)
       rm_stage_load(tab + (size_t)(st + 1) * kRmStageFloats, sm + ((st + 1) & 1) * kRmStageFloats);
@@ -427,6 +500,7 @@ k_vjp_rff_mma(const float* __restrict__ tab, int nstage, float bias, const float
               float eta, int kseg, const float* __restrict__ ckpt, const float* __restrict__ gT, float* __restrict__ g0,
               float* __restrict__ rows, int64_t M) {
   extern __shared__ __align__(16) float sm[];
+  rm_stage_init();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   float* gs = sm + 2 * kRmStageFloats + warp * (kseg + 1) * (kRmWarpSamples * 8);   // [32][8], column 7 = 0
@@ -583,6 +657,7 @@ k_logdet_rff_mma(const float* __restrict__ tab, int nstage, float bias, const fl
                  int T, float eta, float* __restrict__ logdet, float* __restrict__ xT) {
   static_assert(D >= 1 && D <= 7, "dimensions and the phase share the 8 k slots");
   extern __shared__ __align__(16) float sm[];
+  rm_stage_init();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   float* xs = sm + 2 * kLdStageFloats + warp * kRmWarpSamples * (8 + kLdGather);
@@ -611,7 +686,7 @@ k_logdet_rff_mma(const float* __restrict__ tab, int nstage, float bias, const fl
     __syncthreads();   // every warp is done with the previous step's stages
     rm_stage_load<kLdStageFloats>(tab, sm);
     for (int st = 0; st < nstage; ++st) {
-      cp_async_wait_all();
+      rm_stage_wait();
       __syncthreads();
       if (st + 1 < nstage)
         rm_stage_load<kLdStageFloats>(tab + (size_t)(st + 1) * kLdStageFloats,
@@ -767,6 +842,7 @@ k_inverse_rff_mma(const float* __restrict__ tab, int nstage, float bias, const f
                   int T, float eta, float tol, int maxit, float* __restrict__ y_out, int32_t* __restrict__ iters,
                   unsigned long long* __restrict__ work, int64_t M) {
   extern __shared__ __align__(16) float sm[];
+  rm_stage_init();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   float* ys = sm + 2 * kRmStageFloats + warp * (2 * kRmWarpSamples * 8);   // iterate [32][8], column 7 = 1
@@ -856,6 +932,26 @@ cudaError_t inverse_rff_mma(int d, const FieldArgs& fa, const float* z, int64_t 
     case 7: return launch_inverse_rff_mma<7>(fa, z, N, T, eta, tol, maxit, y, iters, work, ws, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// Self-test of the staging wait (one block of 32 threads): the stage barrier
+// is initialised and, with `with_copy`, 16 floats go from src to shared
+// memory by the staging path and on to dst; thread 0 then waits with the
+// given limit.  Without the copy nothing completes the barrier's phase, so
+// the wait runs out and raises FLAG_STAGE_TIMEOUT (nothing is left in flight).
+__global__ void k_stage_wait_selftest(const float* __restrict__ src, float* __restrict__ dst, long long limit,
+                                      int with_copy) {
+  __shared__ __align__(16) float buf[16];
+  rm_stage_init();
+  if (with_copy) rm_stage_load<16>(src, buf);
+  rm_stage_wait(limit);
+  __syncthreads();
+  if (with_copy && threadIdx.x < 16) dst[threadIdx.x] = buf[threadIdx.x];
+}
+
+cudaError_t stage_wait_selftest(const float* src, float* dst, long long limit, int with_copy, cudaStream_t st) {
+  k_stage_wait_selftest<<<1, 32, 0, st>>>(src, dst, limit, with_copy);
+  return cudaGetLastError();
 }
 
 int64_t vjp_rff_mma_blocks(int64_t N) { return (N + kRmSamples - 1) / kRmSamples; }

@@ -273,6 +273,15 @@ def test_stream_wait_rejects_a_negative_timeout():
     assert pdmp.lib().pdmp_stream_wait(None, -1, None) == 1
 
 
+@nogpu
+def test_stage_wait_selftest_validation():
+    L = pdmp.lib()
+    assert L.pdmp_selftest_stage_wait(None, None, 0, 0, None) == 1                 # limit below 1 clock
+    assert L.pdmp_selftest_stage_wait(None, None, (1 << 31) + 1, 0, None) == 1     # above 2^31 clocks
+    assert L.pdmp_selftest_stage_wait(MIS, A, 1000, 1, None) == 1                  # src not 16-byte aligned
+    assert L.pdmp_selftest_stage_wait(A, None, 1000, 1, None) == 1                 # copy without dst
+
+
 def test_header_is_plain_c99():
     """The boundary header compiles as pedantic C99 (no C++ or CUDA types)."""
     import shutil

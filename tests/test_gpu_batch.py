@@ -112,6 +112,28 @@ def test_host_watchdog_times_out_then_completes():
     assert torch.isfinite(out).all()
 
 
+def test_stage_copy_wait_is_bounded():
+    """The bounded wait the random Fourier kernels use for their bulk stage
+    copies: with a copy it completes (the 16 floats arrive through shared
+    memory); with nothing to complete the barrier it gives up after the
+    limit, raises PDMP_FLAG_STAGE_TIMEOUT and the kernel ends (the context
+    stays usable: a morph afterwards is correct and leaves the flag clear)."""
+    src = torch.arange(16, dtype=torch.float32, device="cuda") * 0.5 - 3.0
+    dst = torch.zeros(16, dtype=torch.float32, device="cuda")
+    assert pdmp.selftest_stage_wait(1 << 20, src, dst) == (0, 0)
+    assert torch.equal(dst, src)
+    st, detail = pdmp.selftest_stage_wait(2_000_000)        # about a millisecond of spinning
+    assert st == 7 and detail == 8                          # PDMP_ERR_DEVICE_FLAG, PDMP_FLAG_STAGE_TIMEOUT
+    assert pdmp.stream_status() == (0, 0)                   # read and cleared
+    f = wl.random_field(71, wl.RFF, 7, 300, wscale=6.0, bias=0.1)
+    L, _ = oracle.lipschitz(f)
+    eta = float(np.float32(0.5 / L))
+    x0 = wl.uniform_box(71, 3, 256, np.full(7, -np.pi), np.full(7, np.pi))
+    out = pdmp.morph(pdmp.DeviceField.from_host(f, lipschitz=L), torch.from_numpy(x0).cuda(), 4, eta).cpu().numpy()
+    assert np.abs(out - oracle.morph(f, x0, 4, eta)).max() <= 1e-4
+    assert pdmp.stream_status() == (0, 0)
+
+
 def test_bound_calls_from_several_host_threads():
     """pdmp_lipschitz_bound and pdmp_cull_radius reduce into fixed device slots;
     called from four host threads at once they still return each field's own
