@@ -75,9 +75,10 @@ static void* range_trampoline(void* p) {
   return NULL;
 }
 
-/* Calls fn(ctx, lo, hi) on disjoint contiguous ranges that cover [0, n). */
-static void parallel_range(long n, range_fn fn, void* ctx) {
-  int nt = g_threads;
+/* Calls fn(ctx, lo, hi) on disjoint contiguous ranges that cover [0, n),
+ * on at most nt threads.  Items are independent, so the results do not depend
+ * on the split. */
+static void parallel_range_nt(long n, int nt, range_fn fn, void* ctx) {
   if (n <= 0) return;
   if (nt > n) nt = (int)n;
   if (nt <= 1) { fn(ctx, 0, n); return; }
@@ -99,6 +100,17 @@ static void parallel_range(long n, range_fn fn, void* ctx) {
   for (int t = 0; t < started; ++t)
     if (jobs[t].fn) pthread_join(th[t], NULL);
   free(th); free(jobs);
+}
+
+static void parallel_range(long n, range_fn fn, void* ctx) { parallel_range_nt(n, g_threads, fn, ctx); }
+
+/* As parallel_range, with no more threads than give each about a million
+ * feature evaluations (item_cost per item): the fit's per-iteration passes
+ * are small, and a thread per pass would cost more than the pass. */
+static void parallel_range_sized(long n, double item_cost, range_fn fn, void* ctx) {
+  double want = (double)n * item_cost / 1.0e6;
+  int nt = want < 1.0 ? 1 : (want < (double)g_threads ? (int)want : g_threads);
+  parallel_range_nt(n, nt, fn, ctx);
 }
 
 /* ------------------------------------------------------------------ */
@@ -634,7 +646,7 @@ static double fit_objective(const field_t* f, const double* X, const uint8_t* y,
                             const double* w, double b, double* logits, double* r, double* gw, double* gb) {
   fit_ctx c; memset(&c, 0, sizeof c);
   c.f = f; c.X = X; c.y = y; c.n = n; c.vin = w; c.vbias = b; c.out_n = logits;
-  parallel_range(n, fit_forward_range, &c);
+  parallel_range_sized(n, (double)f->M, fit_forward_range, &c);
   double loss = 0.0, rsum = 0.0;
   for (long i = 0; i < n; ++i) {
     loss += softplus(logits[i]) - (y[i] ? logits[i] : 0.0);
@@ -646,7 +658,7 @@ static double fit_objective(const field_t* f, const double* X, const uint8_t* y,
   loss = loss / n + 0.5 * l2 * reg;
   if (gw) {
     c.r = r; c.out_m = gw;
-    parallel_range(f->M, fit_backward_range, &c);
+    parallel_range_sized(f->M, (double)n, fit_backward_range, &c);
     for (long m = 0; m < f->M; ++m) gw[m] = gw[m] / n + l2 * w[m];
   }
   if (gb) *gb = rsum / n;
@@ -678,9 +690,9 @@ int orc_fit(int kind, int d, long M, const double* centres, const double* phase,
   for (int it = 0; it < power_iters; ++it) {
     fit_ctx c; memset(&c, 0, sizeof c);
     c.f = &f; c.X = X; c.y = y; c.n = n; c.vin = v; c.vbias = vb; c.out_n = tn;
-    parallel_range(n, fit_forward_range, &c);          /* tn = [Phi 1] v */
+    parallel_range_sized(n, (double)M, fit_forward_range, &c);   /* tn = [Phi 1] v */
     c.r = tn; c.out_m = av;
-    parallel_range(M, fit_backward_range, &c);         /* av = Phi^T tn */
+    parallel_range_sized(M, (double)n, fit_backward_range, &c);  /* av = Phi^T tn */
     double avb = 0.0;                                  /* bias row: 1^T tn */
     for (long i = 0; i < n; ++i) avb += tn[i];
     avb /= n;
