@@ -21,7 +21,7 @@
 //
 // A block of 4 warps owns 4 x 32 samples; each warp sweeps all features
 // for its own 32 (two 16-row tiles), the features staged for the whole
-// block in double-buffered shared-memory stages of 128 (cp.async).  A
+// block in double-buffered shared-memory stages of 128 (one bulk copy each).  A
 // sample's state stays in the warp's shared memory for all T steps.
 #include "fast_tile.cuh"
 #include "kernels.cuh"
