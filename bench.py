@@ -485,10 +485,15 @@ def extra_vjp_rbf2d(pdmp, torch, fld, x0, eta, n_sms, pk, k=5):
     pdmp.morph(fld, x0, T, eta, ckpt=ck, k=k)
     g0 = torch.empty_like(x0)
     t = _time(torch, lambda: pdmp.morph_vjp(fld, x0, T, eta, k, gT, ckpt=ck, g0=g0), reps=2)
+    # with d/dw and d/dbias: a third, transposed pass per step on the same tiles
+    ws_pg = torch.empty(pdmp.morph_vjp_workspace(fld, x0.shape[0], T, k, 1), dtype=torch.uint8, device="cuda")
+    t_pg = _time(torch, lambda: pdmp.morph_vjp(fld, x0, T, eta, k, gT, ckpt=ck, g0=g0, want_param_grad=True,
+                                               ws=ws_pg), reps=1)
     work = 2.0 * x0.shape[0] * T * M
     peak = alu_peak(n_sms, float(pk.get("sm_max_mhz", 2070.0)))
     return {"value": work / t, "unit": "feature-evals/s (2 passes)", "ms": 1e3 * t, "k": k,
-            "roofline_frac_vs_forward_count": work / t / peak}
+            "roofline_frac_vs_forward_count": work / t / peak,
+            "param_grad": {"ms": 1e3 * t_pg, "value": 1.5 * work / t_pg, "unit": "feature-evals/s (3 passes)"}}
 
 
 def extra_rff(pdmp, torch, n_sms, pk):

@@ -485,7 +485,9 @@ pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int
  * 2) returns (else PDMP_ERR_WORKSPACE_TOO_SMALL); with the
  * pdmp_morph_vjp_workspace(..., want_param_grad = 1) bytes and k <= 16, RFF
  * fields with d <= 7 also run on the tensor cores (the weight terms in a
- * second MMA pass per step; the query gives the rows alone otherwise).
+ * further MMA pass per step) and RBF fields in d = 2, 3 on the sorted tiles
+ * (a transposed pass per step: each lane sums its own features over the
+ * tile's samples); the query gives the rows alone otherwise.
  * Without them ws is optional: NULL, or at least
  * pdmp_morph_vjp_workspace(..., 0) bytes; with it (k <= 16), RFF fields with
  * d <= 7 run on the tensor cores (theta, grad s, omega . g and the

@@ -502,15 +502,16 @@ static bool vjp_mma_eligible(const pdmp_field* f, int32_t k) {
   return f->kind == PDMP_KIND_RFF && f->d <= 7 && k >= 1 && k <= pdmp::kVjpMmaMaxSegment;
 }
 
-// the sorted-tile VJP: RBF fields in d = 2, 3, segments of at most 16 steps, no parameter gradient
+// the sorted-tile VJP: RBF fields in d = 2, 3, segments of at most 16 steps
 static bool vjp_tiles_eligible(const pdmp_field* f, int64_t N, int32_t k) {
   return f->kind == PDMP_KIND_RBF && (f->d == 2 || f->d == 3) && k >= 1 && k <= pdmp::kVjpMmaMaxSegment &&
          N <= (int64_t)INT32_MAX;
 }
 
-// the per-block rows of the parameter gradient (either VJP kernel's blocks), rounded to 256 bytes
+// the per-block rows of the parameter gradient (any VJP kernel's blocks), rounded to 256 bytes
 static size_t vjp_rows_bytes(const pdmp_field* f, int64_t N) {
-  const int64_t blocks = std::max(pdmp::vjp_blocks(N), pdmp::vjp_rff_mma_blocks(N));
+  int64_t blocks = std::max(pdmp::vjp_blocks(N), pdmp::vjp_rff_mma_blocks(N));
+  if (f->kind == PDMP_KIND_RBF && (f->d == 2 || f->d == 3)) blocks = std::max(blocks, pdmp::vjp_rbf_fast_blocks(f->d, N));
   return (sizeof(float) * (size_t)blocks * (size_t)(f->M + 1) + 255) & ~size_t(255);
 }
 
@@ -519,6 +520,8 @@ size_t pdmp_morph_vjp_workspace(const pdmp_field* f, int64_t N, int32_t T, int32
   if (f == nullptr || N <= 0 || f->M < 1) return 0;
   if (want_param_grad) {
     if (want_param_grad == 1 && vjp_mma_eligible(f, k)) return vjp_rows_bytes(f, N) + pdmp::morph_rff_mma_workspace(f->M);
+    if (want_param_grad == 1 && vjp_tiles_eligible(f, N, k))
+      return vjp_rows_bytes(f, N) + pdmp::morph_rbf_fast_workspace(f->d, f->M, N);
     return vjp_rows_bytes(f, N);
   }
   if (vjp_mma_eligible(f, k)) return pdmp::morph_rff_mma_workspace(f->M);
@@ -567,7 +570,13 @@ pdmp_status pdmp_morph_vjp(const pdmp_field* f, const float* x0, int64_t N, int3
                                          (char*)ws + rows_bytes, st));
   }
   if (!want && ws != nullptr && N > 0 && vjp_tiles_eligible(f, N, k))
-    return cuda_status(pdmp::vjp_rbf_fast(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, ws, st));
+    return cuda_status(pdmp::vjp_rbf_fast(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, nullptr, nullptr,
+                                          nullptr, ws, st));
+  if (want && N > 0 && vjp_tiles_eligible(f, N, k) && ws_bytes >= pdmp_morph_vjp_workspace(f, N, T, k, 1)) {
+    const size_t rows_bytes = vjp_rows_bytes(f, N);
+    return cuda_status(pdmp::vjp_rbf_fast(f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0, (float*)ws, gw, gbias,
+                                          (char*)ws + rows_bytes, st));
+  }
   return cuda_status(pdmp::morph_vjp(f->kind, f->d, field_args(f), x0, N, T, eta, k, ckpt, gT, g0,
                                      want ? (float*)ws : nullptr, gw, gbias, st));
 }

@@ -80,9 +80,12 @@ cudaError_t stage_wait_selftest(const float* src, float* dst, long long limit, i
 cudaError_t vjp_rff_mma(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                         const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias, void* ws,
                         cudaStream_t st);
-// the sorted-tile VJP for RBF fields (d = 2, 3, k <= kVjpMmaMaxSegment; ws: morph_rbf_fast_workspace)
+// the sorted-tile VJP for RBF fields (d = 2, 3, k <= kVjpMmaMaxSegment; ws: morph_rbf_fast_workspace).
+// rows: nullptr, or vjp_rbf_fast_blocks(d, N) x (M + 1) floats for the weight and bias gradient (gw, gbias)
+int64_t vjp_rbf_fast_blocks(int d, int64_t N);
 cudaError_t vjp_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
-                         const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st);
+                         const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias,
+                         void* ws, cudaStream_t st);
 cudaError_t morph_vjp(int kind, int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
                       const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias,
                       cudaStream_t st);

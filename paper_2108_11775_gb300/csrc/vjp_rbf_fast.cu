@@ -11,6 +11,18 @@
 //   (Hess s) v = 4 gamma^2 f ((u . v)(u S - G) - (u K - Kc)) - 2 gamma f S v:
 // 4d + 3 packed FP32 operations and one ex2 per sample pair and feature.
 // Tiles too wide for the expanded form take the direct form.
+//
+// Weight gradient (optional).  Sample n adds to d/dw_m, with g = g_{t+1},
+//   cA phi_m + cB grad phi_m . g = phi_m (alpha + beta . c_m),
+//   cA = -eta sigma'' (grad s . g),  cB = -eta sigma',
+//   alpha = cA - 2 gamma cB (u . g),  beta = 2 gamma cB g
+// (grad phi_m = -2 gamma phi_m (u - c_m)).  After each Hessian-vector pass
+// warp 0 writes u, f alpha and f beta of the tile's samples to shared memory;
+// then the sweep is transposed: each lane owns features and sums over the
+// tile's sample pairs (phi_m / f = 2^(b_m . u - g' |c_m|^2), 2d + 1 packed
+// FP32 operations and one ex2 per pair, as in the forward), so no feature
+// needs a reduction across lanes or warps; the block's sums go to its own
+// row of the workspace, summed over blocks in a fixed order.
 #include "fast_tile.cuh"
 #include "kernels.cuh"
 #include "sort.cuh"
@@ -36,11 +48,129 @@ __host__ __device__ constexpr size_t vj_rbf_region0() {
   constexpr size_t red = (size_t)VjRbf<D>::kW * VjRbf<D>::kSums * VjRbf<D>::kTile * 4;
   return bufs > red ? bufs : red;
 }
-// region 0 (stages / reduction), the raw table entries, the segment's states
+// region 0 (stages / reduction), the raw table entries, the segment's states,
+// and with the weight gradient the tile's sample terms (u, f alpha, f beta)
 template <int D>
-__host__ __device__ constexpr size_t vj_rbf_smem(int kseg) {
+__host__ __device__ constexpr size_t vj_rbf_smem(int kseg, bool want_gw = false) {
   return vj_rbf_region0<D>() + (size_t)VjRbf<D>::kW * kWarpStage * FastRec<D>::kTab * sizeof(float4) +
-         (size_t)kseg * VjRbf<D>::kTile * D * sizeof(float);
+         (size_t)kseg * VjRbf<D>::kTile * D * sizeof(float) +
+         (want_gw ? (size_t)(2 * D + 2) * VjRbf<D>::kTile * sizeof(float) : 0);
+}
+
+constexpr int kGwFeatures = 4;   // features per lane in the weight-gradient sweep
+
+// Sample terms of the weight-gradient sweep, per pair of samples (2p, 2p + 1):
+// 2D + 2 packed pairs [u_0 .. u_{D-1}, f alpha, f beta_0 .. f beta_{D-1}, 0],
+// so that a pair's terms are D + 1 16-byte loads.
+template <int D>
+struct GwTerms {
+  static constexpr int kPairs = 2 * D + 2;
+  __device__ static void put(float* sm, int s, int slot, float v) {
+    sm[((s >> 1) * kPairs + slot) * 2 + (s & 1)] = v;
+  }
+};
+
+// The weight-gradient sweep of one warp over its slice [m_lo, m_hi) of the
+// features (sm: the tile's sample terms); adds each feature's sum to row[m].
+template <int D, int kTile>
+__device__ __forceinline__ void vj_gw_sweep(const float4* __restrict__ tab, int64_t m_lo, int64_t m_hi,
+                                            bool expanded, const float* o, float gl2e, const float* sm,
+                                            float* __restrict__ row, int lane) {
+  constexpr int TP = GwTerms<D>::kPairs;
+  constexpr int KT = FastRec<D>::kTab;
+  constexpr int F = kGwFeatures;
+  for (int64_t m0 = m_lo; m0 < m_hi; m0 += 32 * F) {
+    u64 cst[F], bm[F][D], A[F], Q[F][D];
+    float c[F][D];
+    bool ok[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      const int64_t m = m0 + f * 32 + lane;
+      ok[f] = m < m_hi;
+      float mu[D];
+      if (ok[f]) {
+        const float4 t0 = tab[KT * m];
+        mu[0] = t0.x;
+        mu[1] = t0.y;
+        if (D == 3) mu[2] = t0.z;
+      } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j) mu[j] = o[j];
+      }
+      float c2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        c[f][j] = mu[j] - o[j];   // direct form: o = 0
+        c2 = fmaf(c[f][j], c[f][j], c2);
+      }
+      if (expanded) {   // log2(phi / f) = -g' |c|^2 + 2 g' c . u
+        const float a0 = ok[f] ? -gl2e * c2 : -INFINITY;
+        cst[f] = pk(a0, a0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) bm[f][j] = pk(2.0f * gl2e * c[f][j], 2.0f * gl2e * c[f][j]);
+      } else {          // log2 phi = -g' |x - mu|^2
+        const float nm = ok[f] ? -gl2e : -INFINITY;
+        cst[f] = pk(nm, nm);
+#pragma unroll
+        for (int j = 0; j < D; ++j) bm[f][j] = pk(-mu[j], -mu[j]);
+      }
+      A[f] = 0ull;
+#pragma unroll
+      for (int j = 0; j < D; ++j) Q[f][j] = 0ull;
+    }
+#pragma unroll 2
+    for (int p = 0; p < kTile / 2; ++p) {
+      const ulonglong2* q = reinterpret_cast<const ulonglong2*>(sm + (size_t)p * TP * 2);
+      u64 t[TP];
+#pragma unroll
+      for (int h = 0; h < TP / 2; ++h) {
+        const ulonglong2 v = q[h];
+        t[2 * h] = v.x;
+        t[2 * h + 1] = v.y;
+      }
+      u64 up[D], bp[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        up[j] = t[j];
+        bp[j] = t[D + 1 + j];
+      }
+      const u64 al = t[D];
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        u64 e;
+        if (expanded) {
+          e = fma2(bm[f][0], up[0], cst[f]);
+#pragma unroll
+          for (int j = 1; j < D; ++j) e = fma2(bm[f][j], up[j], e);
+        } else {
+          u64 r2 = 0ull;
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            const u64 dx = add2(up[j], bm[f][j]);
+            r2 = fma2(dx, dx, r2);
+          }
+          e = mul2(r2, cst[f]);
+        }
+        e = ex2x2(e);
+        A[f] = fma2(e, al, A[f]);
+#pragma unroll
+        for (int j = 0; j < D; ++j) Q[f][j] = fma2(e, bp[j], Q[f][j]);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      if (!ok[f]) continue;
+      float lo, hi;
+      upk(A[f], lo, hi);
+      float v = lo + hi;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        upk(Q[f][j], lo, hi);
+        v = fmaf(c[f][j], lo + hi, v);
+      }
+      row[m0 + f * 32 + lane] += v;
+    }
+  }
 }
 
 //   expanded: [a][b_0 ..][sg][c~_0 ..][c_0 ..]     direct: [-mu_0 ..][lw][sg] (rest zero)
@@ -165,10 +295,10 @@ __device__ __forceinline__ void vj_stage_accumulate(const u64* rec, bool expande
   }
 }
 
-template <int D>
+template <int D, bool GW>
 __global__ void __launch_bounds__(VjRbf<D>::kW * 32, 3)
 k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float* __restrict__ gT,
-               float* __restrict__ g0) {
+               float* __restrict__ g0, float* __restrict__ rows) {
   constexpr int W = VjRbf<D>::kW, K = VjRbf<D>::kK, P = K / 2, RP = VjRbf<D>::kPairs;
   constexpr int NS = VjRbf<D>::kSums, kTile = VjRbf<D>::kTile, KT = FastRec<D>::kTab;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -184,6 +314,12 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
   const int64_t Mw = ((M + W - 1) / W + kWarpStage - 1) / kWarpStage * kWarpStage;
   const int64_t mbase = (int64_t)warp * Mw;
   const int nstage = (int)(Mw / kWarpStage);
+  // weight gradient: this block's row of rows[blocks][M + 1] and the sample terms after the segment
+  float* row = GW ? rows + (int64_t)blockIdx.x * (M + 1) : nullptr;
+  float* sm_gw = seg + (size_t)kseg * kTile * D;   // [kTile / 2][2D + 2] packed pairs
+  if (GW)
+    for (int64_t m = threadIdx.x; m <= M; m += blockDim.x) row[m] = 0.0f;
+  float gb = 0.0f;   // warp 0: the bias term of this lane's samples
 
   bool act[K];
   int64_t idx[K];
@@ -335,11 +471,39 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
         float gd = 0.0f;
 #pragma unroll
         for (int j = 0; j < D; ++j) gd = fmaf(gs[j], g[k][j], gd);
+        if (GW && warp == 0) {   // the sample's weight-gradient terms, with g_{t+1}
+          const int sidx = k * 32 + lane;
+          const float cA = act[k] ? -eta * d2 * gd : 0.0f, cB = act[k] ? -eta * d1 : 0.0f;
+          float u[D], ug = 0.0f, f = 1.0f, u2 = 0.0f;
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            // direct form: o = 0; an empty slot sits at the origin, where phi / f <= 1 stays finite
+            u[j] = act[k] ? x[k][j] - o[j] : 0.0f;
+            ug = fmaf(u[j], g[k][j], ug);
+            u2 = fmaf(u[j], u[j], u2);
+          }
+          if (expanded) f = ex2_approx(-gl2e * u2);
+          gb += cA;
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            GwTerms<D>::put(sm_gw, sidx, j, u[j]);
+            GwTerms<D>::put(sm_gw, sidx, D + 1 + j, f * (2.0f * gamma * cB * g[k][j]));
+          }
+          GwTerms<D>::put(sm_gw, sidx, D, f * fmaf(-2.0f * gamma * cB, ug, cA));
+          GwTerms<D>::put(sm_gw, sidx, 2 * D + 1, 0.0f);
+        }
 #pragma unroll
         for (int j = 0; j < D; ++j) g[k][j] = g[k][j] - eta * fmaf(d1, hv[j], d2 * gd * gs[j]);
       }
       __syncthreads();   // every warp has read the reduction buffer before the next pass rebuilds the stages
+      if (GW)            // (and the sample terms are visible)
+        vj_gw_sweep<D, kTile>(a.tab, mbase, mbase + Mw < M ? mbase + Mw : M, expanded, o, gl2e, sm_gw, row, lane);
     }
+  }
+  if (GW && warp == 0) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) gb += __shfl_xor_sync(0xffffffffu, gb, off);
+    if (lane == 0) row[M] = gb;
   }
   if (warp == 0)
 #pragma unroll
@@ -351,7 +515,8 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
 
 template <int D>
 static cudaError_t launch_vjp_rbf_fast(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
-                                       const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st) {
+                                       const float* ckpt, const float* gT, float* g0, float* rows, float* gw,
+                                       float* gbias, void* ws, cudaStream_t st) {
   float4* tab = reinterpret_cast<float4*>(ws);
   SortWs sw = sort_layout((char*)ws + rbf_fast_table_bytes(D, fa.M), D, N);
   k_rbf_table<D><<<(unsigned)((fa.M + 255) / 256), 256, 0, st>>>(fa.centres, fa.w, fa.M, tab);
@@ -369,18 +534,32 @@ static cudaError_t launch_vjp_rbf_fast(const FieldArgs& fa, const float* x0, int
   a.perm_base = 0;
   a.N = N;
   a.kck = 1;
-  const size_t smem = vj_rbf_smem<D>(k);
-  e = cudaFuncSetAttribute(k_vjp_rbf_fast<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = vj_rbf_smem<D>(k, rows != nullptr);
+  const unsigned blocks = (unsigned)vjp_rbf_fast_blocks(D, N);
+  if (rows == nullptr) {
+    e = cudaFuncSetAttribute(k_vjp_rbf_fast<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_vjp_rbf_fast<D, false><<<blocks, VjRbf<D>::kW * 32, smem, st>>>(a, k, ckpt, gT, g0, nullptr);
+    return cudaGetLastError();
+  }
+  e = cudaFuncSetAttribute(k_vjp_rbf_fast<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((N + VjRbf<D>::kTile - 1) / VjRbf<D>::kTile);
-  k_vjp_rbf_fast<D><<<blocks, VjRbf<D>::kW * 32, smem, st>>>(a, k, ckpt, gT, g0);
-  return cudaGetLastError();
+  k_vjp_rbf_fast<D, true><<<blocks, VjRbf<D>::kW * 32, smem, st>>>(a, k, ckpt, gT, g0, rows);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return sum_vjp_rows(rows, (int64_t)blocks, fa.M + 1, gw, gbias, st);
+}
+
+int64_t vjp_rbf_fast_blocks(int d, int64_t N) {
+  const int64_t tile = d == 2 ? VjRbf<2>::kTile : VjRbf<3>::kTile;
+  return (N + tile - 1) / tile;
 }
 
 cudaError_t vjp_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int k,
-                         const float* ckpt, const float* gT, float* g0, void* ws, cudaStream_t st) {
-  if (d == 2) return launch_vjp_rbf_fast<2>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
-  if (d == 3) return launch_vjp_rbf_fast<3>(fa, x0, N, T, eta, k, ckpt, gT, g0, ws, st);
+                         const float* ckpt, const float* gT, float* g0, float* rows, float* gw, float* gbias,
+                         void* ws, cudaStream_t st) {
+  if (d == 2) return launch_vjp_rbf_fast<2>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
+  if (d == 3) return launch_vjp_rbf_fast<3>(fa, x0, N, T, eta, k, ckpt, gT, g0, rows, gw, gbias, ws, st);
   return cudaErrorInvalidValue;
 }
 

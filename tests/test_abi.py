@@ -120,8 +120,12 @@ def test_vjp_validation():
     # k must divide T and be at most the longest segment
     assert L.pdmp_morph_vjp(ctypes.byref(f), A, 8, 10, 0.01, 3, None, A, A, None, None, None, 0, None) == 1
     assert L.pdmp_morph_vjp(ctypes.byref(f), A, 8, 64, 0.01, 64, None, A, A, None, None, None, 0, None) == 1
-    need = L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 1)
+    need = L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 2)   # the parameter gradient's rows
     assert need > 0
+    # RBF, d = 2, k <= 16: the full size adds the sorted tiles' workspace (the morph's) after the rows
+    assert (L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 1)
+            == need + L.pdmp_morph_workspace(ctypes.byref(f), 1000))
+    assert L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 32, 32, 1) == need   # segment too long: rows only
     # RBF, d = 2, no parameter gradient: the optional sorted-tile workspace (the morph's)
     assert L.pdmp_morph_vjp_workspace(ctypes.byref(f), 1000, 10, 5, 0) == L.pdmp_morph_workspace(ctypes.byref(f), 1000)
     assert L.pdmp_morph_vjp_workspace(ctypes.byref(fld(d=1)), 1000, 10, 5, 0) == 0

@@ -339,6 +339,39 @@ def test_vjp_sorted_tiles_rbf(d, N, T, k, use_ckpt):
     assert np.linalg.norm(g0 - direct) <= 1e-4 * np.linalg.norm(direct)
 
 
+@pytest.mark.parametrize("d,N,M,T,k,use_ckpt,hi", [(2, 4096, 500, 6, 3, True, 1.0), (3, 4096, 300, 4, 2, False, 1.0),
+                                                   (2, 300, 500, 6, 3, True, 4.0), (3, 257, 77, 4, 4, False, 4.0),
+                                                   (2, 1, 130, 4, 2, True, 4.0)])
+def test_vjp_param_grad_sorted_tiles_rbf(d, N, M, T, k, use_ckpt, hi):
+    """RBF, d = 2, 3, with the weight and bias gradient: the sorted-tile VJP's
+    transposed pass (4096 samples in the unit box: compact tiles, expanded
+    form; a few hundred in [0, 4]^d: wide tiles, direct form; ragged tiles,
+    M below and past a warp's slice) against the oracle's d/dw, d/dbias and
+    the direct kernel's; g0 is the same, bit for bit, as without the
+    parameter gradient."""
+    f = wl.random_field(90 + d, wl.RBF, d, M, lo=0.0, hi=hi, gamma=4.0, wscale=2.0, bias=0.2)
+    lo, hb = np.zeros(d), np.full(d, hi)
+    eta, _ = rbf_eta(f, lo - 0.5, hb + 0.5, cells=32 if d == 2 else 12)
+    x0 = wl.uniform_box(91 + d, 3, N, lo, hb)
+    gT = wl.f32(wl.rng(92 + d, wl.S_COTANGENT).standard_normal((N, d)))
+    fld = pdmp.DeviceField.from_host(f)
+    assert pdmp.morph_vjp_workspace(fld, N, T, k, 1) > pdmp.morph_vjp_workspace(fld, N, T, k, 2) > 0
+    ck = None
+    if use_ckpt:
+        ck = torch.empty(T // k, N, d, device="cuda")
+        pdmp.morph(fld, dev(x0), T, eta, ckpt=ck, k=k)
+    g0, gw, gb = pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck, want_param_grad=True)
+    g0, gw, gb = g0.cpu().numpy(), gw.cpu().numpy(), float(gb.cpu().numpy()[0])
+    assert pdmp.stream_status()[0] == 0
+    r0, rw, rb = oracle.morph_vjp(f, x0, T, eta, gT, want_gw=True)
+    assert np.linalg.norm(g0 - r0) <= 1e-4 * np.linalg.norm(r0)
+    assert np.linalg.norm(gw - rw) <= 1e-4 * np.linalg.norm(rw)
+    assert abs(gb - rb) <= 1e-4 * max(abs(rb), 1e-3)
+    _, dw, db = pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck, want_param_grad=True, fast=False)
+    assert np.linalg.norm(gw - dw.cpu().numpy()) <= 1e-4 * np.linalg.norm(rw)
+    assert np.array_equal(g0, pdmp.morph_vjp(fld, dev(x0), T, eta, k, dev(gT), ckpt=ck).cpu().numpy())
+
+
 def test_vjp_and_inverse_sorted_tiles_dense_3d():
     """3-D samples dense enough (2^17 in [0,5]^3, gamma = 8: tiles of 192 or
     320 samples span g' R^2 of about 3 to 4) that the sorted tiles take the
