@@ -4,6 +4,12 @@
 // features for the block's samples; a block stops when every sample's update
 // is at most tol (relative to 1 + |y|) or after maxit iterations.
 //
+// Warm start.  Undoing step t, the iteration starts from z + delta, delta =
+// x_{t+1} - x_{t+2} = eta grad c(x_{t+1}) the correction just found for step
+// t + 1 (0 for the first step undone).  Since z = x_{t+1}, that is exactly
+// the first iterate of a start from z, so each step saves one pass; the
+// stopping test and the fixed point are unchanged.
+//
 // Two kernels: a direct one (any field; 256 samples a block in input order,
 // every feature from x - mu or omega . x + b) and, for RBF fields in d = 2, 3
 // with a workspace, one on the forward's sorted tiles (Hilbert order, 320
@@ -37,11 +43,16 @@ k_morph_inverse(FieldArgs fa, const float* __restrict__ z0, int64_t N, int T, fl
   }
   int worst = 0;
   long long total = 0;
+  float dz[K][D];   // the correction of the step undone before (warm start)
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int j = 0; j < D; ++j) dz[k][j] = 0.0f;
   for (int t = T - 1; t >= 0; --t) {
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int j = 0; j < D; ++j) y[k][j] = z[k][j];
+      for (int j = 0; j < D; ++j) y[k][j] = z[k][j] + dz[k][j];
     int it = 0;
     bool converged = false;
     for (; it < maxit; ++it) {
@@ -90,7 +101,10 @@ k_morph_inverse(FieldArgs fa, const float* __restrict__ z0, int64_t N, int T, fl
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int j = 0; j < D; ++j) z[k][j] = y[k][j];
+      for (int j = 0; j < D; ++j) {
+        dz[k][j] = y[k][j] - z[k][j];
+        z[k][j] = y[k][j];
+      }
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -133,6 +147,7 @@ __device__ __forceinline__ void inverse_tile(const TileArgs& a, float tol, int m
   const int nstage = (int)(Mw / kWarpStage);
 
   float* zs = reinterpret_cast<float*>(smem + fast_smem_bytes<D, W, K>());   // kTile x D
+  float* ds = zs + kTile * D;   // the correction of the step undone before (warm start), kTile x D
   float y[K][D];
   bool act[K];
   tile_load<D, K>(a, p0, p_end, lane, y, act);
@@ -140,11 +155,18 @@ __device__ __forceinline__ void inverse_tile(const TileArgs& a, float tol, int m
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int j = 0; j < D; ++j) zs[(k * 32 + lane) * D + j] = y[k][j];
+      for (int j = 0; j < D; ++j) {
+        zs[(k * 32 + lane) * D + j] = y[k][j];
+        ds[(k * 32 + lane) * D + j] = 0.0f;
+      }
   int worst = 0;
   long long total = 0;
   for (int t = a.T - 1; t >= 0; --t) {
-    __syncthreads();   // the step's target z (written by warp 0) is visible; y = z in every warp
+    __syncthreads();   // the step's target z and the last correction (written by warp 0) are visible; y = z
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int j = 0; j < D; ++j) y[k][j] += ds[(k * 32 + lane) * D + j];
     int it = 0;
     bool moving = true;
     while (moving && it < maxit) {
@@ -235,7 +257,11 @@ __device__ __forceinline__ void inverse_tile(const TileArgs& a, float tol, int m
 #pragma unroll
       for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int j = 0; j < D; ++j) zs[(k * 32 + lane) * D + j] = y[k][j];
+        for (int j = 0; j < D; ++j) {
+          const int q = (k * 32 + lane) * D + j;
+          ds[q] = y[k][j] - zs[q];
+          zs[q] = y[k][j];
+        }
   }
   if (warp == 0) {
 #pragma unroll
@@ -284,7 +310,7 @@ static cudaError_t launch_inverse_fast(const FieldArgs& fa, const float* z, int6
   a.N = N;
   a.xT = y;
   constexpr size_t smem =
-      fast_smem_bytes<D, FastShape::kWarps, FastShape::kK>() + (size_t)FastShape::kTile * D * sizeof(float);
+      fast_smem_bytes<D, FastShape::kWarps, FastShape::kK>() + 2 * (size_t)FastShape::kTile * D * sizeof(float);
   e = cudaFuncSetAttribute(k_morph_inverse_fast<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((N + FastShape::kTile - 1) / FastShape::kTile);

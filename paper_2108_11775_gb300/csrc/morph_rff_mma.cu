@@ -845,14 +845,17 @@ k_inverse_rff_mma(const float* __restrict__ tab, int nstage, float bias, const f
   rm_stage_init();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  float* ys = sm + 2 * kRmStageFloats + warp * (2 * kRmWarpSamples * 8);   // iterate [32][8], column 7 = 1
+  float* ys = sm + 2 * kRmStageFloats + warp * (3 * kRmWarpSamples * 8);   // iterate [32][8], column 7 = 1
   float* zs = ys + kRmWarpSamples * 8;                                     // target  [32][8]
+  float* ds = zs + kRmWarpSamples * 8;                                     // last step's correction, column 7 = 0
   const int64_t s0 = (int64_t)blockIdx.x * kRmSamples + warp * kRmWarpSamples;
   rm_load_rows<D>(z0, s0, N, 1.0f, zs);
+  for (int i = lane; i < kRmWarpSamples * 8; i += 32) ds[i] = 0.0f;
   int worst = 0;
   long long total = 0;
   for (int step = T - 1; step >= 0; --step) {
-    for (int i = lane; i < kRmWarpSamples * 8; i += 32) ys[i] = zs[i];
+    // start from z + (the correction of the step undone before): the cold start's first iterate
+    for (int i = lane; i < kRmWarpSamples * 8; i += 32) ys[i] = zs[i] + ds[i];
     __syncwarp();
     int it = 0;
     bool moving = true;
@@ -890,7 +893,10 @@ k_inverse_rff_mma(const float* __restrict__ tab, int nstage, float bias, const f
     if (moving && threadIdx.x == 0) raise_flag(FLAG_NOT_CONVERGED);
     worst = it > worst ? it : worst;
     total += it;
-    for (int i = lane; i < kRmWarpSamples * 8; i += 32) zs[i] = ys[i];
+    for (int i = lane; i < kRmWarpSamples * 8; i += 32) {
+      ds[i] = ys[i] - zs[i];
+      zs[i] = ys[i];
+    }
     __syncwarp();
   }
   rm_store_rows<D>(zs, s0, N, y_out);
@@ -911,7 +917,7 @@ static cudaError_t launch_inverse_rff_mma(const FieldArgs& fa, const float* z, i
   float* tab = reinterpret_cast<float*>(ws);
   const int64_t n_kt = rm_tiles(fa.M);
   k_rff_mma_table<D, false><<<(unsigned)((n_kt * 32 + 255) / 256), 256, 0, st>>>(fa, n_kt, tab);
-  constexpr size_t smem = (2 * (size_t)kRmStageFloats + (size_t)kRmWarps * 2 * kRmWarpSamples * 8) * sizeof(float);
+  constexpr size_t smem = (2 * (size_t)kRmStageFloats + (size_t)kRmWarps * 3 * kRmWarpSamples * 8) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_inverse_rff_mma<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((N + kRmSamples - 1) / kRmSamples);
