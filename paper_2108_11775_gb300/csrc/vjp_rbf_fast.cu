@@ -5,12 +5,14 @@
 // checkpoint with the forward's tile step and kept in shared memory; each
 // step back is one pass over the features at x_t with v = g.  With the
 // tile's origin o, u = x - o, c_m = mu_m - o and e'_m = sg_m 2^(a_m + b_m . u)
-// (w_m phi_m = f e'_m, f = 2^(-g' |u|^2)), the pass sums
-//   S = sum e',  G = sum e' c,  K = sum e' (c . v),  Kc = sum e' (c . v) c,
+// (w_m phi_m = f e'_m, f = 2^(-g' |u|^2)), the pass sums the moments
+//   S = sum e',  G = sum e' c,  H = sum e' c c^T,
 // which give grad s = -2 gamma f (u S - G) and
-//   (Hess s) v = 4 gamma^2 f ((u . v)(u S - G) - (u K - Kc)) - 2 gamma f S v:
-// 4d + 3 packed FP32 operations and one ex2 per sample pair and feature.
-// Tiles too wide for the expanded form take the direct form.
+//   (Hess s) v = 4 gamma^2 f ((u . v)(u S - G) - (u (v . G) - H v)) - 2 gamma f S v
+// (sum e' (c . v) = v . G and sum e' (c . v) c = H v, so v enters only per
+// sample): 2d + 1 + d(d + 1)/2 packed FP32 operations and one ex2 per sample
+// pair and feature, 8 for d = 2.  Tiles too wide for the expanded form take
+// the direct form.
 //
 // Weight gradient (optional).  Sample n adds to d/dw_m, with g = g_{t+1},
 //   cA phi_m + cB grad phi_m . g = phi_m (alpha + beta . c_m),
@@ -31,12 +33,13 @@ namespace pdmp {
 
 template <int D>
 struct VjRbf {
-  static constexpr int kUsed = 3 * D + 2;              // u64 pairs: a, b, sg, c~ = sg c, c
+  static constexpr int kH = D * (D + 1) / 2;           // lower-triangle entries of H
+  static constexpr int kUsed = 2 * D + 2 + kH;         // u64 pairs: a, b, sg, c~ = sg c, h = sg c_a c_b
   // whole 16-byte chunks, an odd number of them: the lanes of a quarter warp
   // building consecutive records then write to distinct banks
   static constexpr int kChunks = (kUsed + 1) / 2 % 2 == 1 ? (kUsed + 1) / 2 : (kUsed + 1) / 2 + 1;
   static constexpr int kPairs = 2 * kChunks;
-  static constexpr int kSums = 2 * D + 2;              // S, G, K, Kc (direct: S, G, -, P)
+  static constexpr int kSums = 1 + D + kH;             // S, G, H (direct: S, G, P in the first D of H)
   static constexpr int kK = D == 2 ? 8 : 6;
   static constexpr int kW = 4;
   static constexpr int kTile = 32 * kK;
@@ -173,7 +176,7 @@ __device__ __forceinline__ void vj_gw_sweep(const float4* __restrict__ tab, int6
   }
 }
 
-//   expanded: [a][b_0 ..][sg][c~_0 ..][c_0 ..]     direct: [-mu_0 ..][lw][sg] (rest zero)
+//   expanded: [a][b_0 ..][sg][c~_0 ..][h_q ..] (h_q = sg c_a c_b)     direct: [-mu_0 ..][lw][sg] (rest zero)
 template <int D>
 __device__ __forceinline__ void vj_stage_build(int64_t M, int64_t m0, bool expanded, const float* o, float gl2e,
                                                const float4* raw, u64* rec, int lane) {
@@ -216,8 +219,14 @@ __device__ __forceinline__ void vj_stage_build(int64_t M, int64_t m0, bool expan
         const float b = 2.0f * gl2e * c[j], ct = sg * c[j];
         r[1 + j] = pk(b, b);
         r[D + 2 + j] = pk(ct, ct);
-        r[2 * D + 2 + j] = pk(c[j], c[j]);
       }
+#pragma unroll
+      for (int ia = 0; ia < D; ++ia)
+#pragma unroll
+        for (int ib = 0; ib <= ia; ++ib) {
+          const float h = sg * c[ia] * c[ib];
+          r[2 * D + 2 + ia * (ia + 1) / 2 + ib] = pk(h, h);
+        }
       r[D + 1] = pk(sg, sg);
     } else {
 #pragma unroll
@@ -231,11 +240,13 @@ __device__ __forceinline__ void vj_stage_build(int64_t M, int64_t m0, bool expan
   }
 }
 
-// sums of one pass at u (U) with v (V); Z = K (expanded) or unused (direct), Y = Kc or P
+// sums of one pass at u (U) with v (V): S, G and H (expanded), or S, G and
+// P = sum w phi ((x - mu) . v)(x - mu) in the first D entries of H (direct)
 template <int D, int P>
 __device__ __forceinline__ void vj_stage_accumulate(const u64* rec, bool expanded, float gl2e, const u64 (&U)[P][D],
-                                                    const u64 (&V)[P][D], u64 (&S)[P], u64 (&G)[P][D], u64 (&Z)[P],
-                                                    u64 (&Y)[P][D]) {
+                                                    const u64 (&V)[P][D], u64 (&S)[P], u64 (&G)[P][D],
+                                                    u64 (&H)[P][VjRbf<D>::kH]) {
+  constexpr int NH = VjRbf<D>::kH;
   constexpr int RP = VjRbf<D>::kPairs;
   if (expanded) {
 #pragma unroll 2
@@ -257,13 +268,8 @@ __device__ __forceinline__ void vj_stage_accumulate(const u64* rec, bool expande
         S[i] = fma2(r[D + 1], e, S[i]);
 #pragma unroll
         for (int j = 0; j < D; ++j) G[i][j] = fma2(e, r[D + 2 + j], G[i][j]);
-        u64 cv = mul2(r[D + 2], V[i][0]);                       // c~ . v
 #pragma unroll
-        for (int j = 1; j < D; ++j) cv = fma2(r[D + 2 + j], V[i][j], cv);
-        const u64 p = mul2(e, cv);                               // e' (c . v)
-        Z[i] = add2(Z[i], p);
-#pragma unroll
-        for (int j = 0; j < D; ++j) Y[i][j] = fma2(p, r[2 * D + 2 + j], Y[i][j]);
+        for (int q = 0; q < NH; ++q) H[i][q] = fma2(e, r[2 * D + 2 + q], H[i][q]);
       }
     }
   } else {
@@ -288,7 +294,7 @@ __device__ __forceinline__ void vj_stage_accumulate(const u64* rec, bool expande
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           G[i][j] = fma2(we, dx[j], G[i][j]);
-          Y[i][j] = fma2(wrv, dx[j], Y[i][j]);                 // sum w phi ((x - mu) . v)(x - mu)
+          H[i][j] = fma2(wrv, dx[j], H[i][j]);                 // sum w phi ((x - mu) . v)(x - mu)
         }
       }
     }
@@ -385,23 +391,26 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
         for (int j = 0; j < D; ++j) x[k][j] = seg[(i * kTile + k * 32 + lane) * D + j];
       float lo[D], hi[D], o[D];
       const bool expanded = tile_frame<D, K>(x, act, gl2e, lo, hi, o);
-      u64 U[P][D], V[P][D], S[P], G[P][D], Z[P], Y[P][D];
+      constexpr int NH = VjRbf<D>::kH;
+      u64 U[P][D], V[P][D], S[P], G[P][D], H[P][NH];
 #pragma unroll
       for (int q = 0; q < P; ++q) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           U[q][j] = pk(x[2 * q][j] - o[j], x[2 * q + 1][j] - o[j]);
           V[q][j] = pk(g[2 * q][j], g[2 * q + 1][j]);
-          G[q][j] = Y[q][j] = 0ull;
+          G[q][j] = 0ull;
         }
-        S[q] = Z[q] = 0ull;
+#pragma unroll
+        for (int h = 0; h < NH; ++h) H[q][h] = 0ull;
+        S[q] = 0ull;
       }
       stage_prefetch<D>(a.tab, M, mbase, wraw, lane);
       vj_stage_build<D>(M, mbase, expanded, o, gl2e, wraw, wbuf, lane);
       __syncwarp();
       for (int st = 0; st < nstage; ++st) {
         if (st + 1 < nstage) stage_prefetch<D>(a.tab, M, mbase + (int64_t)(st + 1) * kWarpStage, wraw, lane);
-        vj_stage_accumulate<D, P>(wbuf + (size_t)(st & 1) * kWarpStage * RP, expanded, gl2e, U, V, S, G, Z, Y);
+        vj_stage_accumulate<D, P>(wbuf + (size_t)(st & 1) * kWarpStage * RP, expanded, gl2e, U, V, S, G, H);
         if (st + 1 < nstage)
           vj_stage_build<D>(M, mbase + (int64_t)(st + 1) * kWarpStage, expanded, o, gl2e, wraw,
                             wbuf + (size_t)((st + 1) & 1) * kWarpStage * RP, lane);
@@ -415,17 +424,17 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
         upk(S[q], v0, v1);
         rw[(2 * q) * 32 + lane] = v0;
         rw[(2 * q + 1) * 32 + lane] = v1;
-        upk(Z[q], v0, v1);
-        rw[(1 + D) * kTile + (2 * q) * 32 + lane] = v0;
-        rw[(1 + D) * kTile + (2 * q + 1) * 32 + lane] = v1;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           upk(G[q][j], v0, v1);
           rw[(1 + j) * kTile + (2 * q) * 32 + lane] = v0;
           rw[(1 + j) * kTile + (2 * q + 1) * 32 + lane] = v1;
-          upk(Y[q][j], v0, v1);
-          rw[(2 + D + j) * kTile + (2 * q) * 32 + lane] = v0;
-          rw[(2 + D + j) * kTile + (2 * q + 1) * 32 + lane] = v1;
+        }
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {   // H (direct: P in the first D)
+          upk(H[q][h], v0, v1);
+          rw[(1 + D + h) * kTile + (2 * q) * 32 + lane] = v0;
+          rw[(1 + D + h) * kTile + (2 * q + 1) * 32 + lane] = v1;
         }
       }
       __syncthreads();
@@ -451,11 +460,20 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
           }
           const float f = ex2_approx(-gl2e * u2);
           shat = f * Ss;
+          float vG = 0.0f;   // K = sum e' (c . v) = v . G
+#pragma unroll
+          for (int j = 0; j < D; ++j) vG = fmaf(g[k][j], sum[1 + j], vG);
 #pragma unroll
           for (int j = 0; j < D; ++j) {
+            float Hv = 0.0f;   // Kc_j = (H v)_j, H from its lower triangle
+#pragma unroll
+            for (int i2 = 0; i2 < D; ++i2) {
+              const int q = j >= i2 ? j * (j + 1) / 2 + i2 : i2 * (i2 + 1) / 2 + j;
+              Hv = fmaf(sum[1 + D + q], g[k][i2], Hv);
+            }
             const float usg = fmaf(u[j], Ss, -sum[1 + j]);                  // u S - G
             gs[j] = -2.0f * gamma * (f * usg);
-            const float m = fmaf(uv, usg, -fmaf(u[j], sum[1 + D], -sum[2 + D + j]));   // (u.v)(uS-G) - (uK-Kc)
+            const float m = fmaf(uv, usg, -fmaf(u[j], vG, -Hv));            // (u.v)(uS-G) - (u K - Kc)
             hv[j] = 4.0f * gamma * gamma * f * m - 2.0f * gamma * f * Ss * g[k][j];
           }
         } else {
@@ -463,7 +481,7 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
 #pragma unroll
           for (int j = 0; j < D; ++j) {
             gs[j] = -2.0f * gamma * sum[1 + j];
-            hv[j] = 4.0f * gamma * gamma * sum[2 + D + j] - 2.0f * gamma * Ss * g[k][j];
+            hv[j] = 4.0f * gamma * gamma * sum[1 + D + j] - 2.0f * gamma * Ss * g[k][j];
           }
         }
         float d1, d2;
