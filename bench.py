@@ -643,7 +643,7 @@ def run_reference(args, world, rank, local):
     f = wk.field.with_weights(wl.proxy_fitted_weights(2, wk.field.centres, wk.boxes))
     L, _ = oracle.lipschitz(f, wk.lo - 0.5, wk.hi + 0.5, cells=64)
     eta = 0.5 / L
-    n = ncores * 4
+    n = ncores * 16            # samples per step: about 0.15 s of the oracle on 16 cores
     for i in range(args.warmup):
         oracle.morph(f, wk.x0[:ncores], T, eta)
     t0 = time.perf_counter()
