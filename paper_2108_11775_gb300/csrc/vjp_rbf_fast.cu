@@ -53,10 +53,12 @@ __host__ __device__ constexpr size_t vj_rbf_region0() {
 }
 // region 0 (stages / reduction), the raw table entries, the segment's states,
 // and with the weight gradient the tile's sample terms (u, f alpha, f beta)
+// (and with the cache, the forward's S and G at each of the segment's states)
 template <int D>
-__host__ __device__ constexpr size_t vj_rbf_smem(int kseg, bool want_gw = false) {
+__host__ __device__ constexpr size_t vj_rbf_smem(int kseg, bool want_gw = false, bool cache = false) {
   return vj_rbf_region0<D>() + (size_t)VjRbf<D>::kW * kWarpStage * FastRec<D>::kTab * sizeof(float4) +
          (size_t)kseg * VjRbf<D>::kTile * D * sizeof(float) +
+         (cache ? (size_t)kseg * (1 + D) * VjRbf<D>::kTile * sizeof(float) : 0) +
          (want_gw ? (size_t)(2 * D + 2) * VjRbf<D>::kTile * sizeof(float) : 0);
 }
 
@@ -242,7 +244,8 @@ __device__ __forceinline__ void vj_stage_build(int64_t M, int64_t m0, bool expan
 
 // sums of one pass at u (U) with v (V): S, G and H (expanded), or S, G and
 // P = sum w phi ((x - mu) . v)(x - mu) in the first D entries of H (direct)
-template <int D, int P>
+// (without SG, S and G are left alone: the caller has them from the recompute)
+template <int D, int P, bool SG>
 __device__ __forceinline__ void vj_stage_accumulate(const u64* rec, bool expanded, float gl2e, const u64 (&U)[P][D],
                                                     const u64 (&V)[P][D], u64 (&S)[P], u64 (&G)[P][D],
                                                     u64 (&H)[P][VjRbf<D>::kH]) {
@@ -265,9 +268,11 @@ __device__ __forceinline__ void vj_stage_accumulate(const u64* rec, bool expande
 #pragma unroll
         for (int j = 1; j < D; ++j) arg = fma2(r[1 + j], U[i][j], arg);
         const u64 e = ex2x2(arg);
-        S[i] = fma2(r[D + 1], e, S[i]);
+        if (SG) {
+          S[i] = fma2(r[D + 1], e, S[i]);
 #pragma unroll
-        for (int j = 0; j < D; ++j) G[i][j] = fma2(e, r[D + 2 + j], G[i][j]);
+          for (int j = 0; j < D; ++j) G[i][j] = fma2(e, r[D + 2 + j], G[i][j]);
+        }
 #pragma unroll
         for (int q = 0; q < NH; ++q) H[i][q] = fma2(e, r[2 * D + 2 + q], H[i][q]);
       }
@@ -289,11 +294,11 @@ __device__ __forceinline__ void vj_stage_accumulate(const u64* rec, bool expande
           rv = fma2(dx[j], V[i][j], rv);
         }
         const u64 we = mul2(r[D + 1], ex2x2(fma2(r2, ng, r[D])));   // w phi
-        S[i] = add2(S[i], we);
+        if (SG) S[i] = add2(S[i], we);
         const u64 wrv = mul2(we, rv);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-          G[i][j] = fma2(we, dx[j], G[i][j]);
+          if (SG) G[i][j] = fma2(we, dx[j], G[i][j]);
           H[i][j] = fma2(wrv, dx[j], H[i][j]);                 // sum w phi ((x - mu) . v)(x - mu)
         }
       }
@@ -304,7 +309,7 @@ __device__ __forceinline__ void vj_stage_accumulate(const u64* rec, bool expande
 template <int D, bool GW>
 __global__ void __launch_bounds__(VjRbf<D>::kW * 32, 3)
 k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float* __restrict__ gT,
-               float* __restrict__ g0, float* __restrict__ rows) {
+               float* __restrict__ g0, float* __restrict__ rows, int use_cache) {
   constexpr int W = VjRbf<D>::kW, K = VjRbf<D>::kK, P = K / 2, RP = VjRbf<D>::kPairs;
   constexpr int NS = VjRbf<D>::kSums, kTile = VjRbf<D>::kTile, KT = FastRec<D>::kTab;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -322,7 +327,9 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
   const int nstage = (int)(Mw / kWarpStage);
   // weight gradient: this block's row of rows[blocks][M + 1] and the sample terms after the segment
   float* row = GW ? rows + (int64_t)blockIdx.x * (M + 1) : nullptr;
-  float* sm_gw = seg + (size_t)kseg * kTile * D;   // [kTile / 2][2D + 2] packed pairs
+  // the forward's S, G (cross-warp totals) at the segment's states: [kseg][1 + D][kTile]
+  float* sgc = seg + (size_t)kseg * kTile * D;
+  float* sm_gw = sgc + (use_cache ? (size_t)kseg * (1 + D) * kTile : 0);   // [kTile / 2][2D + 2] packed pairs
   if (GW)
     for (int64_t m = threadIdx.x; m <= M; m += blockDim.x) row[m] = 0.0f;
   float gb = 0.0f;   // warp 0: the bias term of this lane's samples
@@ -382,8 +389,31 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
       }
       tile_finish_step<D, W, K, false>(a, 0, p0, act, x, o, expanded, S, G, reinterpret_cast<float4*>(red), warp,
                                        lane);
+      if (use_cache && i >= pre) {
+        // the step's totals, added in the finish's order, for the Hessian-vector pass at the same state
+        const float4* r4 = reinterpret_cast<const float4*>(red);
+        if (warp == 0)
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            float4 acc = r4[k * 32 + lane];
+#pragma unroll
+            for (int w = 1; w < W; ++w) {
+              const float4 b = r4[w * kTile + k * 32 + lane];
+              acc.x += b.x;
+              acc.y += b.y;
+              acc.z += b.z;
+              acc.w += b.w;
+            }
+            float* dst = sgc + (size_t)(i - pre) * (1 + D) * kTile + k * 32 + lane;
+            dst[0] = acc.x;
+            dst[kTile] = acc.y;
+            dst[2 * kTile] = acc.z;
+            if (D == 3) dst[3 * kTile] = acc.w;
+          }
+        __syncthreads();   // read before the next step's stages overwrite the buffer
+      }
     }
-    __syncthreads();   // the segment's states are visible to every warp
+    __syncthreads();   // the segment's states (and totals) are visible to every warp
     for (int i = kseg - 1; i >= 0; --i) {
 #pragma unroll
       for (int k = 0; k < K; ++k)
@@ -391,6 +421,7 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
         for (int j = 0; j < D; ++j) x[k][j] = seg[(i * kTile + k * 32 + lane) * D + j];
       float lo[D], hi[D], o[D];
       const bool expanded = tile_frame<D, K>(x, act, gl2e, lo, hi, o);
+      const bool have = use_cache && i < kseg - 1;   // S and G at this state from the recompute
       constexpr int NH = VjRbf<D>::kH;
       u64 U[P][D], V[P][D], S[P], G[P][D], H[P][NH];
 #pragma unroll
@@ -410,7 +441,10 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
       __syncwarp();
       for (int st = 0; st < nstage; ++st) {
         if (st + 1 < nstage) stage_prefetch<D>(a.tab, M, mbase + (int64_t)(st + 1) * kWarpStage, wraw, lane);
-        vj_stage_accumulate<D, P>(wbuf + (size_t)(st & 1) * kWarpStage * RP, expanded, gl2e, U, V, S, G, H);
+        if (have)
+          vj_stage_accumulate<D, P, false>(wbuf + (size_t)(st & 1) * kWarpStage * RP, expanded, gl2e, U, V, S, G, H);
+        else
+          vj_stage_accumulate<D, P, true>(wbuf + (size_t)(st & 1) * kWarpStage * RP, expanded, gl2e, U, V, S, G, H);
         if (st + 1 < nstage)
           vj_stage_build<D>(M, mbase + (int64_t)(st + 1) * kWarpStage, expanded, o, gl2e, wraw,
                             wbuf + (size_t)((st + 1) & 1) * kWarpStage * RP, lane);
@@ -421,14 +455,16 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         float v0, v1;
-        upk(S[q], v0, v1);
-        rw[(2 * q) * 32 + lane] = v0;
-        rw[(2 * q + 1) * 32 + lane] = v1;
+        if (!have) {
+          upk(S[q], v0, v1);
+          rw[(2 * q) * 32 + lane] = v0;
+          rw[(2 * q + 1) * 32 + lane] = v1;
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-          upk(G[q][j], v0, v1);
-          rw[(1 + j) * kTile + (2 * q) * 32 + lane] = v0;
-          rw[(1 + j) * kTile + (2 * q + 1) * 32 + lane] = v1;
+          for (int j = 0; j < D; ++j) {
+            upk(G[q][j], v0, v1);
+            rw[(1 + j) * kTile + (2 * q) * 32 + lane] = v0;
+            rw[(1 + j) * kTile + (2 * q + 1) * 32 + lane] = v1;
+          }
         }
 #pragma unroll
         for (int h = 0; h < NH; ++h) {   // H (direct: P in the first D)
@@ -443,6 +479,10 @@ k_vjp_rbf_fast(TileArgs a, int kseg, const float* __restrict__ ckpt, const float
         float sum[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
+          if (have && q <= D) {   // the recompute's totals at this state
+            sum[q] = sgc[((size_t)i * (1 + D) + q) * kTile + k * 32 + lane];
+            continue;
+          }
           float v = red[q * kTile + k * 32 + lane];
 #pragma unroll
           for (int w = 1; w < W; ++w) v += red[((size_t)w * NS + q) * kTile + k * 32 + lane];
@@ -552,17 +592,25 @@ static cudaError_t launch_vjp_rbf_fast(const FieldArgs& fa, const float* x0, int
   a.perm_base = 0;
   a.N = N;
   a.kck = 1;
-  const size_t smem = vj_rbf_smem<D>(k, rows != nullptr);
+  const bool want = rows != nullptr;
+  const void* fn = want ? reinterpret_cast<const void*>(k_vjp_rbf_fast<D, true>)
+                        : reinterpret_cast<const void*>(k_vjp_rbf_fast<D, false>);
+  // cache the recompute's S and G when the extra shared memory keeps as many blocks on an SM
+  const size_t smem0 = vj_rbf_smem<D>(k, want, false), smem1 = vj_rbf_smem<D>(k, want, true);
+  int b0 = 0, b1 = 0;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, fn, VjRbf<D>::kW * 32, smem0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, fn, VjRbf<D>::kW * 32, smem1);
+  if (e != cudaSuccess) return e;
+  const int use_cache = b1 >= b0 && b1 > 0 ? 1 : 0;
+  const size_t smem = use_cache ? smem1 : smem0;
   const unsigned blocks = (unsigned)vjp_rbf_fast_blocks(D, N);
-  if (rows == nullptr) {
-    e = cudaFuncSetAttribute(k_vjp_rbf_fast<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_vjp_rbf_fast<D, false><<<blocks, VjRbf<D>::kW * 32, smem, st>>>(a, k, ckpt, gT, g0, nullptr);
+  if (!want) {
+    k_vjp_rbf_fast<D, false><<<blocks, VjRbf<D>::kW * 32, smem, st>>>(a, k, ckpt, gT, g0, nullptr, use_cache);
     return cudaGetLastError();
   }
-  e = cudaFuncSetAttribute(k_vjp_rbf_fast<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_vjp_rbf_fast<D, true><<<blocks, VjRbf<D>::kW * 32, smem, st>>>(a, k, ckpt, gT, g0, rows);
+  k_vjp_rbf_fast<D, true><<<blocks, VjRbf<D>::kW * 32, smem, st>>>(a, k, ckpt, gT, g0, rows, use_cache);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return sum_vjp_rows(rows, (int64_t)blocks, fa.M + 1, gw, gbias, st);
