@@ -53,7 +53,7 @@ typedef int32_t pdmp_status;
 #define PDMP_ERR_NOT_CONVERGED        5
 #define PDMP_ERR_TIMEOUT              6
 #define PDMP_ERR_DEVICE_FLAG          7  /* a kernel recorded a numerical failure */
-#define PDMP_ERR_UNSUPPORTED          8  /* valid request this build does not handle */
+#define PDMP_ERR_UNSUPPORTED          8  /* valid request this library version does not handle */
 
 /* Bits of the device flag (the detail of PDMP_ERR_DEVICE_FLAG). */
 #define PDMP_FLAG_NONPOSITIVE_PIVOT   1  /* log-det: I - eta Hess c not positive definite at some step */

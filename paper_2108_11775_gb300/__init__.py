@@ -959,7 +959,7 @@ class Surrogate:
             head = json.loads(f.readline().decode())
             raw = np.frombuffer(f.read(), dtype="<f4")
         if head.get("format") != "pdmp-surrogate-1" or head["nw"] != MLP_NW or head["nb"] != MLP_NB:
-            raise ValueError(f"{path}: not a surrogate of this build ({head.get('format')})")
+            raise ValueError(f"{path}: not a surrogate file of this library version ({head.get('format')})")
         nw, nb = MLP_NW, MLP_NB
         if raw.size != nw + nb + 2 * nw + 2 * nb:
             raise ValueError(f"{path}: {raw.size} floats, expected {3 * (nw + nb)}")

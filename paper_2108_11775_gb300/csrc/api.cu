@@ -83,7 +83,7 @@ const char* pdmp_status_string(pdmp_status s) {
     case PDMP_ERR_NOT_CONVERGED: return "not converged";
     case PDMP_ERR_TIMEOUT: return "timed out";
     case PDMP_ERR_DEVICE_FLAG: return "a kernel recorded a numerical failure";
-    case PDMP_ERR_UNSUPPORTED: return "unsupported by this build";
+    case PDMP_ERR_UNSUPPORTED: return "unsupported by this library version";
     default: return "unknown status";
   }
 }
