@@ -4,8 +4,9 @@ grad c and Hess c through sigma', sigma''), so that an error in a kernel's
 algebra fails here as well as in the GPU parity tests:
 
 * RBF sorted tiles: the expanded exponent about a tile origin o (log2 of
-  |w| phi = a + b . u - g'|u|^2) and the Hessian-vector product from the
-  moments S, G, H alone (sum e'(c . v) = v . G, sum e'(c . v) c = H v);
+  |w| phi = a + b . u - g'|u|^2), the Hessian-vector product from the
+  moments S, G, H alone (sum e'(c . v) = v . G, sum e'(c . v) c = H v), and
+  the log-det's full Hessian from the same moments;
 * RFF tensor-core VJP: (Hess s) v = 2 pi sum_m cos(theta_m) (omega_m . v / 2 pi)(-w_m omega_m);
 * the sorted tiles' weight-gradient pass: cA phi_m + cB grad phi_m . g =
   phi_m (alpha + beta . c_m) with alpha = cA - 2 gamma cB (u . g) and
@@ -52,6 +53,10 @@ def test_rbf_expanded_moments_give_s_grad_and_hessian_vector(d):
         assert abs(s_k - s) <= 1e-12 * max(1.0, abs(s))
         np.testing.assert_allclose(grad_k, gs, rtol=0, atol=1e-11 * max(1.0, np.abs(gs).max()))
         np.testing.assert_allclose(hv_k, hs @ v, rtol=0, atol=1e-10 * max(1.0, np.abs(hs @ v).max()))
+        # the log-det's Hessian from the same moments
+        hs_k = 4 * gamma ** 2 * f_u * (S * np.outer(u, u) - np.outer(G, u) - np.outer(u, G) + H) \
+            - 2.0 * gamma * f_u * S * np.eye(d)
+        np.testing.assert_allclose(hs_k, hs, rtol=0, atol=1e-10 * max(1.0, np.abs(hs).max()))
 
 
 @pytest.mark.parametrize("d", [3, 7])
