@@ -59,6 +59,26 @@ def test_rbf_expanded_moments_give_s_grad_and_hessian_vector(d):
         np.testing.assert_allclose(hs_k, hs, rtol=0, atol=1e-10 * max(1.0, np.abs(hs).max()))
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_rbf_direct_form_sums(d):
+    """Tiles too wide for the expanded form sum, about the origin 0,
+    S = sum w phi, G = sum w phi (x - mu), P = sum w phi ((x - mu) . v)(x - mu):
+    grad s = -2 gamma G and (Hess s) v = 4 gamma^2 P - 2 gamma S v."""
+    f = wl.random_field(31 + d, wl.RBF, d, 300, lo=0.0, hi=3.0, gamma=4.0, wscale=1.5, bias=-0.2)
+    rng = np.random.default_rng(50 + d)
+    mu, w, gamma = f.centres.astype(np.float64), f.w.astype(np.float64), float(f.gamma)
+    for _ in range(5):
+        x, v = rng.uniform(0.0, 3.0, d), rng.standard_normal(d)
+        dx = x - mu
+        we = w * np.exp2(-gamma * LOG2E * (dx * dx).sum(1))
+        S, G, P = we.sum(), we @ dx, (we * (dx @ v)) @ dx
+        s, gs, hs = _plain_s(f, x)
+        assert abs(S + f.bias - s) <= 1e-12 * max(1.0, abs(s))
+        np.testing.assert_allclose(-2.0 * gamma * G, gs, rtol=0, atol=1e-11 * max(1.0, np.abs(gs).max()))
+        np.testing.assert_allclose(4 * gamma ** 2 * P - 2.0 * gamma * S * v, hs @ v, rtol=0,
+                                   atol=1e-10 * max(1.0, np.abs(hs @ v).max()))
+
+
 @pytest.mark.parametrize("d", [3, 7])
 def test_rff_hessian_vector_contraction(d):
     f = wl.random_field(21 + d, wl.RFF, d, 256, wscale=6.0, bias=0.1)
