@@ -325,7 +325,8 @@ static cudaError_t launch_cull(const FieldArgs& fa, const float* x0, int64_t N, 
   a.ckpt = ckpt;
   a.kck = k;
   constexpr size_t smem = cull_smem_bytes<D>();
-  cudaFuncSetAttribute(k_morph_rbf_cull<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k_morph_rbf_cull<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((N + Shape<4, 8>::kTile - 1) / Shape<4, 8>::kTile);
   k_morph_rbf_cull<D><<<blocks, Shape<4, 8>::kThreads, smem, st>>>(a, c.grid, c.offs, work);
   return cudaGetLastError();

@@ -232,11 +232,15 @@ static cudaError_t launch_rff(const FieldArgs& fa, const float* x0, int64_t N, i
   constexpr size_t smem = rff_smem_bytes<D>();
   const unsigned blocks = (unsigned)((N + kRffTile - 1) / kRffTile);
   if (traj != nullptr) {
-    cudaFuncSetAttribute(k_morph_rff_fast<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_morph_rff_fast<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_morph_rff_fast<D, true><<<blocks, kRffWarps * 32, smem, st>>>(tab, fa.M, fa.bias, x0, N, T, eta, xT, ckpt, k,
                                                                     traj, steps);
   } else {
-    cudaFuncSetAttribute(k_morph_rff_fast<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_morph_rff_fast<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_morph_rff_fast<D, false><<<blocks, kRffWarps * 32, smem, st>>>(tab, fa.M, fa.bias, x0, N, T, eta, xT, ckpt,
                                                                      k, nullptr, nullptr);
   }
