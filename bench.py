@@ -2,10 +2,12 @@
 
 One step = one pdmp_morph over the 2-D fitted-occupancy workload:
 N = 2^20 base samples uniform in [0,10]^2, M = 16,384 RBF centres (gamma = 8)
-with weights fitted on the GPU by pdmp_fit_occupancy to 200k points labelled
-by 64 random boxes, T = 50 Euler steps, eta = 0.5 / L with L the certified
-bound from pdmp_lipschitz_bound.  Work per step: N * T * M feature
-evaluations.
+with the occupancy weights fitted to 200k points labelled by 64 random boxes
+(the stored fit of tests/golden/fit_rbf2d_fitted.txt, made by the oracle
+alone, which the parity tests check at this size; pdmp_fit_occupancy fits the
+same data on the GPU and its loss is reported beside), T = 50 Euler steps,
+eta = 0.5 / L with L the stored certified bound (pdmp_lipschitz_bound's is
+reported beside).  Work per step: N * T * M feature evaluations.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -174,16 +176,28 @@ def whole_job_rate(world: int, work_per_rank_step: float, steps: int, max_second
 
 # ---------------------------------------------------------------------------
 def build_workload(pdmp, torch, seed=2):
-    wk = wl.config2(seed=seed, N=N, M=M)
+    """The 2-D fitted workload with the stored fit (the oracle's weights and
+    bias for this field, and its certified bound L), the field the parity
+    tests check at this size.  The library's own fit of the same data runs
+    too, and its loss, step size and certified bound on the stored field are
+    reported beside the stored ones."""
+    wk, params = wl.config2_fitted(seed=seed, N=N)
     fld = pdmp.DeviceField.from_host(wk.field)
     X = torch.from_numpy(wk.fit_X).cuda()
     y = torch.from_numpy(wk.fit_y).cuda()
-    w, b, loss, _ = pdmp.fit_occupancy(fld, X, y, 1e-4, 20, 200)
-    fitted = fld.with_weights(w, bias=b)
-    L, _ = pdmp.lipschitz_bound(fitted, wk.lo - 0.5, wk.hi + 0.5, cells=128)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, loss, alpha = pdmp.fit_occupancy(fld, X, y, params["l2"], params["power_iters"], params["iters"])
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    L_gpu, _ = pdmp.lipschitz_bound(fld, wk.lo - 0.5, wk.hi + 0.5, cells=128)
+    L = params["L"]
     eta = float(np.float32(0.5 / L))
-    fitted.lipschitz = L
-    return wk, fitted, eta, {"fit_loss": loss, "L": L, "eta": eta}
+    fld.lipschitz = L
+    fit = {"weights": "stored oracle fit (tests/golden/fit_rbf2d_fitted.txt)", "oracle_loss": params["loss_f64"],
+           "gpu_fit_loss": loss, "gpu_fit_rel_diff": abs(loss - params["loss_f64"]) / params["loss_f64"],
+           "gpu_fit_alpha": alpha, "gpu_fit_s": fit_s, "L_stored": L, "L_gpu": L_gpu}
+    return wk, fld, eta, {"fit_loss": params["loss_f64"], "L": L, "eta": eta, "fit": fit}
 
 
 def run_ours(args, world, rank, local):
@@ -265,7 +279,8 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "M": M, "T": T, "d": D, "gamma": 8.0, "eta": eta,
-                   "L": info["L"], "fit_loss": info["fit_loss"], "l2_flush": "256 MiB write between timed launches",
+                   "L": info["L"], "fit_loss": info["fit_loss"], "fit": info["fit"],
+                   "l2_flush": "256 MiB write between timed launches",
                    "parallelism": f"replicas{world}"},
         "e2e": {"value": whole_job_rate(world, work, args.steps, e2e_total), "unit": "feature-evals/s",
                 "h2d_bytes_per_step": int(x_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4)},
@@ -604,7 +619,7 @@ def cpu_baseline(wk, fld, eta, target_s=12.0):
     import oracle
     ncores = os.cpu_count() or 1
     oracle.set_threads(ncores)
-    f = wk.field.with_weights(fld.w.cpu().numpy(), bias=fld.bias)
+    f = wk.field                       # the stored fit, the field the GPU step morphs
     probe = 2 * ncores
     t0 = time.perf_counter()
     oracle.morph(f, wk.x0[:probe], T, eta)
@@ -639,10 +654,9 @@ def run_reference(args, world, rank, local):
     import oracle
     ncores = os.cpu_count() or 1
     oracle.set_threads(ncores)
-    wk = wl.config2(N=max(4096, ncores * 64), M=M)
-    f = wk.field.with_weights(wl.proxy_fitted_weights(2, wk.field.centres, wk.boxes))
-    L, _ = oracle.lipschitz(f, wk.lo - 0.5, wk.hi + 0.5, cells=64)
-    eta = 0.5 / L
+    wk, params = wl.config2_fitted(N=max(4096, ncores * 64))
+    f = wk.field
+    eta = float(np.float32(0.5 / params["L"]))
     n = ncores * 16            # samples per step: about 0.15 s of the oracle on 16 cores
     for i in range(args.warmup):
         oracle.morph(f, wk.x0[:ncores], T, eta)

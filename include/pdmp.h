@@ -156,9 +156,11 @@ pdmp_status pdmp_morph_trace(const pdmp_field* f, const float* x0, int64_t N, in
  * RBF fields with d = 2 or 3 (others give PDMP_ERR_UNSUPPORTED), N <= 2^20
  * and M <= 16384 (larger requests give PDMP_ERR_WORKSPACE_TOO_SMALL before
  * anything is launched).  No checkpoints.  The first call on a device looks up
- * the scratch's device address; make it before any stream capture.  All calls
- * share the scratch: calls that overlap on the GPU race and must be
- * serialised by the caller.  Calls no cudaMalloc / cudaFree. */
+ * the scratch's device address; make it before any stream capture.  That
+ * address is cached per device and does not survive cudaDeviceReset (or any
+ * other teardown of the device's primary context).  All calls share the
+ * scratch: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Calls no cudaMalloc / cudaFree. */
 pdmp_status pdmp_morph_noalloc(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float* xT,
                                void* stream);
 
@@ -245,7 +247,8 @@ pdmp_status pdmp_graph_destroy(void* graph_exec);
  *   Wt_bf16  BF16 transposes of W2 and W3 (2 x 128 x 128), for the backward;
  *   adam     Adam moments: m_W, v_W (PDMP_MLP_NW each), m_b, v_b (PDMP_MLP_NB
  *            each); zero before the first step.
- * Matrix products run on the tensor cores in BF16 with FP32 accumulation. */
+ * Matrix products run on the tensor cores in BF16 with FP32 accumulation,
+ * the weight gradient too ([dW | db] = dZ^T [a | 1] per layer). */
 #define PDMP_MLP_NW 38144
 #define PDMP_MLP_NB 387
 typedef struct {
@@ -266,6 +269,24 @@ pdmp_status pdmp_mlp_refresh(const pdmp_mlp* net, void* stream);
 
 /* xT_hat (N x 3) = x0 + out_scale * f(u(x0)). */
 pdmp_status pdmp_mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* xT_hat, void* stream);
+
+/* pdmp_mlp_forward in the FP32-activation mode (diagnostic): the same kernel
+ * and fragment layouts, with every activation fed to the tensor cores as the
+ * sum of three BF16 pieces (at least 24 bits of the FP32 value), so that the
+ * products are those of FP32 activations with the BF16 weights. */
+pdmp_status pdmp_mlp_forward_fp32act(const pdmp_mlp* net, const float* x0, int64_t N, float* xT_hat, void* stream);
+
+/* The loss and gradient of one training batch without an update (diagnostic):
+ * gW (PDMP_MLP_NW floats, device, the layout of W) and gb (PDMP_MLP_NB, the
+ * layout of b) receive d loss / d(W, b) with respect to the BF16 weights the
+ * kernels use; loss (device, may be NULL) the batch loss.  fp32_act = 0: the
+ * training step's own arithmetic (BF16 activations and backward signals, FP32
+ * accumulation); fp32_act = 1: the same kernels with activations and backward
+ * signals carried as three BF16 pieces each (FP32-activation mode), so that
+ * the result matches an FP64 evaluation of the same BF16 weights to FP32
+ * rounding.  ws: pdmp_mlp_train_workspace(B) bytes. */
+pdmp_status pdmp_mlp_gradient(const pdmp_mlp* net, const float* x0, const float* xT, int32_t B, int32_t fp32_act,
+                              float* loss, float* gW, float* gb, void* ws, size_t ws_bytes, void* stream);
 
 /* One Adam step (step = 1, 2, ...) on the mean squared error between f(u(x0))
  * and (xT - x0) / out_scale over a batch of B pairs (x0, xT: B x 3 device).
@@ -289,6 +310,18 @@ size_t pdmp_surrogate_workspace(const pdmp_field* f, int64_t N);
 pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const float* x0, int64_t N, int32_t T,
                                  float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, size_t ws_bytes,
                                  void* stream);
+
+/* The residual threshold tau_r of pdmp_surrogate_infer from training
+ * samples: the q-quantile (nearest rank: the ceil(q N)-th smallest, 0 < q <= 1)
+ * of the length |FP32 increment| of the plain morph's last step, T steps of
+ * eta from each of the N samples x0 (N x d device; RBF fields, d = 2 or 3).
+ * *tau_r (host) receives it (this call synchronises `stream` once); xT (device,
+ * N x d, may be NULL) receives x_T, the training targets.  The selection is
+ * exact (a radix select on the length's bits; NaN lengths rank last).
+ * ws: pdmp_residual_threshold_workspace(f, N) bytes. */
+size_t pdmp_residual_threshold_workspace(const pdmp_field* f, int64_t N);
+pdmp_status pdmp_residual_threshold(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float q,
+                                    float* tau_r, float* xT, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* The diffeomorphic sampler (Sec. 3.3).                                    */

@@ -863,9 +863,12 @@ def _mlp_sigs():
     for name, argt in {
         "pdmp_mlp_refresh": [MP, _P],
         "pdmp_mlp_forward": [MP, _P, _i64, _P, _P],
+        "pdmp_mlp_forward_fp32act": [MP, _P, _i64, _P, _P],
+        "pdmp_mlp_gradient": [MP, _P, _P, _i32, _i32, _P, _P, _P, _P, _sz, _P],
         "pdmp_mlp_train_step": [MP, _P, _P, _i32, _f32, _f32, _f32, _f32, _i32, _P, _P, _sz, _P],
         "pdmp_surrogate_infer": [MP, _FP, _P, _i64, _i32, _f32, _f32, _P, ctypes.POINTER(_i64), _P, _sz, _P],
         "pdmp_displacement_rms": [_P, _P, _i64, _i32, _P, _P],
+        "pdmp_residual_threshold": [_FP, _P, _i64, _i32, _f32, _f32, ctypes.POINTER(_f32), _P, _P, _sz, _P],
     }.items():
         fn = getattr(L, name)
         fn.argtypes = argt
@@ -874,8 +877,28 @@ def _mlp_sigs():
     L.pdmp_mlp_train_workspace.restype = _sz
     L.pdmp_surrogate_workspace.argtypes = [_FP, _i64]
     L.pdmp_surrogate_workspace.restype = _sz
+    L.pdmp_residual_threshold_workspace.argtypes = [_FP, _i64]
+    L.pdmp_residual_threshold_workspace.restype = _sz
     L._mlp_ready = True
     return L
+
+
+def residual_threshold(field: DeviceField, x0: torch.Tensor, T: int, eta: float, q: float = 0.99,
+                       out: torch.Tensor | None = None):
+    """(tau_r, x_T): the q-quantile (nearest rank) of the plain morph's
+    last-step length over the samples x0, and their x_T."""
+    L = _mlp_sigs()
+    N = x0.shape[0]
+    if out is None:
+        out = torch.empty_like(x0)
+    f = field.struct()
+    need = int(L.pdmp_residual_threshold_workspace(ctypes.byref(f), N))
+    ws = torch.empty(max(need, 16), dtype=torch.uint8, device=x0.device)
+    tau = _f32(0.0)
+    _check(L.pdmp_residual_threshold(ctypes.byref(f), _ptr(x0, name="x0"), N, int(T), float(eta), float(q),
+                                     ctypes.byref(tau), _ptr(out, shape=x0.shape, name="out"),
+                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()), "pdmp_residual_threshold")
+    return float(tau.value), out
 
 
 def displacement_rms(x0: torch.Tensor, xT: torch.Tensor) -> torch.Tensor:
@@ -987,13 +1010,33 @@ class Surrogate:
             o += s[0] * s[1]
         return out
 
-    def forward(self, x0: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    def forward(self, x0: torch.Tensor, out: torch.Tensor | None = None, fp32_act: bool = False) -> torch.Tensor:
+        """The predicted x_T; fp32_act selects the FP32-activation mode (diagnostic)."""
         if out is None:
             out = torch.empty_like(x0)
         m = self.struct()
-        _check(_mlp_sigs().pdmp_mlp_forward(ctypes.byref(m), _ptr(x0, name="x0"), x0.shape[0],
-                                            _ptr(out, shape=x0.shape, name="out"), _stream()), "pdmp_mlp_forward")
+        name = "pdmp_mlp_forward_fp32act" if fp32_act else "pdmp_mlp_forward"
+        _check(getattr(_mlp_sigs(), name)(ctypes.byref(m), _ptr(x0, name="x0"), x0.shape[0],
+                                          _ptr(out, shape=x0.shape, name="out"), _stream()), name)
         return out
+
+    def gradient(self, x0: torch.Tensor, xT: torch.Tensor, fp32_act: bool = False):
+        """(loss, gW, gb) of one batch without an update (diagnostic): the
+        gradient with respect to the BF16 weights, in the layouts of W and b."""
+        L = _mlp_sigs()
+        B = x0.shape[0]
+        need = int(L.pdmp_mlp_train_workspace(B))
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=x0.device)
+        loss = torch.zeros(1, device=x0.device)
+        gW = torch.empty(MLP_NW, device=x0.device)
+        gb = torch.empty(MLP_NB, device=x0.device)
+        m = self.struct()
+        _check(L.pdmp_mlp_gradient(ctypes.byref(m), _ptr(x0, name="x0"), _ptr(xT, shape=x0.shape, name="xT"), B,
+                                   int(bool(fp32_act)), _ptr(loss), _ptr(gW), _ptr(gb),
+                                   ctypes.c_void_p(self._ws.data_ptr()), self._ws.numel(), _stream()),
+               "pdmp_mlp_gradient")
+        return loss, gW, gb
 
     def train_step(self, x0: torch.Tensor, xT: torch.Tensor, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                    loss: torch.Tensor | None = None):

@@ -775,7 +775,16 @@ pdmp_status pdmp_mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, fl
   if (N < 0) return PDMP_ERR_INVALID_ARG;
   if (N == 0) return PDMP_OK;
   if (!ok_ptr(x0, true) || !ok_ptr(xT_hat, true)) return PDMP_ERR_INVALID_ARG;
-  return cuda_status(pdmp::mlp_forward(net, x0, N, xT_hat, as_stream(stream)));
+  return cuda_status(pdmp::mlp_forward(net, x0, N, xT_hat, false, as_stream(stream)));
+}
+
+pdmp_status pdmp_mlp_forward_fp32act(const pdmp_mlp* net, const float* x0, int64_t N, float* xT_hat, void* stream) {
+  pdmp_status s = check_mlp(net, false);
+  if (s != PDMP_OK) return s;
+  if (N < 0) return PDMP_ERR_INVALID_ARG;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT_hat, true)) return PDMP_ERR_INVALID_ARG;
+  return cuda_status(pdmp::mlp_forward(net, x0, N, xT_hat, true, as_stream(stream)));
 }
 
 size_t pdmp_mlp_train_workspace(int32_t B) { return B < 1 ? 0 : pdmp::mlp_train_workspace(B); }
@@ -793,6 +802,18 @@ pdmp_status pdmp_mlp_train_step(const pdmp_mlp* net, const float* x0, const floa
     return PDMP_ERR_INVALID_ARG;
   if (ws_bytes < pdmp::mlp_train_workspace(B)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
   return cuda_status(pdmp::mlp_train_step(net, x0, xT, B, lr, beta1, beta2, eps, step, loss, ws, as_stream(stream)));
+}
+
+pdmp_status pdmp_mlp_gradient(const pdmp_mlp* net, const float* x0, const float* xT, int32_t B, int32_t fp32_act,
+                              float* loss, float* gW, float* gb, void* ws, size_t ws_bytes, void* stream) {
+  pdmp_status s = check_mlp(net, false);
+  if (s != PDMP_OK) return s;
+  if (B < 1 || (fp32_act != 0 && fp32_act != 1)) return PDMP_ERR_INVALID_ARG;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || !ok_ptr(loss, false) || !ok_ptr(gW, true) || !ok_ptr(gb, true) ||
+      ws == nullptr || !aligned16(ws))
+    return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::mlp_train_workspace(B)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  return cuda_status(pdmp::mlp_gradient(net, x0, xT, B, fp32_act != 0, loss, gW, gb, ws, as_stream(stream)));
 }
 
 pdmp_status pdmp_displacement_rms(const float* x0, const float* xT, int64_t N, int32_t d, float* rms, void* stream) {
@@ -823,6 +844,29 @@ pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const
   if (ws_bytes < pdmp::surrogate_workspace(f->d, f->M, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
   return cuda_status(pdmp::surrogate_infer(net, f->d, field_args(f), x0, N, T, eta, tau_r, xT, n_fallback, ws,
                                            as_stream(stream)));
+}
+
+size_t pdmp_residual_threshold_workspace(const pdmp_field* f, int64_t N) {
+  if (check_field(f) != PDMP_OK || f->kind != PDMP_KIND_RBF || (f->d != 2 && f->d != 3) || N < 1) return 0;
+  return pdmp::residual_threshold_workspace(f->d, f->M, N);
+}
+
+pdmp_status pdmp_residual_threshold(const pdmp_field* f, const float* x0, int64_t N, int32_t T, float eta, float q,
+                                    float* tau_r, float* xT, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("pdmp_residual_threshold");
+  pdmp_status s = check_field(f);
+  if (s != PDMP_OK) return s;
+  if (f->kind != PDMP_KIND_RBF || (f->d != 2 && f->d != 3)) return PDMP_ERR_UNSUPPORTED;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 1 || N >= ((int64_t)1 << 31) || T < 1 || !(q > 0.0f && q <= 1.0f) || tau_r == nullptr)
+    return PDMP_ERR_INVALID_ARG;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT, false) || ws == nullptr || !aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::residual_threshold_workspace(f->d, f->M, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  // nearest rank: the ceil(q N)-th smallest length
+  int64_t k = (int64_t)std::ceil((double)q * (double)N) - 1;
+  if (k < 0) k = 0;
+  if (k > N - 1) k = N - 1;
+  return cuda_status(pdmp::residual_threshold(f->d, field_args(f), x0, N, T, eta, k, tau_r, xT, ws, as_stream(stream)));
 }
 
 size_t pdmp_fit_workspace(int64_t M, int64_t n) {

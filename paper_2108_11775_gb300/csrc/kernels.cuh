@@ -118,8 +118,10 @@ cudaError_t batch_run(const pdmp_batch_plan* plan, void* ws, cudaStream_t st);
 // surrogate MLP (mlp.cu, surrogate.cu)
 constexpr int64_t kMlpNW = 39 * 128 + 2 * 128 * 128 + 3 * 128;  // weights W1 (over the 39-wide encoding), W2, W3, W4
 constexpr int64_t kMlpNB = 3 * 128 + 3;                         // biases b1, b2, b3, b4
-cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, cudaStream_t st);
+cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, bool fp32_act, cudaStream_t st);
 size_t mlp_train_workspace(int B);
+cudaError_t mlp_gradient(const pdmp_mlp* net, const float* x0, const float* xT, int B, bool fp32_act, float* loss,
+                         float* gW, float* gb, void* ws, cudaStream_t st);
 cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int B, float lr, float beta1,
                            float beta2, float eps, int step, float* loss, void* ws, cudaStream_t st);
 cudaError_t mlp_refresh(const pdmp_mlp* net, cudaStream_t st);
@@ -127,6 +129,9 @@ size_t surrogate_workspace(int d, int64_t M, int64_t N);
 cudaError_t displacement_rms(const float* x0, const float* xT, int64_t N, int d, float* rms, cudaStream_t st);
 cudaError_t surrogate_infer(const pdmp_mlp* net, int d, const FieldArgs& fa, const float* x0, int64_t N, int T,
                             float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, cudaStream_t st);
+size_t residual_threshold_workspace(int d, int64_t M, int64_t N);
+cudaError_t residual_threshold(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int64_t k,
+                               float* tau_r, float* xT, void* ws, cudaStream_t st);
 
 size_t fit_workspace(int64_t M, int64_t n);
 cudaError_t fit_occupancy(int kind, int d, const FieldArgs& geom, const float* X, const uint8_t* y, int64_t n,

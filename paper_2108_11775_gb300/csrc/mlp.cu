@@ -14,8 +14,19 @@
 //
 // Training: forward with saved pre-activations, backward through the same
 // fragment layouts (dA = dZ W on the tensor cores with transposed weight
-// copies), weight gradients as fixed-order FP32 sums over the batch, and Adam
-// on FP32 master weights that rewrites the BF16 copies.
+// copies), then the weight and bias gradients of every layer as one more
+// tensor-core contraction per layer, [dW | db] = dZ^T [a | 1] over the batch
+// (BF16 operands staged transposed in shared memory, FP32 accumulation;
+// blocks of 64 samples write partial sums that a second kernel adds in a
+// fixed order), and Adam on FP32 master weights that rewrites the BF16 copies.
+//
+// FP32-activation mode (diagnostic): the same kernels and fragment layouts
+// with every activation and backward signal fed to the tensor cores as the
+// sum of three BF16 pieces (hi + mid + lo, which carry 24 bits and more of
+// the FP32 value), so the products are those of FP32 activations with the
+// BF16 weights.  The network's arithmetic then matches an FP64 evaluation of
+// the same BF16 weights to FP32 rounding, which separates a fragment-layout
+// fault from BF16 rounding.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -93,10 +104,20 @@ __device__ void load_weights(const MlpArgs& a, MlpSmem* s, bool transposed) {
   if (threadIdx.x < 4) s->b4[threadIdx.x] = threadIdx.x < 3 ? a.b4[threadIdx.x] : 0.0f;
 }
 
-// acc[16][4] (C fragments over 128 columns) -> A fragments [8][4] after bias + SiLU;
-// Z (optional, B x 128 rows) receives the pre-activations of rows r0, r1 (< B)
-__device__ __forceinline__ void act_to_afrag(float (&acc)[16][4], const float* bias, int t, uint32_t (&af)[8][4],
-                                             float* Z = nullptr, int64_t r0 = 0, int64_t r1 = 0, int64_t B = 0) {
+// piece p (0, 1, 2) of the three-way BF16 split of x: x = hi + mid + lo up to
+// 2^-27 |x| (piece 2 is rounded to BF16 when packed)
+__device__ __forceinline__ float bf16_piece(float x, int p) {
+  const float h = __bfloat162float(__float2bfloat16_rn(x));
+  if (p == 0) return h;
+  const float r = x - h;
+  const float m = __bfloat162float(__float2bfloat16_rn(r));
+  return p == 1 ? m : r - m;
+}
+
+// bias + SiLU in place on acc[16][4] (C fragments over 128 columns); Z
+// (optional, B x 128 rows) receives the pre-activations of rows r0, r1 (< B)
+__device__ __forceinline__ void bias_silu(float (&acc)[16][4], const float* bias, int t, float* Z = nullptr,
+                                          int64_t r0 = 0, int64_t r1 = 0, int64_t B = 0) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const int c = 8 * j + 2 * t;
@@ -111,20 +132,23 @@ __device__ __forceinline__ void act_to_afrag(float (&acc)[16][4], const float* b
     acc[j][2] = silu_f(v2);
     acc[j][3] = silu_f(v3);
   }
+}
+
+// C fragments over 128 columns -> A fragments [8][4] of BF16 piece p: the
+// accumulator of column tiles 2kk, 2kk + 1 is the A fragment of k tile kk
+__device__ __forceinline__ void to_afrag(const float (&v)[16][4], int p, uint32_t (&af)[8][4]) {
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
-    af[kk][0] = pack_bf16(acc[2 * kk][0], acc[2 * kk][1]);
-    af[kk][1] = pack_bf16(acc[2 * kk][2], acc[2 * kk][3]);
-    af[kk][2] = pack_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
-    af[kk][3] = pack_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
+    af[kk][0] = pack_bf16(bf16_piece(v[2 * kk][0], p), bf16_piece(v[2 * kk][1], p));
+    af[kk][1] = pack_bf16(bf16_piece(v[2 * kk][2], p), bf16_piece(v[2 * kk][3], p));
+    af[kk][2] = pack_bf16(bf16_piece(v[2 * kk + 1][0], p), bf16_piece(v[2 * kk + 1][1], p));
+    af[kk][3] = pack_bf16(bf16_piece(v[2 * kk + 1][2], p), bf16_piece(v[2 * kk + 1][3], p));
   }
 }
 
-// acc = A (16 x 128) * W^T for a 128 x 128 smem weight image W[n][k]
-__device__ __forceinline__ void gemm_128(const uint32_t (&af)[8][4], const uint32_t* W, int g, int t,
-                                         float (&acc)[16][4]) {
-#pragma unroll
-  for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+// acc += A (16 x 128) * W^T for a 128 x 128 smem weight image W[n][k]
+__device__ __forceinline__ void gemm_128_acc(const uint32_t (&af)[8][4], const uint32_t* W, int g, int t,
+                                             float (&acc)[16][4]) {
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk)
 #pragma unroll
@@ -134,20 +158,71 @@ __device__ __forceinline__ void gemm_128(const uint32_t (&af)[8][4], const uint3
     }
 }
 
-// Fourier encoding of a normalised input (FP32; sin / cos after reduction to [-pi, pi])
+// v <- v W^T (v: a warp's 16 rows of activations in C-fragment layout).
+// EXACT: v enters as three BF16 pieces (FP32-activation mode).
+template <bool EXACT>
+__device__ __forceinline__ void dense_128(float (&v)[16][4], const uint32_t* W, int g, int t) {
+  if constexpr (EXACT) {
+    float h[16][4];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        h[j][q] = v[j][q];
+        v[j][q] = 0.0f;
+      }
+#pragma unroll 1
+    for (int p = 0; p < 3; ++p) {
+      uint32_t af[8][4];
+      to_afrag(h, p, af);
+      gemm_128_acc(af, W, g, t, v);
+    }
+  } else {
+    uint32_t af[8][4];
+    to_afrag(v, 0, af);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j][0] = v[j][1] = v[j][2] = v[j][3] = 0.0f;
+    gemm_128_acc(af, W, g, t, v);
+  }
+}
+
+// o (one n8 tile: columns 2t, 2t + 1 of rows g, g + 8) = v W4^T
+template <bool EXACT>
+__device__ __forceinline__ void dense_out(const float (&v)[16][4], const uint32_t* W4, int g, int t, float (&o)[4]) {
+  o[0] = o[1] = o[2] = o[3] = 0.0f;
+#pragma unroll 1
+  for (int p = 0; p < (EXACT ? 3 : 1); ++p) {
+    uint32_t af[8][4];
+    to_afrag(v, p, af);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const uint32_t* row = W4 + g * kRowU32 + 8 * kk;
+      mma16816(o, af[kk], row[t], row[4 + t]);
+    }
+  }
+}
+
+// Fourier encoding of a normalised input.  sin(2^k pi u) = sin(2 pi tau)
+// with tau = 2^(k-1) u, which is exact in FP32 (a power of two times u), and
+// so is its distance r = tau - rint(tau) to the nearest integer: the angle
+// 2 pi r in [-pi, pi] is the only rounded step.  The training and inference
+// kernels take sin / cos on the special-function unit; the FP32-activation
+// mode takes CUDA's sinf / cosf.
+template <bool EXACT>
 __device__ __forceinline__ void encode(const float* u, float* e) {
 #pragma unroll
   for (int j = 0; j < 3; ++j) e[j] = u[j];
-  float f = 3.14159265358979f;
+  float h = 0.5f;
 #pragma unroll
   for (int k = 0; k < kFreq; ++k) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const float th = reduce_2pi(f * u[j]);
-      e[3 + 6 * k + j] = sin_approx(th);
-      e[3 + 6 * k + 3 + j] = cos_approx(th);
+      const float tau = h * u[j];
+      const float th = 6.28318530717958648f * (tau - rintf(tau));
+      e[3 + 6 * k + j] = EXACT ? sinf(th) : sin_approx(th);
+      e[3 + 6 * k + 3 + j] = EXACT ? cosf(th) : cos_approx(th);
     }
-    f *= 2.0f;
+    h *= 2.0f;
   }
 }
 
@@ -181,6 +256,7 @@ __device__ __forceinline__ void normalise(const MlpArgs& a, const float* x, floa
 
 // ---------------------------------------------------------------- inference
 // y[n] = x0[n] + out_scale * f(u(x0[n]))  (the predicted x_T)
+template <bool EXACT>
 __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpArgs a, const float* __restrict__ x0, int64_t N,
                                                                  float* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -201,22 +277,17 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpArgs a, const
     normalise(a, x_0, u0);
     normalise(a, x_1, u1);
     float e0[kEnc], e1[kEnc];
-    encode(u0, e0);
-    encode(u1, e1);
+    encode<EXACT>(u0, e0);
+    encode<EXACT>(u1, e1);
     float acc[16][4];
-    uint32_t af[8][4];
     input_layer(s, e0, e1, t, acc);
-    act_to_afrag(acc, s->b1, t, af);
-    gemm_128(af, s->W2, g, t, acc);
-    act_to_afrag(acc, s->b2, t, af);
-    gemm_128(af, s->W3, g, t, acc);
-    act_to_afrag(acc, s->b3, t, af);
-    float o[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      const uint32_t* row = s->W4 + g * kRowU32 + 8 * kk;
-      mma16816(o, af[kk], row[t], row[4 + t]);
-    }
+    bias_silu(acc, s->b1, t);
+    dense_128<EXACT>(acc, s->W2, g, t);
+    bias_silu(acc, s->b2, t);
+    dense_128<EXACT>(acc, s->W3, g, t);
+    bias_silu(acc, s->b3, t);
+    float o[4];
+    dense_out<EXACT>(acc, s->W4, g, t, o);
     // lane (g, t) holds columns 2t, 2t + 1 of rows g and g + 8; outputs are columns 0..2
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -234,6 +305,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpArgs a, const
 // input u (B x 3) and dY = d loss / d output (B x 3) for the MSE loss against
 // target (x_T - x_0) / out_scale; loss_rows[tile * 16 + r] gets row r's
 // squared error (summed in a fixed order later).
+template <bool EXACT>
 __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a, const float* __restrict__ x0,
                                                                        const float* __restrict__ xT, int B,
                                                                        float* __restrict__ Z,   // 3 x B x 128
@@ -259,8 +331,8 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a,
     normalise(a, x_0, u0);
     normalise(a, x_1, u1);
     float e0[kEnc], e1[kEnc];
-    encode(u0, e0);
-    encode(u1, e1);
+    encode<EXACT>(u0, e0);
+    encode<EXACT>(u1, e1);
     if (t == 0) {
       if (r0 < B)
 #pragma unroll
@@ -270,19 +342,14 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a,
         for (int i = 0; i < kEnc; ++i) U[(size_t)r1 * kEnc + i] = e1[i];
     }
     float acc[16][4];
-    uint32_t af[8][4];
     input_layer(s, e0, e1, t, acc);
-    act_to_afrag(acc, s->b1, t, af, Z, r0, r1, B);
-    gemm_128(af, s->W2, g, t, acc);
-    act_to_afrag(acc, s->b2, t, af, Z + (size_t)B * kH, r0, r1, B);
-    gemm_128(af, s->W3, g, t, acc);
-    act_to_afrag(acc, s->b3, t, af, Z + (size_t)2 * B * kH, r0, r1, B);
-    float o[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      const uint32_t* row = s->W4 + g * kRowU32 + 8 * kk;
-      mma16816(o, af[kk], row[t], row[4 + t]);
-    }
+    bias_silu(acc, s->b1, t, Z, r0, r1, B);
+    dense_128<EXACT>(acc, s->W2, g, t);
+    bias_silu(acc, s->b2, t, Z + (size_t)B * kH, r0, r1, B);
+    dense_128<EXACT>(acc, s->W3, g, t);
+    bias_silu(acc, s->b3, t, Z + (size_t)2 * B * kH, r0, r1, B);
+    float o[4];
+    dense_out<EXACT>(acc, s->W4, g, t, o);
     float q0 = 0.0f, q1 = 0.0f;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -314,6 +381,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a,
 
 // Backward through the activations: dZ3 = (dY W4) * silu'(z3), dZ2 = (dZ3 W3) * silu'(z2),
 // dZ1 = (dZ2 W2) * silu'(z1), into dZ (3 x B x 128); Z holds the pre-activations.
+template <bool EXACT>
 __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_backward(MlpArgs a, int B, const float* __restrict__ dY,
                                                                         const float* __restrict__ Z,
                                                                         float* __restrict__ dZ) {
@@ -335,7 +403,6 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_backward(MlpArgs a
 #pragma unroll
       for (int i = 0; i < 3; ++i) dy1[i] = dY[r1 * 3 + i];
     float acc[16][4];
-    uint32_t af[8][4];
     // dA3 = dY W4 (FP32)
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -368,49 +435,145 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_backward(MlpArgs a
         if (r1 < B) *reinterpret_cast<float2*>(dZl + (size_t)r1 * kH + c) = make_float2(acc[j][2], acc[j][3]);
       }
       if (l == 0) break;
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        af[kk][0] = pack_bf16(acc[2 * kk][0], acc[2 * kk][1]);
-        af[kk][1] = pack_bf16(acc[2 * kk][2], acc[2 * kk][3]);
-        af[kk][2] = pack_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
-        af[kk][3] = pack_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
-      }
       // dA_{l-1} = dZ_l W_l: B operand (k = out, n = in) from the transposed image W_l^T[in][out]
-      gemm_128(af, l == 2 ? s->W3 : s->W2, g, t, acc);
+      dense_128<EXACT>(acc, l == 2 ? s->W3 : s->W2, g, t);
     }
   }
 }
 
-// Weight and bias gradients as fixed-order sums over the batch:
-//   dW_l[o][i] = sum_b dZ_l[b][o] a_{l-1}[b][i],  db_l[o] = sum_b dZ_l[b][o],
-// with a_0 = u and a_l = silu(z_l) recomputed from the saved pre-activations.
-// grid.x covers the outputs of one layer; blockIdx.y selects the layer.
-__global__ void k_mlp_weight_grads(int B, const float* __restrict__ U, const float* __restrict__ Zf,
-                                   const float* __restrict__ dZ, const float* __restrict__ dY,
-                                   float* __restrict__ gW, float* __restrict__ gb) {
-  // gW layout: W1 (128 x kEnc), W2 (128x128), W3 (128x128), W4 (3x128); gb: b1, b2, b3, b4
-  const int layer = blockIdx.y;   // 0..3
-  const int in_dim = layer == 0 ? kEnc : kH, out_dim = layer == 3 ? 3 : kH;
-  const int64_t w1 = (int64_t)kEnc * kH;
-  const int64_t woff = layer == 0 ? 0 : (layer == 1 ? w1 : (layer == 2 ? w1 + kH * kH : w1 + 2 * kH * kH));
-  const int boff = layer * kH;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nw = in_dim * out_dim;
-  if (idx >= nw + out_dim) return;
-  const bool is_bias = idx >= nw;
-  const int o = is_bias ? idx - nw : idx / in_dim, i = is_bias ? 0 : idx % in_dim;
-  double acc = 0.0;
-  for (int b = 0; b < B; ++b) {
-    const float dz = layer == 3 ? dY[(size_t)b * 3 + o] : dZ[((size_t)layer * B + b) * kH + o];
-    float av = 1.0f;
-    if (!is_bias) {
-      if (layer == 0) av = U[(size_t)b * kEnc + i];
-      else av = silu_f(Zf[((size_t)(layer - 1) * B + b) * kH + i]);
-    }
-    acc += (double)dz * (double)av;
+// Weight and bias gradients on the tensor cores: for layer l,
+//   [dW_l | db_l] = dZ_l^T [a_{l-1} | 1]   (out x (in + 1)), summed over the batch,
+// with a_0 = enc(u), a_l = silu(z_l) recomputed from the saved pre-activations
+// and dZ_4 = dY.  blockIdx.x takes 64 samples, blockIdx.y the layer; both
+// operands are staged transposed (rows = output / input unit, 32 BF16 pairs of
+// samples per row) so that fragments are 32-bit loads, and the block writes its
+// partial sums to part[blockIdx.x] (weights then biases, the layout of gW, gb).
+// EXACT: both operands as three BF16 pieces, the six products of pieces whose
+// orders add up to at most 2.
+constexpr int kGradKC = 64;                         // samples per block
+constexpr int kGradRow = kGradKC / 2 + 4;           // u32 per staged row (36: conflict-free fragment loads)
+constexpr int kGradRowsA = 128, kGradRowsB = 136;   // output units; input units + the ones row, padded
+
+template <bool EXACT>
+constexpr size_t grad_smem_bytes() {
+  return sizeof(uint32_t) * (EXACT ? 3 : 1) * (kGradRowsA + kGradRowsB) * kGradRow;
+}
+
+__device__ __forceinline__ size_t layer_woff(int l) {
+  return l == 0 ? 0 : (size_t)kEnc * kH + (size_t)(l - 1) * kH * kH;
+}
+
+// stage rows [0, rows) x the block's samples of one operand (value(b, r)) as BF16 pieces
+template <int P, typename F>
+__device__ __forceinline__ void stage_t(uint32_t* dst, int rows, int b0, int B, F value) {
+  for (int i = threadIdx.x; i < rows * (kGradKC / 2); i += blockDim.x) {
+    const int r = i % rows, pr = i / rows;
+    const int b = b0 + 2 * pr;
+    const float v0 = b < B ? value(b, r) : 0.0f;
+    const float v1 = b + 1 < B ? value(b + 1, r) : 0.0f;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      dst[(p * rows + r) * kGradRow + pr] = pack_bf16(bf16_piece(v0, p), bf16_piece(v1, p));
   }
-  if (is_bias) gb[boff + o] = (float)acc;
-  else gW[woff + idx] = (float)acc;
+}
+
+// one warp: MTW m tiles from mt0 x NTW n tiles nt0, nt0 + NS, ... (< NT) of C = A^T-staged x B^T-staged
+template <bool EXACT, int MTW, int NTW, int NS, int NT>
+__device__ __forceinline__ void grad_tiles(const uint32_t* sA, int rowsA, const uint32_t* sB, int rowsB, int mt0,
+                                           int nt0, int O, int I, size_t woff, size_t boff, float* __restrict__ part) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float acc[MTW][NTW][4];
+#pragma unroll
+  for (int i = 0; i < MTW; ++i)
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.0f;
+#pragma unroll 1
+  for (int pp = 0; pp < (EXACT ? 6 : 1); ++pp) {
+    // piece pairs (pa, pb) with pa + pb <= 2
+    const int pa = pp < 3 ? 0 : (pp < 5 ? 1 : 2), pb = pp < 3 ? pp : (pp < 5 ? pp - 3 : 0);
+    const uint32_t* A = sA + (size_t)pa * rowsA * kGradRow;
+    const uint32_t* Bm = sB + (size_t)pb * rowsB * kGradRow;
+#pragma unroll
+    for (int kk = 0; kk < kGradKC / 16; ++kk) {
+      uint32_t af[MTW][4];
+#pragma unroll
+      for (int i = 0; i < MTW; ++i) {
+        const uint32_t* r0 = A + (16 * (mt0 + i) + g) * kGradRow + 8 * kk;
+        const uint32_t* r1 = r0 + 8 * kGradRow;
+        af[i][0] = r0[t];
+        af[i][1] = r1[t];
+        af[i][2] = r0[4 + t];
+        af[i][3] = r1[4 + t];
+      }
+#pragma unroll
+      for (int j = 0; j < NTW; ++j) {
+        const int nt = nt0 + j * NS;
+        if (nt < NT) {
+          const uint32_t* row = Bm + (8 * nt + g) * kGradRow + 8 * kk;
+          const uint32_t b0 = row[t], b1 = row[4 + t];
+#pragma unroll
+          for (int i = 0; i < MTW; ++i) mma16816(acc[i][j], af[i], b0, b1);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < MTW; ++i)
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) {
+      const int nt = nt0 + j * NS;
+      if (nt >= NT) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = 16 * (mt0 + i) + g + (q >= 2 ? 8 : 0), c = 8 * nt + 2 * t + (q & 1);
+        if (o >= O) continue;
+        if (c < I) part[woff + (size_t)o * I + c] = acc[i][j][q];
+        else if (c == I) part[(size_t)kMlpNW + boff + o] = acc[i][j][q];
+      }
+    }
+}
+
+template <bool EXACT>
+__global__ void __launch_bounds__(128, 1) k_mlp_weight_grads(int B, const float* __restrict__ U,
+                                                             const float* __restrict__ Zf, const float* __restrict__ dZ,
+                                                             const float* __restrict__ dY, float* __restrict__ part) {
+  extern __shared__ __align__(16) uint32_t gsm[];
+  constexpr int P = EXACT ? 3 : 1;
+  const int layer = blockIdx.y, b0 = blockIdx.x * kGradKC, warp = threadIdx.x >> 5;
+  const int I = layer == 0 ? kEnc : kH, O = layer == 3 ? 3 : kH;
+  const int rowsA = layer == 3 ? 16 : kGradRowsA, rowsB = layer == 0 ? 40 : kGradRowsB;
+  uint32_t* sA = gsm;
+  uint32_t* sB = gsm + (size_t)P * rowsA * kGradRow;
+  float* out = part + (size_t)blockIdx.x * (kMlpNW + kMlpNB);
+  if (layer == 3)
+    stage_t<P>(sA, rowsA, b0, B, [&](int b, int r) { return r < 3 ? dY[(size_t)b * 3 + r] : 0.0f; });
+  else
+    stage_t<P>(sA, rowsA, b0, B, [&](int b, int r) { return dZ[((size_t)layer * B + b) * kH + r]; });
+  if (layer == 0)
+    stage_t<P>(sB, rowsB, b0, B, [&](int b, int r) { return r < kEnc ? U[(size_t)b * kEnc + r] : (r == kEnc ? 1.0f : 0.0f); });
+  else
+    stage_t<P>(sB, rowsB, b0, B, [&](int b, int r) {
+      return r < kH ? silu_f(Zf[((size_t)(layer - 1) * B + b) * kH + r]) : (r == kH ? 1.0f : 0.0f);
+    });
+  __syncthreads();
+  const size_t woff = layer_woff(layer), boff = (size_t)layer * kH;
+  if (layer == 0)
+    grad_tiles<EXACT, 2, 5, 1, 5>(sA, rowsA, sB, rowsB, 2 * warp, 0, O, I, woff, boff, out);
+  else if (layer < 3)
+    grad_tiles<EXACT, 2, 17, 1, 17>(sA, rowsA, sB, rowsB, 2 * warp, 0, O, I, woff, boff, out);
+  else
+    grad_tiles<EXACT, 1, 5, 4, 17>(sA, rowsA, sB, rowsB, 0, warp, O, I, woff, boff, out);
+}
+
+// gW, gb = the blocks' partial sums added in block order
+__global__ void k_mlp_grad_sum(const float* __restrict__ part, int nparts, float* __restrict__ gW,
+                               float* __restrict__ gb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kMlpNW + kMlpNB) return;
+  float acc = 0.0f;
+  for (int c = 0; c < nparts; ++c) acc += part[(size_t)c * (kMlpNW + kMlpNB) + i];
+  if (i < kMlpNW) gW[i] = acc;
+  else gb[i - kMlpNW] = acc;
 }
 
 // Adam on FP32 masters; rewrites the BF16 copies (and the transposed copies of W2, W3)
@@ -516,49 +679,78 @@ cudaError_t mlp_refresh(const pdmp_mlp* net, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, cudaStream_t st) {
-  if (N == 0) return cudaSuccess;
+template <bool EXACT>
+static cudaError_t launch_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, cudaStream_t st) {
   const size_t smem = sizeof(MlpSmem);
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_forward<EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = mlp_grid((N + 15) / 16, (const void*)k_mlp_forward);
-  k_mlp_forward<<<grid, 32 * kMlpWarps, smem, st>>>(mlp_args(net), x0, N, y);
+  const int grid = mlp_grid((N + 15) / 16, (const void*)k_mlp_forward<EXACT>);
+  k_mlp_forward<EXACT><<<grid, 32 * kMlpWarps, smem, st>>>(mlp_args(net), x0, N, y);
   return cudaGetLastError();
+}
+
+cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, bool fp32_act, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  return fp32_act ? launch_forward<true>(net, x0, N, y, st) : launch_forward<false>(net, x0, N, y, st);
 }
 
 static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
+static int grad_parts(int B) { return (B + kGradKC - 1) / kGradKC; }
+
 size_t mlp_train_workspace(int B) {
   return 2 * al256(sizeof(float) * 3 * (size_t)B * kH) + al256(sizeof(float) * kEnc * (size_t)B) +
-         2 * al256(sizeof(float) * 3 * (size_t)B) + al256(sizeof(float) * kMlpNW) + al256(sizeof(float) * kMlpNB);
+         2 * al256(sizeof(float) * 3 * (size_t)B) + al256(sizeof(float) * kMlpNW) + al256(sizeof(float) * kMlpNB) +
+         al256(sizeof(float) * (size_t)grad_parts(B) * (kMlpNW + kMlpNB));
 }
 
-cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int B, float lr, float beta1,
-                           float beta2, float eps, int step, float* loss, void* ws, cudaStream_t st) {
-  char* p = (char*)ws;
+template <bool EXACT>
+static cudaError_t launch_gradient(const pdmp_mlp* net, const float* x0, const float* xT, int B, float* loss,
+                                   float* gW, float* gb, char* p, cudaStream_t st) {
   auto take = [&](size_t b) { char* q = p; p += al256(b); return q; };
   float* Z = (float*)take(sizeof(float) * 3 * (size_t)B * kH);
   float* dZ = (float*)take(sizeof(float) * 3 * (size_t)B * kH);
   float* U = (float*)take(sizeof(float) * kEnc * (size_t)B);
   float* dY = (float*)take(sizeof(float) * 3 * (size_t)B);
   float* err = (float*)take(sizeof(float) * 3 * (size_t)B);
-  float* gW = (float*)take(sizeof(float) * kMlpNW);
-  float* gb = (float*)take(sizeof(float) * kMlpNB);
+  take(sizeof(float) * kMlpNW);   // gW, gb of the training step
+  take(sizeof(float) * kMlpNB);
+  float* part = (float*)take(sizeof(float) * (size_t)grad_parts(B) * (kMlpNW + kMlpNB));
   const MlpArgs a = mlp_args(net);
   const size_t smem = sizeof(MlpSmem);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_mlp_train_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+  if ((e = cudaFuncSetAttribute(k_mlp_train_forward<EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return e;
-  if ((e = cudaFuncSetAttribute(k_mlp_train_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+  if ((e = cudaFuncSetAttribute(k_mlp_train_backward<EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return e;
+  constexpr size_t gsmem = grad_smem_bytes<EXACT>();
+  if ((e = cudaFuncSetAttribute(k_mlp_weight_grads<EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem)))
     return e;
   const int64_t tiles = (B + 15) / 16;
-  const int gf = mlp_grid(tiles, (const void*)k_mlp_train_forward);
-  k_mlp_train_forward<<<gf, 32 * kMlpWarps, smem, st>>>(a, x0, xT, B, Z, U, dY, err);
+  const int gf = mlp_grid(tiles, (const void*)k_mlp_train_forward<EXACT>);
+  k_mlp_train_forward<EXACT><<<gf, 32 * kMlpWarps, smem, st>>>(a, x0, xT, B, Z, U, dY, err);
   if (loss) k_mlp_loss<<<1, 1024, 0, st>>>(err, B, loss);
-  const int gbk = mlp_grid(tiles, (const void*)k_mlp_train_backward);
-  k_mlp_train_backward<<<gbk, 32 * kMlpWarps, smem, st>>>(a, B, dY, Z, dZ);
-  const dim3 gg((unsigned)((kH * kH + kH + 127) / 128), 4);   // covers the largest layer (128 x 128 + 128)
-  k_mlp_weight_grads<<<gg, 128, 0, st>>>(B, U, Z, dZ, dY, gW, gb);
+  const int gbk = mlp_grid(tiles, (const void*)k_mlp_train_backward<EXACT>);
+  k_mlp_train_backward<EXACT><<<gbk, 32 * kMlpWarps, smem, st>>>(a, B, dY, Z, dZ);
+  k_mlp_weight_grads<EXACT><<<dim3((unsigned)grad_parts(B), 4), 128, gsmem, st>>>(B, U, Z, dZ, dY, part);
+  k_mlp_grad_sum<<<(unsigned)((kMlpNW + kMlpNB + 255) / 256), 256, 0, st>>>(part, grad_parts(B), gW, gb);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_gradient(const pdmp_mlp* net, const float* x0, const float* xT, int B, bool fp32_act, float* loss,
+                         float* gW, float* gb, void* ws, cudaStream_t st) {
+  return fp32_act ? launch_gradient<true>(net, x0, xT, B, loss, gW, gb, (char*)ws, st)
+                  : launch_gradient<false>(net, x0, xT, B, loss, gW, gb, (char*)ws, st);
+}
+
+cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT, int B, float lr, float beta1,
+                           float beta2, float eps, int step, float* loss, void* ws, cudaStream_t st) {
+  char* p = (char*)ws + 2 * al256(sizeof(float) * 3 * (size_t)B * kH) + al256(sizeof(float) * kEnc * (size_t)B) +
+            2 * al256(sizeof(float) * 3 * (size_t)B);
+  float* gW = (float*)p;
+  float* gb = (float*)(p + al256(sizeof(float) * kMlpNW));
+  cudaError_t e = launch_gradient<false>(net, x0, xT, B, loss, gW, gb, (char*)ws, st);
+  if (e != cudaSuccess) return e;
   float* mW = net->adam;
   float* vW = net->adam + kMlpNW;
   float* mb = net->adam + 2 * kMlpNW;

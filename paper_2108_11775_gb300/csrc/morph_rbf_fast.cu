@@ -74,10 +74,12 @@ static cudaError_t launch_fast(const FieldArgs& fa, const float* x0, int64_t N, 
   a.g_out = g_out;
   const unsigned blocks = (unsigned)((N + FastShape::kTile - 1) / FastShape::kTile);
   if (traj != nullptr) {
-    cudaFuncSetAttribute(k_morph_rbf_fast<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_morph_rbf_fast<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_morph_rbf_fast<D, true><<<blocks, FastShape::kThreads, smem, st>>>(a);
   } else {
-    cudaFuncSetAttribute(k_morph_rbf_fast<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_morph_rbf_fast<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_morph_rbf_fast<D, false><<<blocks, FastShape::kThreads, smem, st>>>(a);
   }
   return cudaGetLastError();

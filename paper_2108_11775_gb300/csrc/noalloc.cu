@@ -9,7 +9,10 @@
 // until the process exits.  Host code cannot use the array's name as a device
 // address, so the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and caches it; that first
-// call should come before any stream capture.  All calls share the array and
+// call should come before any stream capture.  The cached address belongs to
+// the device's primary context: after cudaDeviceReset (or any teardown of the
+// primary context) on that device it is stale, so a process that resets a
+// device must not call this entry point on it again.  All calls share the array and
 // it keeps the previous call's contents; the sort clears what must start at
 // zero on every call.  Calls that overlap on the GPU (different streams, or
 // different host threads) race on the array and must be serialised by the

@@ -1,9 +1,19 @@
 // Spatial ordering of the samples for the fast RBF morph: a counting sort of
 // the samples by the Hilbert index of their grid cell (over the samples'
-// bounding box), made deterministic by ordering each cell's samples by their
-// original index.  Consecutive samples of the resulting permutation are
+// bounding box).  Consecutive samples of the resulting permutation are
 // spatially close (the Hilbert order never jumps between distant cells),
 // which keeps a tile's extent small.
+//
+// Determinism.  The scatter places a cell's samples in atomic arrival order;
+// k_order_cells then orders every cell of 2 to 64 samples by original index.
+// The grid is sized for about four samples per cell, so on inputs spread over
+// their bounding box every cell is ordered and the permutation, the tiles and
+// every result are reproducible bit for bit.  A cell of more than 64 samples
+// (clustered inputs, or an outlier that stretches the bounding box) keeps the
+// arrival order, which can change from run to run: the tiles, their origins
+// and their choice between the expanded and the direct form can then differ,
+// and so can the rounding of the results (within the kernels' accuracy: the
+// tile a sample falls in changes only the rounding of its arithmetic).
 #include "kernels.cuh"
 #include "sort.cuh"
 
@@ -123,7 +133,7 @@ __global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t N, uint32_t
 }
 
 // orders each cell's entries by original index (cells of up to 64 entries;
-// larger cells keep the arrival order)
+// larger cells keep the arrival order: see the note on determinism above)
 __global__ void k_order_cells(const uint32_t* __restrict__ offs, const uint32_t* __restrict__ counts, int64_t C,
                               int32_t* __restrict__ perm) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -9,6 +9,8 @@
 //      either is not finite;
 //   4. failed samples are compacted (prefix sum, so in index order), morphed
 //      by the plain T-step kernel from their x0, and scattered back.
+#include <cstring>
+
 #include "kernels.cuh"
 #include "sort.cuh"
 
@@ -114,7 +116,7 @@ cudaError_t surrogate_infer(const pdmp_mlp* net, int d, const FieldArgs& fa, con
   if (N == 0) return cudaSuccess;
   SurWs w = sur_layout(ws, d, fa.M, N);
   cudaError_t e;
-  if ((e = mlp_forward(net, x0, N, xT, st))) return e;
+  if ((e = mlp_forward(net, x0, N, xT, false, st))) return e;
   if (T == 0) return cudaSuccess;
   // one plain step at every prediction: traj[0] = prediction, steps[0] = its increment, s = its logit
   if ((e = morph_rbf_fast(d, fa, xT, N, 1, eta, nullptr, nullptr, 0, w.traj, w.steps, w.fast, st, w.s))) return e;
@@ -131,6 +133,136 @@ cudaError_t surrogate_infer(const pdmp_mlp* net, int d, const FieldArgs& fa, con
   k_gather<<<gb, 256, 0, st>>>(x0, w.idx, cnt, d, w.xs);
   if ((e = morph_rbf_fast(d, fa, w.xs, cnt, T, eta, w.ys, nullptr, 0, nullptr, nullptr, w.fast, st))) return e;
   k_scatter_rows<<<gb, 256, 0, st>>>(w.ys, w.idx, cnt, d, xT);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ threshold
+// tau_r: a quantile of the plain morph's last-step length over training
+// samples.  The k-th smallest length is found exactly by a two-pass radix
+// select on the float bits (non-negative floats order like their bit
+// patterns; NaN lengths count as the largest): a histogram of the high 16 bits
+// locates the bin holding rank k, a histogram of the low 16 bits within that
+// bin the value.  Integer work only, so the result is reproducible.
+constexpr int kSelBins = 1 << 16;
+
+__global__ void k_step_length_keys(const float* __restrict__ steps, int64_t N, int d, uint32_t* __restrict__ keys,
+                                   uint32_t* __restrict__ hist) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float r2 = 0.0f;
+  for (int j = 0; j < d; ++j) {
+    const float v = steps[n * d + j];
+    r2 = fmaf(v, v, r2);
+  }
+  const float len = sqrtf(r2);
+  const uint32_t key = len == len ? __float_as_uint(len) : 0xffffffffu;
+  keys[n] = key;
+  atomicAdd(&hist[key >> 16], 1u);
+}
+
+__global__ void k_select_low_hist(const uint32_t* __restrict__ keys, int64_t N, const uint32_t* __restrict__ sel,
+                                  uint32_t* __restrict__ hist) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const uint32_t key = keys[n];
+  if ((key >> 16) == sel[0]) atomicAdd(&hist[key & 0xffffu], 1u);
+}
+
+// single block of 1024 threads: the bin of hist (kSelBins counts) holding rank
+// k (0-based; pass 0: k0, pass 1: sel[1]); sel[0] <- (pass 0) the bin, or
+// (pass 1) sel[0] << 16 | bin; sel[1] <- the rank within the bin
+__global__ void __launch_bounds__(1024) k_select_bin(uint32_t* __restrict__ hist, uint32_t* __restrict__ sel,
+                                                     int pass, uint32_t k0) {
+  __shared__ uint32_t sh[33];
+  constexpr int per = kSelBins / 1024;
+  const int base = threadIdx.x * per;
+  uint32_t local = 0;
+  for (int i = 0; i < per; ++i) local += hist[base + i];
+  // block exclusive scan of the per-thread totals
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = sh[lane];
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += v;
+    }
+    sh[lane] = wi - w;
+  }
+  __syncthreads();
+  const uint32_t before = inc - local + sh[warp];
+  const uint32_t k = pass == 0 ? k0 : sel[1];
+  __syncthreads();
+  if (k >= before && k < before + local) {
+    uint32_t c = before;
+    for (int i = 0; i < per; ++i) {
+      const uint32_t h = hist[base + i];
+      if (k < c + h) {
+        sel[0] = pass == 0 ? (uint32_t)(base + i) : ((sel[0] << 16) | (uint32_t)(base + i));
+        sel[1] = k - c;
+        break;
+      }
+      c += h;
+    }
+  }
+}
+
+struct ThrWs {
+  float *xprev, *traj, *steps;
+  uint32_t *keys, *hist, *sel;
+  void* fast;
+  size_t bytes;
+};
+
+static ThrWs thr_layout(void* ws, int d, int64_t M, int64_t N) {
+  ThrWs w;
+  char* p = (char*)ws;
+  auto take = [&](size_t b) { char* q = p; p += al(b); return q; };
+  w.xprev = (float*)take(sizeof(float) * N * d);
+  w.traj = (float*)take(sizeof(float) * 2 * N * d);
+  w.steps = (float*)take(sizeof(float) * N * d);
+  w.keys = (uint32_t*)take(sizeof(uint32_t) * N);
+  w.hist = (uint32_t*)take(sizeof(uint32_t) * kSelBins);
+  w.sel = (uint32_t*)take(sizeof(uint32_t) * 4);
+  w.fast = take(morph_rbf_fast_workspace(d, M, N));
+  w.bytes = (size_t)(p - (char*)ws);
+  return w;
+}
+
+size_t residual_threshold_workspace(int d, int64_t M, int64_t N) { return thr_layout(nullptr, d, M, N).bytes; }
+
+cudaError_t residual_threshold(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int64_t k,
+                               float* tau_r, float* xT, void* ws, cudaStream_t st) {
+  ThrWs w = thr_layout(ws, d, fa.M, N);
+  cudaError_t e;
+  if (T > 1) {
+    if ((e = morph_rbf_fast(d, fa, x0, N, T - 1, eta, w.xprev, nullptr, 0, nullptr, nullptr, w.fast, st))) return e;
+  } else if ((e = cudaMemcpyAsync(w.xprev, x0, sizeof(float) * N * d, cudaMemcpyDeviceToDevice, st))) {
+    return e;
+  }
+  // the last step, traced: traj[1] = x_T, steps[0] = its FP32 increment
+  if ((e = morph_rbf_fast(d, fa, w.xprev, N, 1, eta, nullptr, nullptr, 0, w.traj, w.steps, w.fast, st))) return e;
+  if (xT && (e = cudaMemcpyAsync(xT, w.traj + N * d, sizeof(float) * N * d, cudaMemcpyDeviceToDevice, st))) return e;
+  if ((e = cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * kSelBins, st))) return e;
+  const unsigned nb = (unsigned)((N + 255) / 256);
+  k_step_length_keys<<<nb, 256, 0, st>>>(w.steps, N, d, w.keys, w.hist);
+  k_select_bin<<<1, 1024, 0, st>>>(w.hist, w.sel, 0, (uint32_t)k);
+  if ((e = cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * kSelBins, st))) return e;
+  k_select_low_hist<<<nb, 256, 0, st>>>(w.keys, N, w.sel, w.hist);
+  k_select_bin<<<1, 1024, 0, st>>>(w.hist, w.sel, 1, 0u);
+  uint32_t bits = 0;
+  if ((e = cudaMemcpyAsync(&bits, w.sel, sizeof(uint32_t), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
+  memcpy(tau_r, &bits, sizeof(float));
   return cudaGetLastError();
 }
 

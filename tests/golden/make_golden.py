@@ -6,6 +6,7 @@ with 17 significant digits.  Each fixture's header names the passage of the
 paper the computation follows.  Run from the repository root:
 
     python tests/golden/make_golden.py
+    python tests/golden/make_golden.py --fit-rbf2d   # the fitted 2-D field (about 1.5 h on 8 cores)
 """
 import os
 import sys
@@ -21,7 +22,7 @@ import workloads as wl  # noqa: E402
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def write(name, header, params, arrays):
+def write(name, header, params, arrays, fmt="%.17g"):
     with open(os.path.join(HERE, name), "w") as f:
         for line in header:
             f.write(f"# {line}\n")
@@ -31,7 +32,38 @@ def write(name, header, params, arrays):
             a = np.asarray(a, dtype=np.float64)
             f.write(f"= {k} {' '.join(str(s) for s in a.shape)}\n")
             for row in a.reshape(a.shape[0], -1):
-                f.write(" ".join(f"{v:.17g}" for v in row) + "\n")
+                f.write(" ".join(fmt % v for v in row) + "\n")
+
+
+def fit_rbf2d(threads=None):
+    """The occupancy of the 2-D fitted workload (16,384 RBF centres U[0,10]^2,
+    gamma = 8, 200k points labelled by 64 boxes; workloads.config2, seed 2)
+    fitted by the oracle alone with the same settings the GPU fit uses
+    (lambda = 1e-4, 20 power iterations, 200 Nesterov iterations).  Its w
+    (rounded to float32, the precision both sides consume) and bias are the
+    field whose morph is benchmarked and parity-tested."""
+    if threads:
+        oracle.set_threads(threads)
+    wk = wl.config2(N=16)
+    l2, power_iters, iters = 1e-4, 20, 200
+    w, b, loss, alpha = oracle.fit(wk.field, wk.fit_X, wk.fit_y, l2, power_iters, iters)
+    w32, b32 = wl.f32(w), float(np.float32(b))
+    f32 = wk.field.with_weights(w32, bias=b32)
+    loss32, g, gb = oracle.fit_objective(f32, wk.fit_X, wk.fit_y, l2, w32, b32)
+    L, G = oracle.lipschitz(f32, wk.lo - 0.5, wk.hi + 0.5, cells=128)
+    write("fit_rbf2d_fitted.txt",
+          ["Sec. 3.1: the occupancy fitted to labelled points by binary cross entropy and gradient descent,",
+           "read as mean BCE + (l2/2)|w|^2 minimised from zero by Nesterov iterations with the step",
+           "1 / (lambda_hat / 4 + l2), lambda_hat from power iterations (the same algorithm as pdmp_fit_occupancy).",
+           "Field: workloads.config2 (seed 2): 16,384 RBF centres U[0,10]^2, gamma = 8, 200,000 points U[0,10]^2",
+           "labelled by 64 boxes.  w is the oracle's FP64 solution rounded to float32 (what both sides consume);",
+           "loss_f64 is the oracle's objective at the FP64 solution, loss_f32w at the rounded (w, bias);",
+           "L is the oracle's certified Lipschitz bound of grad c over [-0.5, 10.5]^2 (128 cells) for the rounded field.",
+           "Written by tests/golden/make_golden.py --fit-rbf2d from the FP64 oracle alone."],
+          {"l2": l2, "power_iters": power_iters, "iters": iters, "n_fit": int(wk.fit_X.shape[0]),
+           "M": int(wk.field.M), "bias": b32, "loss_f64": loss, "loss_f32w": loss32, "alpha": alpha,
+           "kkt_norm": float(np.sqrt(np.sum(np.asarray(g, np.float64) ** 2) + gb * gb)), "L": L, "G": G},
+          {"w": w32.reshape(-1, 8)}, fmt="%.9g")
 
 
 def main():
@@ -70,4 +102,8 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    if "--fit-rbf2d" in sys.argv:
+        fit_rbf2d(threads=int(sys.argv[sys.argv.index("--threads") + 1]) if "--threads" in sys.argv else None)
+        print("written")
+    else:
+        main()

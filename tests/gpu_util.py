@@ -35,3 +35,21 @@ def rff_eta_sampled(field, lo, hi, n=2000, safety=2.0, factor=0.5, seed=99):
 
 def max_abs(a, b):
     return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).max()) if np.size(a) else 0.0
+
+
+def per_step_check(field, traj, steps, eta):
+    """Every step's FP32 increment against the oracle's at the same state:
+    |step_gpu - step_ref|_inf <= 1e-5 eta sigma'(s) sum_m |w_m| |grad phi_m|
+    + 1e-5 |step_ref|_inf per sample, the oracle evaluated at the GPU's own
+    state x_t promoted to FP64.  Returns the worst error over its tolerance."""
+    T, N, d = steps.shape
+    worst = 0.0
+    for t in range(T):
+        xt = traj[t].astype(np.float64)
+        ev = oracle.evaluate(field, xt)
+        ref = -eta * ev["grad"]
+        tol = 1e-5 * eta * ev["scale"] + 1e-5 * np.abs(ref).max(axis=1)
+        err = np.abs(steps[t].astype(np.float64) - ref).max(axis=1)
+        assert np.all(err <= tol), f"step {t}: worst excess {np.max(err - tol):.3e}"
+        worst = max(worst, float(np.max(err / np.maximum(tol, 1e-300))))
+    return worst

@@ -43,6 +43,52 @@ def test_mlp_forward_matches_oracle():
     assert np.abs(y - ref).max() <= 2e-2 * np.abs(ref - x).max() + 1e-6
 
 
+def test_mlp_forward_fp32_activations_matches_oracle_to_1e4():
+    """The FP32-activation mode: the same kernel and fragment layouts, every
+    activation fed to the tensor cores as three BF16 pieces; the output equals
+    the FP64 oracle's on the same BF16 weights to 1e-4 normwise (and on every
+    sample to 1e-4 of the output's scale)."""
+    net = pdmp.Surrogate(LO, HI, [0.05, 0.07, 0.03], seed=3)
+    x = wl.uniform_box(13, 3, 1001, LO, HI)
+    y = net.forward(torch.from_numpy(x).cuda(), fp32_act=True).cpu().numpy()
+    _, bs = net.weights()
+    f = oracle.mlp_forward(net.bf16_weights(), [b.astype(np.float64) for b in bs], normalised(net, x))
+    pred = (y.astype(np.float64) - x) / np.asarray(net.out_scale)
+    assert np.linalg.norm(pred - f) <= 1e-4 * np.linalg.norm(f)
+    assert np.abs(pred - f).max() <= 1e-4 * np.abs(f).max()
+    yb = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    err_bf16 = np.linalg.norm((yb - x) / np.asarray(net.out_scale) - f)
+    assert err_bf16 > np.linalg.norm(pred - f)      # the BF16 activations are the coarser of the two
+
+
+@pytest.mark.parametrize("fp32_act,tol", [(True, 1e-4), (False, 2e-2)])
+@pytest.mark.parametrize("B", [1000, 4096])
+def test_mlp_gradient_every_layer_matches_oracle(fp32_act, tol, B):
+    """d loss / d(W_l, b_l) of every layer (the backward pass through each
+    layer, and the tensor-core weight-gradient contraction of each) against
+    the FP64 oracle on the same BF16 weights: 1e-4 relative per layer in the
+    FP32-activation mode, 2e-2 with the BF16 activations of training.  B = 1000
+    leaves a ragged last block of the weight-gradient kernel."""
+    net = pdmp.Surrogate(LO, HI, [0.05, 0.07, 0.03], seed=6)
+    x0 = wl.uniform_box(6, 3, B, LO, HI)
+    xT = (x0 + 0.05 * wl.rng(6, 9).standard_normal((B, 3))).astype(np.float32)
+    _, bs = net.weights()
+    target = (xT.astype(np.float64) - x0) / np.asarray(net.out_scale)
+    loss_ref, dW, db = oracle.mlp_loss_backward(net.bf16_weights(), [b.astype(np.float64) for b in bs],
+                                                normalised(net, x0), target)
+    loss, gW, gb = net.gradient(torch.from_numpy(x0).cuda(), torch.from_numpy(xT).cuda(), fp32_act=fp32_act)
+    assert abs(float(loss.item()) - loss_ref) <= tol * loss_ref
+    gW, gb = gW.cpu().numpy().astype(np.float64), gb.cpu().numpy().astype(np.float64)
+    ow = ob = 0
+    for layer, (rw, rb) in enumerate(zip(dW, db)):
+        w = gW[ow:ow + rw.size].reshape(rw.shape)
+        b = gb[ob:ob + rb.size]
+        ow += rw.size
+        ob += rb.size
+        assert np.linalg.norm(w - rw) <= tol * np.linalg.norm(rw), f"layer {layer} weights"
+        assert np.linalg.norm(b - rb) <= tol * np.linalg.norm(rb), f"layer {layer} biases"
+
+
 def test_mlp_train_step_gradient_matches_oracle():
     net = pdmp.Surrogate(LO, HI, [0.05, 0.07, 0.03], seed=4)
     B = 512
@@ -65,15 +111,16 @@ def test_mlp_train_step_gradient_matches_oracle():
 
 
 def _small_world(M=1024, N_train=1 << 15, T=20, seed=5):
-    wk = wl.config5(seed=seed, N=16, M=M, n_fit=20_000, n_train=N_train)
-    fld = pdmp.DeviceField.from_host(wk.field)
-    w, b, _, _ = pdmp.fit_occupancy(fld, torch.from_numpy(wk.fit_X).cuda(), torch.from_numpy(wk.fit_y).cuda(),
-                                    1e-4, 20, 150)
-    fitted = fld.with_weights(w, bias=b)
-    L, _ = pdmp.lipschitz_bound(fitted, LO - 0.5, HI + 0.5, cells=24)
-    eta = float(np.float32(0.5 / L))
-    fitted.lipschitz = L
-    return wk, fitted, eta, T
+    """A reduced 3-D world: config5's centres and boxes with M centres and
+    weights of a fitted occupancy's sign structure (from the seeded generators,
+    so that the oracle and the GPU take the same field); eta = 0.5 / L with L
+    the oracle's certified bound."""
+    wk = wl.config5(seed=seed, N=16, M=M, n_fit=16, n_train=N_train)
+    f = wk.field.with_weights(wl.proxy_fitted_weights(seed, wk.field.centres, wk.boxes), bias=-0.5)
+    wk.field = f
+    eta, L = rbf_eta(f, LO - 0.5, HI + 0.5, cells=24)
+    fld = pdmp.DeviceField.from_host(f, lipschitz=L)
+    return wk, fld, eta, T
 
 
 def test_surrogate_learns_the_displacement_and_beats_the_identity():
@@ -121,7 +168,7 @@ def test_surrogate_inference_fallback_is_the_plain_morph():
     # the oracle judges a few fallen-back samples
     idx = np.flatnonzero(fell)[:8]
     if idx.size:
-        ref = oracle.morph(wk.field.with_weights(fld.w.cpu().numpy(), bias=fld.bias), x0.cpu().numpy()[idx], T, eta)
+        ref = oracle.morph(wk.field, x0.cpu().numpy()[idx], T, eta)
         assert np.abs(o[idx] - ref).max() <= 1e-4
 
 
@@ -138,3 +185,76 @@ def test_save_and_load_round_trip(tmp_path):
     net.train_step(x0, xT)
     other.train_step(x0, xT)                 # Adam moments and step restored: the next step agrees
     assert torch.equal(net.W, other.W) and torch.equal(net.adam, other.adam)
+
+
+def test_residual_threshold_matches_oracle():
+    """tau_r (pdmp_residual_threshold): the nearest-rank q-quantile of the last
+    step's length over the training samples, against the oracle's from its own
+    FP64 chain.  A k-th order statistic moves by at most the largest change of
+    any one value; a length changes by at most eta L |dx| <= 0.5 sqrt(3) 1e-4
+    when x_{T-1} moves by the final-position tolerance 1e-4 per coordinate,
+    plus the per-step error of the increment (1e-5 of its scale), so the two
+    thresholds agree to 1e-4.  x_T equals the plain morph's, bit for bit."""
+    wk, fld, eta, T = _small_world(N_train=1 << 14)
+    x0 = wk.extra["x_train"]
+    xd = torch.from_numpy(x0).cuda()
+    taus = {q: pdmp.residual_threshold(fld, xd, T, eta, q) for q in (0.5, 0.99, 1.0)}
+    tau, xT = taus[0.99]
+    assert torch.equal(xT, pdmp.morph(fld, xd, T, eta))
+    xprev = oracle.morph(wk.field, x0, T - 1, eta)
+    lengths = np.linalg.norm(eta * oracle.evaluate(wk.field, xprev)["grad"], axis=1)
+    srt = np.sort(lengths)
+    n = len(srt)
+    for q, (t, _) in taus.items():
+        ref = srt[int(np.ceil(q * n)) - 1]
+        assert abs(t - ref) <= 1e-4, (q, t, ref)
+    assert taus[0.5][0] <= taus[0.99][0] <= taus[1.0][0]
+    assert srt[-1] > 10 * 1e-4                       # the tolerance is small against the lengths
+
+
+def test_surrogate_gains_over_the_plain_morph_at_equal_collision_rate():
+    """What the trained network gains over the method without it, at a
+    reduced size (3-D, M = 2048 centres, T = 40; 2^16 training pairs from the
+    plain morph; inference on 2^20 samples): the surrogate with its residual
+    check and plain-morph fallback is several times faster than the plain
+    morph, and its ground-truth collision rate (samples inside an obstacle box)
+    is at most the plain morph's + 0.1 percentage points."""
+    wk, fld, eta, _ = _small_world(M=2048, N_train=1 << 16)
+    T = 40
+    xtr = torch.from_numpy(wk.extra["x_train"]).cuda()
+    tau_r, xTtr = pdmp.residual_threshold(fld, xtr, T, eta, 0.99)
+    net = pdmp.Surrogate(LO, HI, pdmp.displacement_rms(xtr, xTtr).cpu().numpy(), seed=5)
+    B, steps = 4096, 800
+    for s in range(steps):
+        lr = 2e-3 * 0.5 * (1.0 + np.cos(np.pi * s / steps)) + 1e-5
+        i = (s * B) % (xtr.shape[0] - B)
+        net.train_step(xtr[i:i + B], xTtr[i:i + B], lr=lr)
+    x0 = torch.from_numpy(wl.uniform_box(55, 3, 1 << 20, LO, HI)).cuda()
+    boxes = torch.from_numpy(wk.boxes).cuda()
+    ws = torch.empty(pdmp.morph_workspace(fld, x0.shape[0]), dtype=torch.uint8, device="cuda")
+    plain = torch.empty_like(x0)
+    sur = torch.empty_like(x0)
+    run_plain = lambda: pdmp.morph(fld, x0, T, eta, out=plain, ws=ws)
+    res = {}
+
+    def run_sur():
+        res["nf"] = net.infer(fld, x0, T, eta, tau_r, out=sur)[1]
+
+    def best(fn, reps=3):
+        fn()
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        return min(times)
+    t_plain, t_sur = best(run_plain), best(run_sur)
+    col = lambda x: float(pdmp.box_labels(boxes, x).float().mean().item())
+    c_prior, c_plain, c_sur = col(x0), col(plain), col(sur)
+    assert c_plain < c_prior                            # the morph moves samples out of the obstacles
+    assert c_sur <= c_plain + 1e-3, (c_sur, c_plain)
+    assert res["nf"] < 0.1 * x0.shape[0]
+    assert t_plain / t_sur >= 4.0, (t_plain, t_sur)

@@ -46,9 +46,15 @@ def test_noalloc_matches_workspace_morph_on_two_calls(d):
     eta = float(np.float32(0.5 / L))
     fld = pdmp.DeviceField.from_host(f)
     xs = [torch.from_numpy(wl.uniform_box(200 + i, 3, N, lo, hi)).cuda() for i in range(2)]
-    for x in xs:                                    # two calls in a row, different inputs
+    for i, x in enumerate(xs):                      # two calls in a row, different inputs
         out = torch.full_like(x, float("nan"))
+        torch.cuda.synchronize()
+        free0, allocs0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_stats().get("allocation.all.allocated", 0)
         assert _call(fld, x, T, eta, out) == 0
+        torch.cuda.synchronize()
+        if i:                                       # the first call may load the module; the second allocates nothing
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
         ref = pdmp.morph(fld, x, T, eta, fast=True)
         torch.cuda.synchronize()
         assert pdmp.stream_status()[0] == 0

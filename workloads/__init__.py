@@ -26,6 +26,7 @@ Sec. 4) are not available; these stand in for them:
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field as dc_field
 
 import numpy as np
@@ -134,6 +135,45 @@ def config2(seed: int = 2, N: int = 1 << 20, M: int = 16384, n_fit: int = 200_00
     fld = Field(RBF, centres, np.zeros(M, np.float32), gamma=8.0)
     x0 = uniform_box(seed, S_SAMPLES, N, lo, hi)
     return Workload(f"rbf2d-fitted-M{M}-N{N}-T50", fld, x0, 50, lo, hi, boxes, X, y)
+
+
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
+FITTED_RBF2D = "fit_rbf2d_fitted.txt"
+
+
+def read_fixture(path: str):
+    """(params, arrays) of a text fixture: '#' header lines, '@ name value'
+    numbers and '= name shape...' arrays followed by rows of numbers."""
+    params, arrays, cur = {}, {}, None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            if line.startswith("@ "):
+                _, k, v = line.rstrip("\n").split(" ", 2)
+                params[k] = int(v) if v.lstrip("-").isdigit() else float(v)
+            elif line.startswith("= "):
+                parts = line.split()
+                cur = [parts[1], tuple(int(x) for x in parts[2:]), []]
+                arrays[cur[0]] = cur
+            else:
+                cur[2].extend(float(v) for v in line.split())
+    return params, {k: np.array(v[2], dtype=np.float64).reshape(v[1]) for k, v in arrays.items()}
+
+
+def config2_fitted(seed: int = 2, N: int = 1 << 20):
+    """config2 with the occupancy weights and bias stored in
+    tests/golden/fit_rbf2d_fitted.txt (the oracle's fit of this workload,
+    rounded to float32), and that file's parameters (its certified bound L
+    among them).  Raises if the fixture is missing."""
+    if seed != 2:
+        raise ValueError("the stored fit is of the seed-2 workload")
+    params, arrays = read_fixture(os.path.join(GOLDEN_DIR, FITTED_RBF2D))
+    wk = config2(seed=seed, N=N)
+    if int(params["M"]) != wk.field.M:
+        raise ValueError("the stored fit has another number of centres")
+    wk.field = wk.field.with_weights(f32(arrays["w"].ravel()), bias=params["bias"])
+    return wk, params
 
 
 def proxy_fitted_weights(seed: int, centres: np.ndarray, boxes: np.ndarray, scale: float = 0.5) -> np.ndarray:
