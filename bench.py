@@ -42,6 +42,8 @@ LAUNCHES_PER_MORPH = 9
 FP32_LANES_PER_SM = 128           # FP32 pipe width per SM per clock
 MUFU_EX2_PER_SM = 32              # measured ex2 throughput per SM per clock on GB300
 MUFU_SINCOS_PER_SM = 15.6         # measured sin (or cos) throughput per SM per clock on GB300
+MMA_TF32_PER_SM = 480.0           # measured mma.sync TF32 multiply-adds per SM per clock on GB300
+MLP_MACS_PER_SAMPLE = 39 * 128 + 2 * 128 * 128 + 128 * 3   # the surrogate network's multiply-adds per sample
 KERNEL_SOURCES = ["paper_2108_11775_gb300/csrc/morph_rbf_fast.cu", "paper_2108_11775_gb300/csrc/fast_tile.cuh",
                   "paper_2108_11775_gb300/csrc/sort.cu", "paper_2108_11775_gb300/csrc/common.cuh"]
 
@@ -482,10 +484,18 @@ def extra_tanh_net(pdmp, torch, n_sms, pk, d=2, H=64, n=1 << 20, t_steps=50):
     t = _time(torch, run, reps=5)
     macs = 2 * H * H + 2 * d * H + 2 * H          # W2 h1 and W2^T v2; W1 x and W1^T g1; w3 h2 and w3 (.) (1 - h2^2)
     rate = n * t_steps / t
-    peak = n_sms * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 * FP32_LANES_PER_SM / macs
+    clk = n_sms * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    # binding bound: the two H x H products on the tensor cores as TF32 MMAs with
+    # hi/lo splits (3 products each) at 480 multiply-adds per SM per clock; the rest
+    # (2dH + 2H FP32 multiply-adds, 2H tanh) fits beside it
+    tc_clk = 3 * 2 * H * H / MMA_TF32_PER_SM
+    alu_clk = (2 * d * H + 2 * H) / FP32_LANES_PER_SM + 2 * H / MUFU_EX2_PER_SM
+    peak = clk / max(tc_clk, alu_clk)
     return {"value": rate, "unit": "sample-steps/s", "ms": 1e3 * t, "N": n, "T": t_steps, "d": d, "H": H,
-            "macs_per_sample_step": macs, "roofline_frac": rate / peak, "L": L, "eta": eta,
-            "note": "FP32 multiply-adds at 128 lanes per SM per clock; tanh not counted"}
+            "macs_per_sample_step": macs, "roofline_frac": rate / peak, "roofline_bound": "tensor (mma.sync TF32)",
+            "fp32_count_frac": rate / (clk * FP32_LANES_PER_SM / macs), "L": L, "eta": eta,
+            "note": "roofline_frac against the tensor pipe (3 TF32 products per H x H multiply-add); "
+                    "fp32_count_frac against every multiply-add on the FP32 lanes"}
 
 
 def extra_vjp_rbf2d(pdmp, torch, fld, x0, eta, n_sms, pk, k=5):
@@ -540,28 +550,39 @@ def extra_rff(pdmp, torch, n_sms, pk):
     work = float(N) * T * M
     d = 7
     clk = n_sms * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
-    # FP32 / MUFU rooflines per feature (128 FP32 lanes, 15.6 sin or cos per SM per clock):
-    # forward 2d+2 FP32 + 2 MUFU; VJP pass 4d+3 FP32 + 2 MUFU; log-det 2d+2 + d(d+1)/2 FP32 + 2 MUFU.
-    # The forward and the VJP put their contractions on the tensor cores, so their FP32 counts no
-    # longer bind: the sin and cos of every feature (2 MUFU per feature and pass) do.
-    mufu = MUFU_SINCOS_PER_SM / 2.0
-    peaks = {"forward": clk * min(FP32_LANES_PER_SM / (2 * d + 2), mufu),
-             "vjp_per_pass": clk * min(FP32_LANES_PER_SM / (4 * d + 3), mufu),
-             "logdet": clk * min(FP32_LANES_PER_SM / (2 * d + 2 + d * (d + 1) // 2), mufu)}
+    # Binding bounds per feature and sample, per SM and clock.  MUFU: sin and
+    # cos (15.6 each per SM per clock, measured), 2 per feature in every pass.
+    # Tensor pipe: mma.sync m16n8k8 TF32 at 480 multiply-adds per SM per clock
+    # (measured); a 16 x 8 tile of one MMA is 1024 multiply-adds over 128
+    # feature-samples.  Forward / VJP recompute: theta and grad s, 3 + 3 MMAs
+    # (48 per feature-sample); VJP Hessian-vector pass: 12 MMAs (96); log-det:
+    # 18 MMAs (144).  The pass's bound is the slower of the two.
+    mufu_fs = MUFU_SINCOS_PER_SM / 2.0
+    tc = lambda n_mma: MMA_TF32_PER_SM / (n_mma * 1024.0 / 128.0)
+    bounds = {"forward": min(mufu_fs, tc(6)), "vjp_recompute": min(mufu_fs, tc(6)), "vjp_hvp": min(mufu_fs, tc(12)),
+              "logdet": min(mufu_fs, tc(18))}
+    names = {k: ("mufu" if bounds[k] == mufu_fs else "tensor") for k in bounds}
+    # the VJP's two passes each sweep N T M: its bound is the sum of the passes' times
+    t_bound = {"forward": work / (clk * bounds["forward"]),
+               "vjp": work / (clk * bounds["vjp_recompute"]) + work / (clk * bounds["vjp_hvp"]),
+               "logdet": work / (clk * bounds["logdet"])}
+    t_meas = {"forward": t_fwd, "vjp": t_vjp, "logdet": t_ld}
     rates = {"forward": work / t_fwd, "vjp_per_pass": 2 * work / t_vjp, "logdet": work / t_ld,
              "vjp_param_grad_per_pass": 3 * work / t_pg}
-    peaks["vjp_param_grad_per_pass"] = peaks["vjp_per_pass"]
     return {**rates, "unit": "feature-evals/s",
-            "roofline_frac": {k: rates[k] / peaks[k] for k in rates}, "roofline_peak": peaks,
-            "mufu_frac": {k: rates[k] / (clk * mufu) for k in rates}, "mufu_peak": clk * mufu,
+            "roofline_frac": {k: t_bound[k] / t_meas[k] for k in t_bound},
+            "roofline_bound": {"forward": names["forward"], "vjp": f"{names['vjp_recompute']} + {names['vjp_hvp']}",
+                               "logdet": names["logdet"]},
+            "roofline_peak_per_sm_clk": bounds,
+            "mufu_frac": {k: rates[k] / (clk * mufu_fs) for k in rates}, "mufu_peak": clk * mufu_fs,
             "ms": {"forward": 1e3 * t_fwd, "vjp": 1e3 * t_vjp, "vjp_param_grad": 1e3 * t_pg, "logdet": 1e3 * t_ld,
                    "inverse": 1e3 * t_inv},
             "inverse": {"value": float(wk_inv.item()) / t_inv, "unit": "feature-evals/s performed",
                         "mean_iterations_per_step": float(wk_inv.item()) / work, "round_trip_max_abs": inv_rt},
-            "note": "VJP counts its recompute pass and its Hessian-vector pass (2 N T M), with the parameter "
-                    "gradient also its weight pass (3 N T M); roofline_frac uses the "
-                    "FP32-operation count of each pass (above 1 where the tensor cores take that work), "
-                    "mufu_frac the sin/cos bound every pass shares"}
+            "note": "roofline_frac = the bound's time / the measured time, with each pass bound by the slower of "
+                    "MUFU sin+cos and the mma.sync TF32 tensor pipe (feature-samples per SM per clock in "
+                    "roofline_peak_per_sm_clk); the VJP counts its recompute and Hessian-vector passes "
+                    "(2 N T M), with the parameter gradient also its weight pass (3 N T M)"}
 
 
 def extra_surrogate(pdmp, torch, args):
@@ -578,21 +599,24 @@ def extra_surrogate(pdmp, torch, args):
     eta = float(np.float32(0.5 / L))
     T = wk.T
     xtr = torch.from_numpy(wk.extra["x_train"]).cuda()
-    x_prev = pdmp.morph(f, xtr, T - 1, eta)
-    xTtr = pdmp.morph(f, x_prev, 1, eta)
-    last = (xTtr - x_prev).norm(dim=1).cpu().numpy()
-    tau_r = float(np.quantile(last, 0.99))
+    tau_r, xTtr = pdmp.residual_threshold(f, xtr, T, eta, 0.99)
     scale = pdmp.displacement_rms(xtr, xTtr).cpu().numpy()
     net = pdmp.Surrogate(wk.lo, wk.hi, scale, seed=5)
     B, steps = 4096, args.surrogate_steps
     loss = torch.zeros(1, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
+    ev0.record(stream)
     for s in range(steps):
         lr = 2e-3 * 0.5 * (1.0 + np.cos(np.pi * s / steps)) + 1e-5
         i = (s * B) % (xtr.shape[0] - B)
         net.train_step(xtr[i:i + B], xTtr[i:i + B], lr=lr, loss=loss if s == steps - 1 else None)
+    ev1.record(stream)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    train_step_ms = ev0.elapsed_time(ev1) / steps
     x0 = torch.from_numpy(wk.x0).cuda()
     boxes = torch.from_numpy(wk.boxes).cuda()
     plain = torch.empty_like(x0)
@@ -607,7 +631,26 @@ def extra_surrogate(pdmp, torch, args):
     t_sur = _time(torch, run_sur, reps=2)
     col = lambda x: float(pdmp.box_labels(boxes, x).float().mean().item())
     c_prior, c_plain, c_sur = col(x0), col(plain), col(sur)
+    # the network alone (inference kernel) on the N samples
+    pred = torch.empty_like(x0)
+    t_net = _time(torch, lambda: net.forward(x0, out=pred), reps=3)
+    n_inf = float(x0.shape[0])
+    macs = MLP_MACS_PER_SAMPLE
+    clk = torch.cuda.get_device_properties(0).multi_processor_count * float(
+        peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6
+    bf16_peak = float(peaks()[0].get("bf16_tflops", 1908.7)) * 1e12
+    # the network's non-tensor work per sample: 384 SiLU (an ex2 and a reciprocal each
+    # on the special-function unit) and 36 sin / cos of the encoding
+    mufu_peak_samples = clk * MUFU_EX2_PER_SM / (2 * 384 + 36)
+    mlp = {"samples_per_s": n_inf / t_net, "ms": 1e3 * t_net, "macs_per_sample": macs,
+           "tflops": 2.0 * macs * n_inf / t_net / 1e12,
+           "frac_of_bf16_peak": 2.0 * macs * n_inf / t_net / bf16_peak,
+           "frac_of_mufu_bound": n_inf / t_net / mufu_peak_samples,
+           "train_step_ms": train_step_ms, "train_batch": B,
+           "note": "bf16 peak: MEASURED_PEAKS.json bf16_tflops (cuBLAS, burst); MUFU bound: the SiLU and "
+                   "encoding's special-function operations per sample at 32 per SM per clock"}
     return {"speedup_vs_plain_morph": t_plain / t_sur, "ms_plain": 1e3 * t_plain, "ms_surrogate": 1e3 * t_sur,
+            "mlp": mlp,
             "fallback_fraction": res["nf"] / x0.shape[0], "collision_rate": {"prior": c_prior, "plain_morph": c_plain,
                                                                              "surrogate": c_sur},
             "equal_collision_rate": c_sur <= c_plain + 1e-3, "tau_r": tau_r, "train_steps": steps,

@@ -60,6 +60,7 @@ typedef int32_t pdmp_status;
 #define PDMP_FLAG_FIT_NONFINITE       2  /* fit: the loss became NaN or infinite */
 #define PDMP_FLAG_NOT_CONVERGED       4  /* inverse: a block stopped at maxit iterations */
 #define PDMP_FLAG_STAGE_TIMEOUT       8  /* a bounded wait for a shared-memory stage copy gave up (results invalid) */
+#define PDMP_FLAG_MMA_TIMEOUT        16  /* a bounded wait for a tensor-core (tcgen05) MMA gave up (results invalid) */
 
 #define PDMP_KIND_RBF 0
 #define PDMP_KIND_RFF 1

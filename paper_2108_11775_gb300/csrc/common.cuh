@@ -19,6 +19,7 @@ enum : int32_t {
   FLAG_FIT_NONFINITE = PDMP_FLAG_FIT_NONFINITE,
   FLAG_NOT_CONVERGED = PDMP_FLAG_NOT_CONVERGED,
   FLAG_STAGE_TIMEOUT = PDMP_FLAG_STAGE_TIMEOUT,
+  FLAG_MMA_TIMEOUT = PDMP_FLAG_MMA_TIMEOUT,
 };
 extern __device__ int32_t g_device_flag;
 

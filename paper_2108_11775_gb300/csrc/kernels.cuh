@@ -119,6 +119,8 @@ cudaError_t batch_run(const pdmp_batch_plan* plan, void* ws, cudaStream_t st);
 constexpr int64_t kMlpNW = 39 * 128 + 2 * 128 * 128 + 3 * 128;  // weights W1 (over the 39-wide encoding), W2, W3, W4
 constexpr int64_t kMlpNB = 3 * 128 + 3;                         // biases b1, b2, b3, b4
 cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, bool fp32_act, cudaStream_t st);
+cudaError_t mlp_forward_tc05(const pdmp_mlp* net, const float* x0, int64_t N, float* y, bool fp32_act,
+                             cudaStream_t st);
 size_t mlp_train_workspace(int B);
 cudaError_t mlp_gradient(const pdmp_mlp* net, const float* x0, const float* xT, int B, bool fp32_act, float* loss,
                          float* gW, float* gb, void* ws, cudaStream_t st);

@@ -6,11 +6,12 @@
 // (without it the displacement field, sharp near obstacle boundaries, is out
 // of reach of a small SiLU network).  BF16 weights, FP32 accumulation.
 //
-// The two 128 x 128 layers and the output layer run on the tensor cores
-// (mma.sync m16n8k16, BF16 x BF16 -> FP32): a warp owns 16 samples, and the
-// accumulator fragments of one layer, after bias + SiLU and rounding to BF16,
-// are exactly the A fragments of the next layer, so activations never leave
-// registers.  The 3 -> 128 input layer is FP32 on the CUDA cores.
+// Inference runs on the fifth-generation tensor cores (mlp_tc05.cu).  The
+// training kernels here use warp-level MMAs (mma.sync m16n8k16, BF16 x BF16 ->
+// FP32) over the batch: a warp owns 16 samples, and the accumulator fragments
+// of one layer, after bias + SiLU and rounding to BF16, are exactly the A
+// fragments of the next layer, so activations never leave registers.  The
+// 39 -> 128 input layer is FP32 on the CUDA cores.
 //
 // Training: forward with saved pre-activations, backward through the same
 // fragment layouts (dA = dZ W on the tensor cores with transposed weight
@@ -30,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
+#include "mlp_common.cuh"
 
 namespace pdmp {
 
@@ -202,28 +204,15 @@ __device__ __forceinline__ void dense_out(const float (&v)[16][4], const uint32_
   }
 }
 
-// Fourier encoding of a normalised input.  sin(2^k pi u) = sin(2 pi tau)
-// with tau = 2^(k-1) u, which is exact in FP32 (a power of two times u), and
-// so is its distance r = tau - rint(tau) to the nearest integer: the angle
-// 2 pi r in [-pi, pi] is the only rounded step.  The training and inference
-// kernels take sin / cos on the special-function unit; the FP32-activation
-// mode takes CUDA's sinf / cosf.
+// the Fourier encoding of x's normalised coordinates (mlp_common.cuh); the
+// training kernels take sin / cos on the special-function unit, the
+// FP32-activation mode CUDA's sinf / cosf
 template <bool EXACT>
-__device__ __forceinline__ void encode(const float* u, float* e) {
+__device__ __forceinline__ void encode(const MlpArgs& a, const float* x, float* e) {
+  MlpEncIn in;
+  mlp_enc_prepare(x, a.lo, a.in_scale, in);
 #pragma unroll
-  for (int j = 0; j < 3; ++j) e[j] = u[j];
-  float h = 0.5f;
-#pragma unroll
-  for (int k = 0; k < kFreq; ++k) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const float tau = h * u[j];
-      const float th = 6.28318530717958648f * (tau - rintf(tau));
-      e[3 + 6 * k + j] = EXACT ? sinf(th) : sin_approx(th);
-      e[3 + 6 * k + 3 + j] = EXACT ? cosf(th) : cos_approx(th);
-    }
-    h *= 2.0f;
-  }
+  for (int f = 0; f < kEnc; ++f) e[f] = mlp_enc_feature<EXACT>(f, in);
 }
 
 // input layer (FP32): acc[j] = W1 enc for rows g, g + 8 of the warp's tile
@@ -249,57 +238,6 @@ __device__ __forceinline__ void input_layer(const MlpSmem* s, const float* e0, c
   }
 }
 
-__device__ __forceinline__ void normalise(const MlpArgs& a, const float* x, float* u) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) u[i] = fmaf(x[i] - a.lo[i], a.in_scale[i], -1.0f);
-}
-
-// ---------------------------------------------------------------- inference
-// y[n] = x0[n] + out_scale * f(u(x0[n]))  (the predicted x_T)
-template <bool EXACT>
-__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpArgs a, const float* __restrict__ x0, int64_t N,
-                                                                 float* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MlpSmem* s = reinterpret_cast<MlpSmem*>(smem_raw);
-  load_weights(a, s, false);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const int64_t tiles = (N + 15) / 16;
-  for (int64_t tile = (int64_t)blockIdx.x * kMlpWarps + warp; tile < tiles; tile += (int64_t)gridDim.x * kMlpWarps) {
-    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-    float x_0[3] = {0, 0, 0}, x_1[3] = {0, 0, 0}, u0[3], u1[3];
-    if (r0 < N)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) x_0[i] = x0[r0 * 3 + i];
-    if (r1 < N)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) x_1[i] = x0[r1 * 3 + i];
-    normalise(a, x_0, u0);
-    normalise(a, x_1, u1);
-    float e0[kEnc], e1[kEnc];
-    encode<EXACT>(u0, e0);
-    encode<EXACT>(u1, e1);
-    float acc[16][4];
-    input_layer(s, e0, e1, t, acc);
-    bias_silu(acc, s->b1, t);
-    dense_128<EXACT>(acc, s->W2, g, t);
-    bias_silu(acc, s->b2, t);
-    dense_128<EXACT>(acc, s->W3, g, t);
-    bias_silu(acc, s->b3, t);
-    float o[4];
-    dense_out<EXACT>(acc, s->W4, g, t, o);
-    // lane (g, t) holds columns 2t, 2t + 1 of rows g and g + 8; outputs are columns 0..2
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int c = 2 * t + q;
-      if (c < 3) {
-        if (r0 < N) y[r0 * 3 + c] = fmaf(o[q] + s->b4[c], a.out_scale[c], x_0[c]);
-        if (r1 < N) y[r1 * 3 + c] = fmaf(o[2 + q] + s->b4[c], a.out_scale[c], x_1[c]);
-      }
-    }
-  }
-}
-
 // ---------------------------------------------------------------- training
 // Forward over a batch, saving z1..z3 (B x 128 each, FP32), the normalised
 // input u (B x 3) and dY = d loss / d output (B x 3) for the MSE loss against
@@ -321,18 +259,16 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train_forward(MlpArgs a,
   const float inv = 2.0f / (3.0f * (float)B);
   for (int tile = blockIdx.x * kMlpWarps + warp; tile < tiles; tile += gridDim.x * kMlpWarps) {
     const int r0 = tile * 16 + g, r1 = r0 + 8;
-    float x_0[3] = {0, 0, 0}, x_1[3] = {0, 0, 0}, u0[3], u1[3];
+    float x_0[3] = {0, 0, 0}, x_1[3] = {0, 0, 0};
     if (r0 < B)
 #pragma unroll
       for (int i = 0; i < 3; ++i) x_0[i] = x0[r0 * 3 + i];
     if (r1 < B)
 #pragma unroll
       for (int i = 0; i < 3; ++i) x_1[i] = x0[r1 * 3 + i];
-    normalise(a, x_0, u0);
-    normalise(a, x_1, u1);
     float e0[kEnc], e1[kEnc];
-    encode<EXACT>(u0, e0);
-    encode<EXACT>(u1, e1);
+    encode<EXACT>(a, x_0, e0);
+    encode<EXACT>(a, x_1, e1);
     if (t == 0) {
       if (r0 < B)
 #pragma unroll
@@ -679,19 +615,9 @@ cudaError_t mlp_refresh(const pdmp_mlp* net, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <bool EXACT>
-static cudaError_t launch_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, cudaStream_t st) {
-  const size_t smem = sizeof(MlpSmem);
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_forward<EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int grid = mlp_grid((N + 15) / 16, (const void*)k_mlp_forward<EXACT>);
-  k_mlp_forward<EXACT><<<grid, 32 * kMlpWarps, smem, st>>>(mlp_args(net), x0, N, y);
-  return cudaGetLastError();
-}
-
 cudaError_t mlp_forward(const pdmp_mlp* net, const float* x0, int64_t N, float* y, bool fp32_act, cudaStream_t st) {
   if (N == 0) return cudaSuccess;
-  return fp32_act ? launch_forward<true>(net, x0, N, y, st) : launch_forward<false>(net, x0, N, y, st);
+  return mlp_forward_tc05(net, x0, N, y, fp32_act, st);
 }
 
 static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }

@@ -1,0 +1,167 @@
+// Fifth-generation tensor cores (tcgen05) on sm_103a: descriptors, tensor
+// memory (TMEM) and the instructions the tcgen05 kernels use, as inline PTX.
+//
+// Operands.  A (M x K) and B (N x K) sit in shared memory in the canonical
+// K-major layout without swizzle: "core matrices" of 8 rows x 16 bytes, each
+// stored as 128 contiguous bytes (row r at byte 16 r).  Row group g (rows
+// 8g .. 8g + 7) and K chunk c (16 bytes of K) start at
+//   base + g * SBO + c * LBO,
+// with LBO the byte distance between core matrices adjacent in K and SBO the
+// distance between adjacent row groups.  These kernels keep all K chunks of a
+// row group together: LBO = 128, SBO = 128 * (K chunks of the whole operand),
+// and one instruction's K slice starts at base + slice * (K bytes per slice /
+// 16) * 128.
+//
+// Accumulator.  For M = 128 (one CTA), row i of D is TMEM lane i and column j
+// TMEM column (base column + j), 32 bits each.  Warp w may access lanes
+// 32 (w % 4) .. 32 (w % 4) + 31 only.
+//
+// Descriptor layouts (PTX ISA, tcgen05 "Instruction descriptor" and "Shared
+// memory descriptor"); both are built by constexpr functions that a CPU test
+// checks field by field.
+#pragma once
+
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define PDMP_TC05_HD __host__ __device__
+#else
+#define PDMP_TC05_HD
+#endif
+
+namespace pdmp {
+namespace tc05 {
+
+// instruction descriptor, kind::f16 / kind::tf32, dense:
+//   [4,6) D format (1 = F32)   [7,10) A format   [10,13) B format
+//   (kind::f16: 0 = F16, 1 = BF16; kind::tf32: 2 = TF32)
+//   [13] negate A  [14] negate B  [15] A major  [16] B major (0 = K-major)
+//   [17,23) N >> 3   [24,29) M >> 4
+enum Format : uint32_t { kF16 = 0, kBF16 = 1, kTF32 = 2 };
+
+PDMP_TC05_HD constexpr uint32_t idesc(uint32_t a_fmt, uint32_t b_fmt, int M, int N) {
+  return (1u << 4)                                  // D: F32
+         | (a_fmt << 7) | (b_fmt << 10)            // A, B formats
+         | (0u << 15) | (0u << 16)                 // both K-major
+         | ((uint32_t)(N >> 3) << 17)              // N / 8
+         | ((uint32_t)(M >> 4) << 24);             // M / 16
+}
+
+// shared-memory descriptor, no swizzle:
+//   [0,14) start address >> 4   [16,30) LBO >> 4   [32,46) SBO >> 4
+//   [46,48) version = 1         [49,52) base offset = 0   [52] LBO mode = 0
+//   [61,64) swizzle = 0 (none)
+PDMP_TC05_HD constexpr uint64_t sdesc(uint32_t smem_addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((smem_addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// byte offset of element (row, k) of a K-major operand with kchunks K chunks of
+// 16 bytes a row group (esize bytes an element)
+PDMP_TC05_HD constexpr uint32_t kmajor_offset(int row, int k, int kchunks, int esize) {
+  return (uint32_t)((row >> 3) * (kchunks * 128) + ((k * esize) >> 4) * 128 + (row & 7) * 16 + ((k * esize) & 15));
+}
+
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// TMEM allocation (one whole warp); the address goes to *dst (shared memory)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the tensor core's reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// D (TMEM) = (accumulate ? D : 0) + A B^T, A and B from shared memory
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc_, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc_), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_ss_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc_,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc_), "r"(accumulate)
+      : "memory");
+}
+
+// the MMAs this thread issued so far arrive on the mbarrier when complete
+__device__ __forceinline__ void commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+
+// waits for the completion of phase `parity` of the mbarrier for at most
+// `limit` clocks; false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long limit) {
+  const uint32_t a = smem_u32(mbar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane (two loads of 16),
+// waited for in the same statement so that no use of the values can be
+// scheduled before they arrive
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%33];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr), "r"(taddr + 16u)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 columns, waited for in the same statement
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+#endif  // __CUDACC__
+
+}  // namespace tc05
+}  // namespace pdmp

@@ -25,9 +25,22 @@ LO, HI = np.zeros(3), np.full(3, 5.0)
 
 
 def normalised(net, x):
-    """The network's input: the oracle's Fourier encoding of the normalised coordinates."""
-    u = (np.asarray(x, np.float64) - np.asarray(net.lo)) * np.asarray(net.in_scale) - 1.0
+    """The network's input: the oracle's Fourier encoding of the normalised
+    coordinates u = (x - lo) s - 1, in FP64 with the network's own float32
+    lo and s (pdmp_mlp carries them as float)."""
+    lo = np.asarray(net.lo, np.float32).astype(np.float64)
+    sc = np.asarray(net.in_scale, np.float32).astype(np.float64)
+    u = (np.asarray(x, np.float64) - lo) * sc - 1.0
     return oracle.mlp_encode(u, 6)
+
+
+def fp32_output_excess(net, x, y, f):
+    """|y - (x + out_scale f)| beyond one unit in the last place of the
+    float32 output y = x_T_hat (the interface returns x_0 + displacement in
+    float32, whose rounding alone is about 5e-4 of a 5e-4 displacement)."""
+    ref = np.asarray(x, np.float64) + f * np.asarray(net.out_scale)
+    ulp = np.spacing(np.abs(np.asarray(y, np.float32))).astype(np.float64)
+    return np.maximum(np.abs(np.asarray(y, np.float64) - ref) - ulp, 0.0)
 
 
 def test_mlp_forward_matches_oracle():
@@ -53,12 +66,32 @@ def test_mlp_forward_fp32_activations_matches_oracle_to_1e4():
     y = net.forward(torch.from_numpy(x).cuda(), fp32_act=True).cpu().numpy()
     _, bs = net.weights()
     f = oracle.mlp_forward(net.bf16_weights(), [b.astype(np.float64) for b in bs], normalised(net, x))
-    pred = (y.astype(np.float64) - x) / np.asarray(net.out_scale)
-    assert np.linalg.norm(pred - f) <= 1e-4 * np.linalg.norm(f)
-    assert np.abs(pred - f).max() <= 1e-4 * np.abs(f).max()
+    excess = fp32_output_excess(net, x, y, f)
+    disp = f * np.asarray(net.out_scale)
+    assert np.linalg.norm(excess) <= 1e-4 * np.linalg.norm(disp)
+    assert excess.max() <= 1e-4 * np.abs(disp).max()
     yb = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
-    err_bf16 = np.linalg.norm((yb - x) / np.asarray(net.out_scale) - f)
-    assert err_bf16 > np.linalg.norm(pred - f)      # the BF16 activations are the coarser of the two
+    assert np.linalg.norm(fp32_output_excess(net, x, yb, f)) > np.linalg.norm(excess)   # BF16 activations: coarser
+
+
+@pytest.mark.parametrize("N", [1, 127, 129, 256 * 152 * 3 + 77])
+def test_mlp_forward_ragged_and_many_tiles(N):
+    """The tensor-core inference kernel over ragged sample counts (a partial
+    128-sample tile, a partial pair of tiles) and over more tile pairs than
+    CTAs (each CTA loops): sampled rows against the oracle in both modes, and
+    every output finite."""
+    net = pdmp.Surrogate(LO, HI, [0.05, 0.07, 0.03], seed=8)
+    x = wl.uniform_box(18, 3, N, LO, HI)
+    xd = torch.from_numpy(x).cuda()
+    idx = np.unique(np.concatenate([wl.rng(18, 1).choice(N, min(N, 300), replace=False), [0, N - 1]]))
+    _, bs = net.weights()
+    f = oracle.mlp_forward(net.bf16_weights(), [b.astype(np.float64) for b in bs], normalised(net, x[idx]))
+    for fp32_act, tol in ((False, 2e-2), (True, 1e-4)):
+        y = net.forward(xd, fp32_act=fp32_act).cpu().numpy()
+        assert np.isfinite(y).all()
+        excess = fp32_output_excess(net, x[idx], y[idx], f)
+        assert np.linalg.norm(excess) <= tol * np.linalg.norm(f * np.asarray(net.out_scale))
+    assert pdmp.stream_status()[0] == 0
 
 
 @pytest.mark.parametrize("fp32_act,tol", [(True, 1e-4), (False, 2e-2)])
