@@ -147,3 +147,31 @@ def test_inverse_sampled_at_the_bench_size(fitted):
     ref, _ = oracle.morph_inverse(wk.field, z.cpu().numpy()[idx], wk.T, eta, tol=1e-13, maxit=200)
     assert max_abs(y[idx], ref) <= 1e-4
     assert int(work.item()) >= n * wk.T * wk.field.M
+
+
+def test_log_density_in_one_kernel_at_the_bench_size(fitted):
+    """The log-density (Eq. 2 and the change of variables of Sec. 3.2) as the
+    benchmark's extra runs it: the first 2^18 samples morphed through T = 50
+    steps, then inverted with every step's log-det taken from the inverse's
+    last fixed-point sweep.  Against the two-kernel path (the inverse, then
+    the forward log-det from the recovered points) on every sample and the
+    oracle's log-det at the recovered points on sampled ones, both at abs
+    1e-4 T; the recovered points equal x0 to 1e-4."""
+    wk, params, eta, fld = fitted
+    n, T = 1 << 18, wk.T
+    lo, hi = np.asarray(wk.lo, np.float64), np.asarray(wk.hi, np.float64)
+    x0 = np.ascontiguousarray(wk.x0[:n])
+    z = pdmp.morph(fld, dev(x0), T, eta)
+    lp, y = pdmp.log_density(fld, z, T, eta, lo, hi, tol=1e-6, maxit=60)
+    lp, yh = lp.cpu().numpy(), y.cpu().numpy()
+    assert max_abs(yh, x0) <= 1e-4
+    inside = np.all((yh > lo + 1e-3) & (yh < hi - 1e-3), axis=1)
+    assert inside.mean() > 0.99 and np.isfinite(lp[inside]).all()
+    log_vol = float(np.log(np.prod(hi - lo)))
+    ld2 = pdmp.logdet(fld, y, T, eta).cpu().numpy()
+    assert np.abs(lp[inside] - (-log_vol - ld2[inside])).max() <= 1e-4 * T
+    idx = sample_idx(n, 24, 25)
+    idx = idx[inside[idx]]
+    rl, _, _ = oracle.logdet(wk.field, yh[idx], T, eta)
+    assert np.abs(lp[idx] - (-log_vol - rl)).max() <= 1e-4 * T
+    assert np.abs(rl).max() > 1e-3
