@@ -499,7 +499,12 @@ pdmp_status pdmp_morph_inverse(const pdmp_field* f, const float* z, int64_t N, i
  *            = -inf                                otherwise,
  * with y = phi^{-1}(z) from pdmp_morph_inverse (tol, maxit, ws, ws_bytes as
  * there) written to y (N x d, must not alias z) and log det J as pdmp_logdet
- * computes it (with the same workspace). */
+ * computes it (with the same workspace).  With a workspace, RBF fields in
+ * d = 2, 3 take one kernel on sorted tiles (256 samples for d = 2, 192 for
+ * d = 3): every fixed-point sweep of the inverse also sums the Hessian
+ * moments, and step t's log det (I - eta Hess c) is taken at the iterate of
+ * the sweep that stopped, a point within the stopping tolerance of x_t,
+ * instead of on a second forward pass from y. */
 pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int32_t T, float eta, const double* lo,
                              const double* hi, float tol, int32_t maxit, float* y, float* log_p, void* ws,
                              size_t ws_bytes, void* stream);

@@ -490,6 +490,14 @@ pdmp_status pdmp_log_density(const pdmp_field* f, const float* z, int64_t N, int
   if (N == 0) return PDMP_OK;
   if (!ok_ptr(z, true) || !ok_ptr(y, true) || !ok_ptr(log_p, true) || y == z) return PDMP_ERR_INVALID_ARG;
   cudaStream_t st = as_stream(stream);
+  if ((s = check_ws(f, N, ws, ws_bytes)) != PDMP_OK) return s;
+  if (T > 0 && ws != nullptr && f->kind == PDMP_KIND_RBF && (f->d == 2 || f->d == 3)) {
+    // one kernel: each step's log-det from the inverse's last fixed-point sweep
+    if ((s = cuda_status(pdmp::log_density_rbf_fast(f->d, field_args(f), z, N, T, eta, tol, maxit, y, log_p, nullptr,
+                                                    nullptr, ws, st))) != PDMP_OK)
+      return s;
+    return cuda_status(pdmp::uniform_log_density(y, N, f->d, lo, hi, log_p, st));
+  }
   if ((s = pdmp_morph_inverse(f, z, N, T, eta, tol, maxit, y, nullptr, ws, ws_bytes, nullptr, stream)) != PDMP_OK)
     return s;
   if ((s = cuda_status(pdmp::logdet(f->kind, f->d, field_args(f), y, N, T, eta, log_p, nullptr, ws, st))) != PDMP_OK)

@@ -100,6 +100,12 @@ cudaError_t inverse_rff_mma(int d, const FieldArgs& fa, const float* z, int64_t 
 // RBF, d = 2, 3 on sorted tiles (ws: morph_rbf_fast_workspace)
 cudaError_t logdet_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld,
                             float* xT, void* ws, cudaStream_t st);
+// the inverse map with every step's log-det from its last fixed-point sweep
+// (RBF, d = 2, 3 on sorted tiles; ws: morph_rbf_fast_workspace): y = phi^{-1}(z),
+// ld = log det J(y)
+cudaError_t log_density_rbf_fast(int d, const FieldArgs& fa, const float* z, int64_t N, int T, float eta, float tol,
+                                 int maxit, float* y, float* ld, int32_t* iters, unsigned long long* work, void* ws,
+                                 cudaStream_t st);
 
 cudaError_t occupancy_query(int kind, int d, const FieldArgs& fa, const float* x, int64_t N, float* c, float* s,
                             float* grad, cudaStream_t st);

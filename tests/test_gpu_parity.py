@@ -701,3 +701,41 @@ def test_log_density_matches_oracle_and_integrates_to_one():
     ls, _ = pdmp.log_density(fld, dev(zs), T, eta, lo, hi)
     mass = float(torch.exp(ls.double()).mean()) * np.prod(zb_hi - zb_lo)
     assert abs(mass - 1.0) <= 5e-3
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_log_density_one_kernel_matches_two_kernels_and_oracle(d):
+    """With a workspace, RBF fields in d = 2, 3 take the log-density in one
+    kernel (each step's log-det from the inverse's last fixed-point sweep).
+    Ragged tiles (256 samples for d = 2, 192 for d = 3) and points outside
+    the image of the box: the recovered points against the oracle's inverse
+    (1e-4), the log-density against the two-kernel path (the inverse, then
+    the forward log-det from the recovered points) and against the oracle's
+    log-det at the recovered points, both abs 1e-4 T."""
+    lo, hi = np.zeros(d), np.full(d, 10.0)
+    fld_h = wl.random_field(40 + d, wl.RBF, d, 600 if d == 2 else 900, gamma=2.0, wscale=2.0, bias=-0.5)
+    eta, _ = rbf_eta(fld_h, lo - 1.0, hi + 1.0, cells=32 if d == 2 else 10)
+    T = 8
+    fld = pdmp.DeviceField.from_host(fld_h)
+    n = 4096 + 77
+    x0 = wl.uniform_box(41 + d, 3, n, lo - 0.5, hi + 0.5)
+    z = pdmp.morph(fld, dev(x0), T, eta)
+    lp, y = pdmp.log_density(fld, z, T, eta, lo, hi, tol=1e-6, maxit=60)
+    lp, yh = lp.cpu().numpy(), y.cpu().numpy()
+    assert max_abs(yh, x0) <= 1e-4
+    clear = np.all(np.minimum(np.abs(yh - lo), np.abs(yh - hi)) > 1e-3, axis=1)
+    rin = np.all((yh >= lo) & (yh <= hi), axis=1)
+    assert np.array_equal(np.isfinite(lp)[clear], rin[clear])
+    assert (clear & ~rin).sum() > 0 and (clear & rin).sum() > n // 2
+    log_vol = float(np.log(np.prod(hi - lo)))
+    yin = np.ascontiguousarray(yh[clear & rin])
+    ld2 = pdmp.logdet(fld, dev(yin), T, eta).cpu().numpy()
+    assert np.abs(lp[clear & rin] - (-log_vol - ld2)).max() <= 1e-4 * T
+    idx = np.flatnonzero(clear & rin)[:: max(1, (clear & rin).sum() // 40)]
+    ry, _ = oracle.morph_inverse(fld_h, z.cpu().numpy()[idx], T, eta, tol=1e-13, maxit=200)
+    assert max_abs(yh[idx], ry) <= 1e-4
+    rl, _, mindet = oracle.logdet(fld_h, yh[idx], T, eta)
+    assert np.all(mindet > 0)
+    assert np.abs(lp[idx] - (-log_vol - rl)).max() <= 1e-4 * T
+    assert np.abs(rl).max() > 1e-3
+    assert pdmp.stream_status()[0] == 0
