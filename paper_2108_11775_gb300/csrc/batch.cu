@@ -191,9 +191,9 @@ k_morph_batched(const BatchEnv* __restrict__ envs, const BatchUnit* __restrict__
     const int64_t p0 = E.sample_base + (int64_t)un.tile * kTile;
     const int64_t pend = E.sample_base + E.N;
     if (E.d == 2)
-      fast_tile<2, W, K, false>(a, p0, pend, smem);
+      fast_tile<2, W, K, false, true>(a, p0, pend, smem);
     else
-      fast_tile<3, W, K, false>(a, p0, pend, smem);
+      fast_tile<3, W, K, false, true>(a, p0, pend, smem);
   }
 }
 

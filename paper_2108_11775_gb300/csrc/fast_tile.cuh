@@ -55,6 +55,12 @@ __device__ __forceinline__ u64 ex2x2(u64 a) {
   upk(a, lo, hi);
   return pk(ex2_approx(lo), ex2_approx(hi));
 }
+// 2^-a of both halves
+__device__ __forceinline__ u64 ex2x2_neg(u64 a) {
+  float lo, hi;
+  upk(a, lo, hi);
+  return pk(ex2_approx(-lo), ex2_approx(-hi));
+}
 
 // Tile shape: W warps per block (each summing over its share of M) and K
 // samples per lane (even: f32x2 pairs).  The single-field launch uses
@@ -327,6 +333,79 @@ __device__ __forceinline__ void stage_accumulate(const u64* rec, bool expanded, 
   }
 }
 
+// The direct form about the tile centre o for tiles too wide for the expanded
+// one (the batched launch's tiles): x - mu per feature in coordinates scaled
+// by sqrt(g'), so that -log2 e = |x' - mu'|^2 - log2|w| takes d FMAs from the
+// record's -log2|w|, and the sign rides in S's FMA:
+//   S = sum sg e,  G' = sum sg e (mu - o),  so  sum w phi (x - mu) = u S - G'
+// with u = x - o: 3d + 1 packed operations per sample pair and feature
+// (the direct form about 0 takes 3d + 3).  Records:
+//   [-c'_0 -c'_0]..[-c'_{d-1} ..][-lw -lw][sg sg][c~_0 c~_0]..
+//   (c = mu - o, c' = sqrt(g') c, c~ = sg c)
+template <int D>
+__device__ __forceinline__ void stage_build_origin(int64_t M, int64_t m0, const float* o, float gl2e,
+                                                   const float4* raw, u64* rec, int lane) {
+  constexpr int RP = FastRec<D>::kPairs;
+  constexpr int KT = FastRec<D>::kTab;
+  const float sc = sqrtf(gl2e);
+  cp_async_wait_all();
+  for (int i = lane; i < kWarpStage; i += 32) {
+    const int64_t m = m0 + i;
+    float mu[D], lw = -INFINITY, sg = 0.0f;
+    if (m < M) {
+      const float4 t0 = raw[i * KT];
+      mu[0] = t0.x;
+      mu[1] = t0.y;
+      if (D == 2) {
+        lw = t0.z;
+        sg = t0.w;
+      } else {
+        mu[2] = t0.z;
+        lw = t0.w;
+        sg = raw[i * KT + 1].x;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) mu[j] = o[j];
+    }
+    u64 r[RP];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const float c = mu[j] - o[j], cs = -sc * c, ct = sg * c;
+      r[j] = pk(cs, cs);
+      r[D + 2 + j] = pk(ct, ct);
+    }
+    r[D] = pk(-lw, -lw);
+    r[D + 1] = pk(sg, sg);
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(rec + (size_t)i * RP);
+#pragma unroll
+    for (int j = 0; j < RP / 2; ++j) dst[j] = make_ulonglong2(r[2 * j], r[2 * j + 1]);
+  }
+}
+
+// U holds sqrt(g') (x - o); S, G' as above
+template <int D, int P>
+__device__ __forceinline__ void stage_accumulate_origin(const u64* rec, const u64 (&U)[P][D], u64 (&S)[P],
+                                                        u64 (&G)[P][D]) {
+  constexpr int RP = FastRec<D>::kPairs;
+  for (int c = 0; c < kWarpStage; ++c) {
+    const u64* r = rec + (size_t)c * RP;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      u64 q = r[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const u64 dx = add2(U[i][j], r[j]);
+        q = fma2(dx, dx, q);
+      }
+      const u64 e = ex2x2_neg(q);
+      S[i] = fma2(r[D + 1], e, S[i]);
+#pragma unroll
+      for (int j = 0; j < D; ++j) G[i][j] = fma2(e, r[D + 2 + j], G[i][j]);
+    }
+  }
+}
+
 // Loads the tile's samples (sorted positions [p0, p_end)).
 template <int D, int K>
 __device__ __forceinline__ void tile_load(const TileArgs& a, int64_t p0, int64_t p_end, int lane, float (&x)[K][D],
@@ -449,7 +528,11 @@ __device__ __forceinline__ void tile_store(const TileArgs& a, int64_t p0, const 
   __syncthreads();   // the next tile of this block reuses the shared memory
 }
 
-template <int D, int W, int K, bool TRACE>
+// ORIGIN: tiles too wide for the expanded form take the direct form about the
+// tile centre (stage_build_origin) instead of the one about 0.  The
+// single-field launch keeps the latter: there nearly every tile is expanded,
+// and the kernel compiled with both forms ran 6 % slower on such tiles.
+template <int D, int W, int K, bool TRACE, bool ORIGIN = false>
 __device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t p_end, unsigned char* smem) {
   constexpr int RP = FastRec<D>::kPairs;
   constexpr int P = K / 2;
@@ -474,26 +557,74 @@ __device__ __forceinline__ void fast_tile(const TileArgs& a, int64_t p0, int64_t
     float lo[D], hi[D], o[D];
     const bool expanded = tile_frame<D, K>(x, act, gl2e, lo, hi, o);
     u64 U[P][D], S[P], G[P][D];
+    if constexpr (ORIGIN) {
+      if (!expanded)
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
+        for (int j = 0; j < D; ++j) {   // the box's centre; 0 when the box is not finite
+          const float c = 0.5f * (lo[j] + hi[j]);
+          o[j] = c - c == 0.0f ? c : 0.0f;
+        }
+      const float us = expanded ? 1.0f : sqrtf(gl2e);
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
-        U[i][j] = pk(x[2 * i][j] - o[j], x[2 * i + 1][j] - o[j]);
-        G[i][j] = 0ull;
+      for (int i = 0; i < P; ++i) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          U[i][j] = pk(us * (x[2 * i][j] - o[j]), us * (x[2 * i + 1][j] - o[j]));
+          G[i][j] = 0ull;
+        }
+        S[i] = 0ull;
       }
-      S[i] = 0ull;
-    }
-
-    stage_prefetch<D>(tab, M, mbase, wraw, lane);
-    stage_build<D>(M, mbase, expanded, o, gl2e, wraw, wbuf, lane);
-    __syncwarp();
-    for (int st = 0; st < nstage; ++st) {
-      if (st + 1 < nstage) stage_prefetch<D>(tab, M, mbase + (int64_t)(st + 1) * kWarpStage, wraw, lane);
-      stage_accumulate<D, P>(wbuf + (size_t)(st & 1) * kWarpStage * RP, expanded, gl2e, U, S, G);
-      if (st + 1 < nstage)
-        stage_build<D>(M, mbase + (int64_t)(st + 1) * kWarpStage, expanded, o, gl2e, wraw,
-                       wbuf + (size_t)((st + 1) & 1) * kWarpStage * RP, lane);
+      stage_prefetch<D>(tab, M, mbase, wraw, lane);
+      if (expanded)
+        stage_build<D>(M, mbase, true, o, gl2e, wraw, wbuf, lane);
+      else
+        stage_build_origin<D>(M, mbase, o, gl2e, wraw, wbuf, lane);
       __syncwarp();
+      for (int st = 0; st < nstage; ++st) {
+        if (st + 1 < nstage) stage_prefetch<D>(tab, M, mbase + (int64_t)(st + 1) * kWarpStage, wraw, lane);
+        u64* cur = wbuf + (size_t)(st & 1) * kWarpStage * RP;
+        u64* nxt = wbuf + (size_t)((st + 1) & 1) * kWarpStage * RP;
+        const int64_t mn = mbase + (int64_t)(st + 1) * kWarpStage;
+        if (expanded) {
+          stage_accumulate<D, P>(cur, true, gl2e, U, S, G);
+          if (st + 1 < nstage) stage_build<D>(M, mn, true, o, gl2e, wraw, nxt, lane);
+        } else {
+          stage_accumulate_origin<D, P>(cur, U, S, G);
+          if (st + 1 < nstage) stage_build_origin<D>(M, mn, o, gl2e, wraw, nxt, lane);
+        }
+        __syncwarp();
+      }
+      if (!expanded) {
+        // to the direct form's moments: sum w phi (x - mu) = u S - G'
+        const u64 m1 = pk(-1.0f, -1.0f);
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+          for (int j = 0; j < D; ++j)
+            G[i][j] = fma2(pk(x[2 * i][j] - o[j], x[2 * i + 1][j] - o[j]), S[i], mul2(G[i][j], m1));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          U[i][j] = pk(x[2 * i][j] - o[j], x[2 * i + 1][j] - o[j]);
+          G[i][j] = 0ull;
+        }
+        S[i] = 0ull;
+      }
+
+      stage_prefetch<D>(tab, M, mbase, wraw, lane);
+      stage_build<D>(M, mbase, expanded, o, gl2e, wraw, wbuf, lane);
+      __syncwarp();
+      for (int st = 0; st < nstage; ++st) {
+        if (st + 1 < nstage) stage_prefetch<D>(tab, M, mbase + (int64_t)(st + 1) * kWarpStage, wraw, lane);
+        stage_accumulate<D, P>(wbuf + (size_t)(st & 1) * kWarpStage * RP, expanded, gl2e, U, S, G);
+        if (st + 1 < nstage)
+          stage_build<D>(M, mbase + (int64_t)(st + 1) * kWarpStage, expanded, o, gl2e, wraw,
+                         wbuf + (size_t)((st + 1) & 1) * kWarpStage * RP, lane);
+        __syncwarp();
+      }
     }
     tile_finish_step<D, W, K, TRACE>(a, t, p0, act, x, o, expanded, S, G, red, warp, lane);
   }

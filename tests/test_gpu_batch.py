@@ -48,13 +48,33 @@ def test_batched_matches_single_field_and_oracle(variant):
         if x0.shape[0] == 0:
             continue
         single = pdmp.morph(fld, x0, T, eta).cpu().numpy()
-        if variant == 0:                       # same tile shape as the single-field launch
-            assert np.array_equal(out, single)
-        else:
-            assert np.abs(out - single).max() <= 1e-4
+        # tiles too wide for the expanded form take the direct form about the
+        # tile centre here and about 0 in the single-field launch: rounding only
+        assert np.abs(out - single).max() <= (1e-5 if variant == 0 else 1e-4)
         idx = np.arange(0, x0.shape[0], max(1, x0.shape[0] // 8))
         ref = oracle.morph(f, xh[idx], T, eta)
         assert np.abs(out[idx] - ref).max() <= 1e-4
+
+
+def test_batched_variant0_is_the_single_field_launch_on_compact_tiles():
+    """Variant 0 has the single-field launch's tile shape (320 samples): where
+    every tile is compact enough for the expanded form (dense samples, small
+    steps) the two agree bit for bit, in d = 2 and 3, with ragged last tiles."""
+    envs, host = [], []
+    for e, (d, N) in enumerate([(2, 20000 + 17), (3, 60000 + 5), (2, 321)]):
+        f = wl.random_field(500 + e, wl.RBF, d, 300 + 100 * e, lo=0, hi=4, gamma=3.0, wscale=1.5, bias=0.1)
+        eta, _ = rbf_eta(f, np.full(d, -0.5), np.full(d, 4.5), cells=24 if d == 2 else 10)
+        x0 = wl.uniform_box(500 + e, 3, N, np.zeros(d), np.full(d, 4.0))
+        if N == 321:
+            x0 = np.ascontiguousarray(0.5 + 0.05 * x0)     # 321 samples in a box of side 0.2
+        envs.append((pdmp.DeviceField.from_host(f), torch.from_numpy(x0).cuda(), eta, 3))
+        host.append((f, x0))
+    b = pdmp.Batch(envs)
+    b.prepare(0)
+    outs = b.run()
+    for (fld, x0, eta, T), out in zip(envs, outs):
+        assert torch.equal(out, pdmp.morph(fld, x0, T, eta))
+    assert pdmp.stream_status()[0] == 0
 
 
 def test_batched_graph_replay_and_autotune(tmp_path):

@@ -227,14 +227,19 @@ def test_residual_threshold_matches_oracle():
     any one value; a length changes by at most eta L |dx| <= 0.5 sqrt(3) 1e-4
     when x_{T-1} moves by the final-position tolerance 1e-4 per coordinate,
     plus the per-step error of the increment (1e-5 of its scale), so the two
-    thresholds agree to 1e-4.  x_T equals the plain morph's, bit for bit."""
+    thresholds agree to 1e-4.  x_T agrees with the plain morph's to 1e-5 (its
+    last step runs on tiles re-sorted at x_{T-1}, whose frames change only the
+    rounding) and with the oracle's to the final-position tolerance 1e-4."""
     wk, fld, eta, T = _small_world(N_train=1 << 14)
     x0 = wk.extra["x_train"]
     xd = torch.from_numpy(x0).cuda()
     taus = {q: pdmp.residual_threshold(fld, xd, T, eta, q) for q in (0.5, 0.99, 1.0)}
     tau, xT = taus[0.99]
-    assert torch.equal(xT, pdmp.morph(fld, xd, T, eta))
+    xm = pdmp.morph(fld, xd, T, eta)
+    assert float((xT - xm).abs().max()) <= 1e-5
     xprev = oracle.morph(wk.field, x0, T - 1, eta)
+    rT = oracle.morph(wk.field, xprev, 1, eta)
+    assert np.abs(xT.cpu().numpy() - rT).max() <= 1e-4
     lengths = np.linalg.norm(eta * oracle.evaluate(wk.field, xprev)["grad"], axis=1)
     srt = np.sort(lengths)
     n = len(srt)
