@@ -284,6 +284,50 @@ def test_vjp_and_logdet_rff_7d_full_size_sampled():
     assert max_abs(ld[idx], rl) <= 1e-4 * T
 
 
+def test_rff_7d_full_size_with_a_visible_step():
+    """The 7-D workload's field and shape (N = 2^20, M = 4096, T = 20, k = 5)
+    at a step from the sampled Hessian (reading 6) rather than the loose
+    certified bound, so that the chain moves visibly, through the
+    tensor-core kernels: every step of sampled samples at the per-step
+    tolerance (the oracle at the GPU's own state), the VJP correction with the
+    oracle chained segment by segment from the GPU's checkpoints (1e-4 of its
+    norm), and the log-det (abs 1e-4 T, det > 0 at every step)."""
+    wk = wl.config3()
+    f = wk.field
+    lo, hi = np.full(7, -np.pi), np.full(7, np.pi)
+    eta, _ = rff_eta_sampled(f, lo, hi, n=800)
+    fld = pdmp.DeviceField.from_host(f)
+    N, T, k = wk.x0.shape[0], wk.T, wk.extra["k"]
+    x0 = dev(wk.x0)
+    idx = np.concatenate([np.sort(wl.rng(12, 1).choice(N, 40, replace=False)), [0, N - 1]])
+    it = torch.from_numpy(idx).cuda()
+    traj, steps = pdmp.morph_trace(fld, x0, T, eta)
+    tr, st = traj[:, it].cpu().numpy(), steps[:, it].cpu().numpy()
+    del traj, steps
+    assert per_step_check(f, tr, st, eta) <= 1.0
+    assert np.abs(tr[-1] - wk.x0[idx]).max() > 1e-2             # the chain moves visibly
+    ck = torch.empty(T // k, N, 7, device="cuda")
+    xT = pdmp.morph(fld, x0, T, eta, ckpt=ck, k=k)
+    assert np.array_equal(xT[it].cpu().numpy(), tr[-1])
+    gT = wk.extra["gT"]
+    g0 = pdmp.morph_vjp(fld, x0, T, eta, k, dev(gT), ckpt=ck).cpu().numpy()
+    cks = ck[:, it].cpu().numpy()
+    g = gT[idx].astype(np.float64)
+    for j in reversed(range(T // k)):
+        start = wk.x0[idx] if j == 0 else cks[j - 1]
+        g = oracle.morph_vjp(f, start, k, eta, g)
+    corr = g - gT[idx]
+    assert np.linalg.norm(corr) > 1e-2 * np.linalg.norm(gT[idx])
+    assert np.linalg.norm((g0[idx] - gT[idx]) - corr) <= 1e-4 * np.linalg.norm(corr)
+    ld = pdmp.logdet(fld, x0, T, eta).cpu().numpy()
+    assert np.isfinite(ld).all()
+    rl, _, mindet = oracle.logdet(f, wk.x0[idx], T, eta)
+    assert np.all(mindet > 0)
+    assert max_abs(ld[idx], rl) <= 1e-4 * T
+    assert np.abs(rl).max() > 1e-2
+    assert pdmp.stream_status()[0] == 0
+
+
 @pytest.mark.parametrize("d,N,T,k,use_ckpt", [(2, 1000, 10, 5, True), (2, 700, 6, 6, False), (3, 451, 6, 2, True),
                                               (3, 193, 4, 1, False)])
 def test_vjp_sorted_tiles_rbf(d, N, T, k, use_ckpt):
