@@ -622,15 +622,28 @@ def extra_surrogate(pdmp, torch, args):
     plain = torch.empty_like(x0)
     ws = torch.empty(pdmp.morph_workspace(f, x0.shape[0]), dtype=torch.uint8, device="cuda")
     t_plain = _time(torch, lambda: pdmp.morph(f, x0, T, eta, out=plain, ws=ws), reps=2)
-    sur = torch.empty_like(x0)
+    # the residual check on the culled kernel (eps = 1e-6 on s and |grad s|), and on the dense one
+    r_cut, _ = pdmp.cull_radius(f, 1e-6)
+    sws = torch.empty(pdmp.surrogate_workspace(f, x0.shape[0]), dtype=torch.uint8, device="cuda")
+    sur, sur_d = torch.empty_like(x0), torch.empty_like(x0)
     res = {}
 
     def run_sur():
-        res["nf"] = net.infer(f, x0, T, eta, tau_r, out=sur)[1]
+        res["nf"] = net.infer(f, x0, T, eta, tau_r, out=sur, ws=sws, r_cut=r_cut)[1]
+
+    def run_sur_dense():
+        res["nf_dense"] = net.infer(f, x0, T, eta, tau_r, out=sur_d, ws=sws)[1]
     run_sur()
     t_sur = _time(torch, run_sur, reps=2)
+    run_sur_dense()
+    t_sur_d = _time(torch, run_sur_dense, reps=2)
+    # the plain morph culled the same way, for context (not the method the surrogate replaces)
+    cws = torch.empty(pdmp.morph_culled_workspace(f, x0.shape[0]), dtype=torch.uint8, device="cuda")
+    plain_c = torch.empty_like(x0)
+    t_plain_c = _time(torch, lambda: pdmp.morph_culled(f, x0, T, eta, r_cut, out=plain_c, ws=cws), reps=1)
     col = lambda x: float(pdmp.box_labels(boxes, x).float().mean().item())
-    c_prior, c_plain, c_sur = col(x0), col(plain), col(sur)
+    c_prior, c_plain, c_sur, c_sur_d = col(x0), col(plain), col(sur), col(sur_d)
+    del sws, cws
     # the network alone (inference kernel) on the N samples
     pred = torch.empty_like(x0)
     t_net = _time(torch, lambda: net.forward(x0, out=pred), reps=3)
@@ -650,6 +663,10 @@ def extra_surrogate(pdmp, torch, args):
            "note": "bf16 peak: MEASURED_PEAKS.json bf16_tflops (cuBLAS, burst); MUFU bound: the SiLU and "
                    "encoding's special-function operations per sample at 32 per SM per clock"}
     return {"speedup_vs_plain_morph": t_plain / t_sur, "ms_plain": 1e3 * t_plain, "ms_surrogate": 1e3 * t_sur,
+            "check": "culled (r_cut = %.4g from eps = 1e-6)" % r_cut,
+            "dense_check": {"ms_surrogate": 1e3 * t_sur_d, "speedup_vs_plain_morph": t_plain / t_sur_d,
+                            "fallback_fraction": res["nf_dense"] / x0.shape[0], "collision_rate": c_sur_d},
+            "context_culled_plain_morph": {"ms": 1e3 * t_plain_c, "speedup_of_surrogate": t_plain_c / t_sur},
             "mlp": mlp,
             "fallback_fraction": res["nf"] / x0.shape[0], "collision_rate": {"prior": c_prior, "plain_morph": c_plain,
                                                                              "surrogate": c_sur},

@@ -506,6 +506,13 @@ def cull_radius(field: DeviceField, eps: float):
     return float(r.value), float(W.value)
 
 
+def surrogate_workspace(field: DeviceField, N: int) -> int:
+    """Bytes of device workspace pdmp_surrogate_infer(_culled) needs for N samples."""
+    L = _mlp_sigs()
+    f = field.struct()
+    return int(L.pdmp_surrogate_workspace(ctypes.byref(f), int(N)))
+
+
 def morph_culled_workspace(field: DeviceField, N: int) -> int:
     """Bytes of device workspace pdmp_morph_culled needs for N samples."""
     f = field.struct()
@@ -867,6 +874,8 @@ def _mlp_sigs():
         "pdmp_mlp_gradient": [MP, _P, _P, _i32, _i32, _P, _P, _P, _P, _sz, _P],
         "pdmp_mlp_train_step": [MP, _P, _P, _i32, _f32, _f32, _f32, _f32, _i32, _P, _P, _sz, _P],
         "pdmp_surrogate_infer": [MP, _FP, _P, _i64, _i32, _f32, _f32, _P, ctypes.POINTER(_i64), _P, _sz, _P],
+        "pdmp_surrogate_infer_culled": [MP, _FP, _P, _i64, _i32, _f32, _f32, _f32, _P, ctypes.POINTER(_i64), _P, _sz,
+                                        _P],
         "pdmp_displacement_rms": [_P, _P, _i64, _i32, _P, _P],
         "pdmp_residual_threshold": [_FP, _P, _i64, _i32, _f32, _f32, ctypes.POINTER(_f32), _P, _P, _sz, _P],
     }.items():
@@ -1054,8 +1063,10 @@ class Surrogate:
         return loss
 
     def infer(self, field: DeviceField, x0: torch.Tensor, T: int, eta: float, tau_r: float,
-              out: torch.Tensor | None = None, ws: torch.Tensor | None = None):
-        """(x_T, number of samples that fell back to the plain morph)."""
+              out: torch.Tensor | None = None, ws: torch.Tensor | None = None, r_cut: float | None = None):
+        """(x_T, number of samples that fell back to the plain morph).  r_cut:
+        run the residual check on the culled kernel with that cut-off radius
+        (pdmp_surrogate_infer_culled; from cull_radius(field, eps))."""
         L = _mlp_sigs()
         N = x0.shape[0]
         if out is None:
@@ -1066,9 +1077,17 @@ class Surrogate:
             ws = torch.empty(max(need, 16), dtype=torch.uint8, device=x0.device)
         nf = _i64(0)
         m = self.struct()
-        _check(L.pdmp_surrogate_infer(ctypes.byref(m), ctypes.byref(f), _ptr(x0, name="x0"), N, int(T), float(eta),
-                                      float(tau_r), _ptr(out, shape=x0.shape, name="out"), ctypes.byref(nf),
-                                      ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()), "pdmp_surrogate_infer")
+        if r_cut is None:
+            _check(L.pdmp_surrogate_infer(ctypes.byref(m), ctypes.byref(f), _ptr(x0, name="x0"), N, int(T),
+                                          float(eta), float(tau_r), _ptr(out, shape=x0.shape, name="out"),
+                                          ctypes.byref(nf), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()),
+                   "pdmp_surrogate_infer")
+        else:
+            _check(L.pdmp_surrogate_infer_culled(ctypes.byref(m), ctypes.byref(f), _ptr(x0, name="x0"), N, int(T),
+                                                 float(eta), float(tau_r), float(r_cut),
+                                                 _ptr(out, shape=x0.shape, name="out"), ctypes.byref(nf),
+                                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream()),
+                   "pdmp_surrogate_infer_culled")
         return out, int(nf.value)
 
 

@@ -850,8 +850,29 @@ pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const
   if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || ws == nullptr || !aligned16(ws)) return PDMP_ERR_INVALID_ARG;
   if (xT == x0) return PDMP_ERR_INVALID_ARG;   // the fallback re-reads x0 after xT is written
   if (ws_bytes < pdmp::surrogate_workspace(f->d, f->M, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
-  return cuda_status(pdmp::surrogate_infer(net, f->d, field_args(f), x0, N, T, eta, tau_r, xT, n_fallback, ws,
-                                           as_stream(stream)));
+  return cuda_status(pdmp::surrogate_infer(net, f->d, field_args(f), x0, N, T, eta, tau_r, 0.0f, xT, n_fallback,
+                                           ws, as_stream(stream)));
+}
+
+pdmp_status pdmp_surrogate_infer_culled(const pdmp_mlp* net, const pdmp_field* f, const float* x0, int64_t N,
+                                        int32_t T, float eta, float tau_r, float r_cut, float* xT,
+                                        int64_t* n_fallback, void* ws, size_t ws_bytes, void* stream) {
+  NvtxRange nvtx_range("pdmp_surrogate_infer_culled");
+  pdmp_status s = check_mlp(net, false);
+  if (s != PDMP_OK) return s;
+  if ((s = check_field(f)) != PDMP_OK) return s;
+  if (f->kind != PDMP_KIND_RBF || f->d != 3) return PDMP_ERR_UNSUPPORTED;
+  if ((s = check_step(f, eta)) != PDMP_OK) return s;
+  if (N < 0 || T < 0 || n_fallback == nullptr || !(tau_r >= 0.0f)) return PDMP_ERR_INVALID_ARG;
+  if (!(r_cut > 0.0f) || !std::isfinite(r_cut)) return PDMP_ERR_INVALID_ARG;
+  if (N >= ((int64_t)1 << 31)) return PDMP_ERR_INVALID_ARG;
+  *n_fallback = 0;
+  if (N == 0) return PDMP_OK;
+  if (!ok_ptr(x0, true) || !ok_ptr(xT, true) || ws == nullptr || !aligned16(ws)) return PDMP_ERR_INVALID_ARG;
+  if (xT == x0) return PDMP_ERR_INVALID_ARG;
+  if (ws_bytes < pdmp::surrogate_workspace(f->d, f->M, N)) return PDMP_ERR_WORKSPACE_TOO_SMALL;
+  return cuda_status(pdmp::surrogate_infer(net, f->d, field_args(f), x0, N, T, eta, tau_r, r_cut, xT, n_fallback,
+                                           ws, as_stream(stream)));
 }
 
 size_t pdmp_residual_threshold_workspace(const pdmp_field* f, int64_t N) {

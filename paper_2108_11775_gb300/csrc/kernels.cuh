@@ -58,8 +58,10 @@ cudaError_t tanh_net_query(const TanhNetArgs& net, const float* x, int64_t N, fl
                            cudaStream_t st);
 
 size_t morph_rbf_cull_workspace(int d, int64_t M, int64_t N);
+// s_out, g_out (may be NULL): the logit and grad c of the last step's state, per sample
 cudaError_t morph_rbf_cull(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float r_cut,
-                           float* xT, float* ckpt, int k, void* ws, unsigned long long* work, cudaStream_t st);
+                           float* xT, float* ckpt, int k, void* ws, unsigned long long* work, cudaStream_t st,
+                           float* s_out = nullptr, float* g_out = nullptr);
 cudaError_t abs_weight_sum(const float* w, int64_t M, double* out, cudaStream_t st);
 
 cudaError_t logdet_rff7_mma(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* ld, float* xT,
@@ -135,8 +137,11 @@ cudaError_t mlp_train_step(const pdmp_mlp* net, const float* x0, const float* xT
 cudaError_t mlp_refresh(const pdmp_mlp* net, cudaStream_t st);
 size_t surrogate_workspace(int d, int64_t M, int64_t N);
 cudaError_t displacement_rms(const float* x0, const float* xT, int64_t N, int d, float* rms, cudaStream_t st);
+// r_cut > 0: the residual check on the culled kernel (features farther than
+// r_cut from a tile dropped); r_cut = 0: on the dense kernel
 cudaError_t surrogate_infer(const pdmp_mlp* net, int d, const FieldArgs& fa, const float* x0, int64_t N, int T,
-                            float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, cudaStream_t st);
+                            float eta, float tau_r, float r_cut, float* xT, int64_t* n_fallback, void* ws,
+                            cudaStream_t st);
 size_t residual_threshold_workspace(int d, int64_t M, int64_t N);
 cudaError_t residual_threshold(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, int64_t k,
                                float* tau_r, float* xT, void* ws, cudaStream_t st);

@@ -296,7 +296,8 @@ size_t morph_rbf_cull_workspace(int d, int64_t M, int64_t N) { return cull_layou
 
 template <int D>
 static cudaError_t launch_cull(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float r_cut,
-                               float* xT, float* ckpt, int k, void* ws, unsigned long long* work, cudaStream_t st) {
+                               float* xT, float* ckpt, int k, void* ws, unsigned long long* work, cudaStream_t st,
+                               float* s_out, float* g_out) {
   const CullWs c = cull_layout(ws, D, fa.M, N);
   const int64_t cells = cull_cell_capacity<D>() + 1;
   cudaError_t e;
@@ -324,6 +325,8 @@ static cudaError_t launch_cull(const FieldArgs& fa, const float* x0, int64_t N, 
   a.xT = xT;
   a.ckpt = ckpt;
   a.kck = k;
+  a.s_out = s_out;
+  a.g_out = g_out;
   constexpr size_t smem = cull_smem_bytes<D>();
   e = cudaFuncSetAttribute(k_morph_rbf_cull<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -333,9 +336,10 @@ static cudaError_t launch_cull(const FieldArgs& fa, const float* x0, int64_t N, 
 }
 
 cudaError_t morph_rbf_cull(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float r_cut,
-                           float* xT, float* ckpt, int k, void* ws, unsigned long long* work, cudaStream_t st) {
-  if (d == 2) return launch_cull<2>(fa, x0, N, T, eta, r_cut, xT, ckpt, k, ws, work, st);
-  if (d == 3) return launch_cull<3>(fa, x0, N, T, eta, r_cut, xT, ckpt, k, ws, work, st);
+                           float* xT, float* ckpt, int k, void* ws, unsigned long long* work, cudaStream_t st,
+                           float* s_out, float* g_out) {
+  if (d == 2) return launch_cull<2>(fa, x0, N, T, eta, r_cut, xT, ckpt, k, ws, work, st, s_out, g_out);
+  if (d == 3) return launch_cull<3>(fa, x0, N, T, eta, r_cut, xT, ckpt, k, ws, work, st, s_out, g_out);
   return cudaErrorInvalidValue;
 }
 

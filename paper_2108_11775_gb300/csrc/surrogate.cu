@@ -3,7 +3,10 @@
 // fall-back to the prior when the morphed samples are not available).
 //   1. the MLP predicts x_T for every sample;
 //   2. one plain Euler step is evaluated at every prediction (the fast RBF
-//      kernel with T = 1, which also reports the logit s);
+//      kernel with T = 1, which also reports the logit s), or, with a cut-off
+//      radius, the culled kernel's step (features farther than r_cut from a
+//      tile dropped, so that s and |grad s| are within the culling bound of
+//      the dense ones; it reports s and grad c, and the step is -eta grad c);
 //   3. a sample fails when s >= 0 (c >= 1/2: the prediction is in
 //      predicted-occupied space), when that step is longer than tau_r, or when
 //      either is not finite;
@@ -23,6 +26,21 @@ __global__ void k_residual_flags(const float* __restrict__ s, const float* __res
   float r2 = 0.0f;
   for (int j = 0; j < d; ++j) {
     const float v = steps[n * d + j];
+    r2 = fmaf(v, v, r2);
+  }
+  const float sv = s[n];
+  const bool ok = (sv < 0.0f) && (r2 <= tau_r2);     // false for NaN
+  flags[n] = ok ? 0u : 1u;
+}
+
+// the same from grad c of the checked state (the culled check): the step is -eta grad c
+__global__ void k_residual_flags_grad(const float* __restrict__ s, const float* __restrict__ g, int64_t N, int d,
+                                      float eta, float tau_r2, uint32_t* __restrict__ flags) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float r2 = 0.0f;
+  for (int j = 0; j < d; ++j) {
+    const float v = __fmul_rn(eta, g[n * d + j]);
     r2 = fmaf(v, v, r2);
   }
   const float sv = s[n];
@@ -77,7 +95,9 @@ static SurWs sur_layout(void* ws, int d, int64_t M, int64_t N) {
   w.chunks = (uint32_t*)take(sizeof(uint32_t) * ((N + kScanChunk - 1) / kScanChunk + 1));
   w.idx = (int32_t*)take(sizeof(int32_t) * N);
   w.count = (int64_t*)take(sizeof(int64_t));
-  w.fast = take(morph_rbf_fast_workspace(d, M, N));
+  // the fast kernel's workspace, or the culled kernel's for the check (used one after the other)
+  const size_t fb = morph_rbf_fast_workspace(d, M, N), cb = morph_rbf_cull_workspace(d, M, N);
+  w.fast = take(fb > cb ? fb : cb);
   w.bytes = (size_t)(p - (char*)ws);
   return w;
 }
@@ -111,17 +131,25 @@ cudaError_t displacement_rms(const float* x0, const float* xT, int64_t N, int d,
 }
 
 cudaError_t surrogate_infer(const pdmp_mlp* net, int d, const FieldArgs& fa, const float* x0, int64_t N, int T,
-                            float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, cudaStream_t st) {
+                            float eta, float tau_r, float r_cut, float* xT, int64_t* n_fallback, void* ws,
+                            cudaStream_t st) {
   *n_fallback = 0;
   if (N == 0) return cudaSuccess;
   SurWs w = sur_layout(ws, d, fa.M, N);
   cudaError_t e;
   if ((e = mlp_forward(net, x0, N, xT, false, st))) return e;
   if (T == 0) return cudaSuccess;
-  // one plain step at every prediction: traj[0] = prediction, steps[0] = its increment, s = its logit
-  if ((e = morph_rbf_fast(d, fa, xT, N, 1, eta, nullptr, nullptr, 0, w.traj, w.steps, w.fast, st, w.s))) return e;
   const unsigned nb = (unsigned)((N + 255) / 256);
-  k_residual_flags<<<nb, 256, 0, st>>>(w.s, w.steps, N, d, tau_r * tau_r, w.flags);
+  if (r_cut > 0.0f) {
+    // one culled step at every prediction: s = its logit, steps = grad c there (the step is -eta grad c)
+    if ((e = morph_rbf_cull(d, fa, xT, N, 1, eta, r_cut, w.traj, nullptr, 0, w.fast, nullptr, st, w.s, w.steps)))
+      return e;
+    k_residual_flags_grad<<<nb, 256, 0, st>>>(w.s, w.steps, N, d, eta, tau_r * tau_r, w.flags);
+  } else {
+    // one plain step at every prediction: traj[0] = prediction, steps[0] = its increment, s = its logit
+    if ((e = morph_rbf_fast(d, fa, xT, N, 1, eta, nullptr, nullptr, 0, w.traj, w.steps, w.fast, st, w.s))) return e;
+    k_residual_flags<<<nb, 256, 0, st>>>(w.s, w.steps, N, d, tau_r * tau_r, w.flags);
+  }
   if ((e = exclusive_scan_u32(w.flags, N, w.offs, w.chunks, st))) return e;
   k_compact<<<nb, 256, 0, st>>>(w.flags, w.offs, N, w.idx, w.count);
   int64_t cnt = 0;

@@ -1,6 +1,8 @@
 """The learned surrogate: BF16 MLP forward and gradients against the FP64
 oracle (same BF16 weights upcast), training on pairs the plain morph
 generates, and inference with the plain morph as fallback and judge."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -203,6 +205,55 @@ def test_surrogate_inference_fallback_is_the_plain_morph():
     if idx.size:
         ref = oracle.morph(wk.field, x0.cpu().numpy()[idx], T, eta)
         assert np.abs(o[idx] - ref).max() <= 1e-4
+
+
+def test_culled_residual_check_matches_the_dense_check():
+    """pdmp_surrogate_infer_culled: the residual check on the culled kernel
+    (r_cut from cull_radius(f, 1e-6)) decides like the dense check except for
+    samples within the culling margin of a threshold (s = 0 or step length =
+    tau_r); accepted samples are the network's predictions and fallen-back
+    ones the plain morph, bit for bit where both checks agree on the whole
+    fallback set, within rounding otherwise."""
+    wk, fld, eta, T = _small_world(M=768)
+    N = 20000
+    x0 = torch.from_numpy(wl.uniform_box(23, 3, N, LO, HI)).cuda()
+    net = pdmp.Surrogate(LO, HI, [0.02, 0.02, 0.02], seed=2)
+    r_cut, _ = pdmp.cull_radius(fld, 1e-6)
+    assert 0.0 < r_cut < 5.0                                   # the check really is culled
+    pred = net.forward(x0)
+    q = pdmp.occupancy_query(fld, pred, want=("s", "grad"))
+    s = q["s"].cpu().numpy()
+    slen = (eta * q["grad"]).norm(dim=1).cpu().numpy()
+    plain = pdmp.morph(fld, x0, T, eta)
+    # tau_r = 0: every sample falls back under both checks
+    oc, nc = net.infer(fld, x0, T, eta, 0.0, r_cut=r_cut)
+    od, nd = net.infer(fld, x0, T, eta, 0.0)
+    assert nc == nd == N and torch.equal(oc, od) and torch.equal(oc, plain)
+    for tau in (1e9, float(np.median(slen[s < 0]))):
+        od, nd = net.infer(fld, x0, T, eta, tau)
+        oc, nc = net.infer(fld, x0, T, eta, tau, r_cut=r_cut)
+        fd = ~(od == pred).all(dim=1).cpu().numpy()
+        fc = ~(oc == pred).all(dim=1).cpu().numpy()
+        assert fd.sum() == nd and fc.sum() == nc
+        assert 0 < nc < N
+        differ = fd != fc
+        near = (np.abs(s) <= 1e-4) | (np.abs(slen / tau - 1.0) <= 1e-3)
+        assert np.all(near[differ]) and differ.sum() <= 5
+        o_c, o_d, p_ = oc.cpu().numpy(), od.cpu().numpy(), plain.cpu().numpy()
+        same = ~differ
+        assert np.array_equal(o_c[same & ~fc], pred.cpu().numpy()[same & ~fc])
+        tol = 0.0 if not differ.any() else 1e-5
+        assert np.abs(o_c[same & fc] - p_[same & fc]).max() <= tol
+        assert np.abs(o_c[same] - o_d[same]).max() <= tol
+    L = pdmp._mlp_sigs()
+    m, f = net.struct(), fld.struct()
+    ws = torch.empty(int(L.pdmp_surrogate_workspace(ctypes.byref(f), N)), dtype=torch.uint8, device="cuda")
+    out, nf = torch.empty_like(x0), ctypes.c_int64(0)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        st = L.pdmp_surrogate_infer_culled(ctypes.byref(m), ctypes.byref(f), x0.data_ptr(), N, T, eta, 1.0, bad,
+                                           out.data_ptr(), ctypes.byref(nf), ws.data_ptr(), ws.numel(), None)
+        assert st == 1                                          # PDMP_ERR_INVALID_ARG
+    assert pdmp.stream_status()[0] == 0
 
 
 def test_save_and_load_round_trip(tmp_path):
