@@ -799,6 +799,10 @@ def profile_case(case: str, reps: int = 1):
         L, _ = pdmp.tanh_net_lipschitz(net)
         x0 = torch.from_numpy(wl.uniform_box(7, wl.S_SAMPLES, 1 << 18, np.zeros(2), np.full(2, 10.0))).cuda()
         out["ms"] = 1e3 * _time(torch, lambda: pdmp.tanh_net_morph(net, x0, 3, float(np.float32(0.5 / L))), reps=reps)
+    elif case == "surrogate":
+        # the 3-D surrogate end to end, as the extra runs it (training, plain morph, inference)
+        import types
+        out.update(extra_surrogate(pdmp, torch, types.SimpleNamespace(surrogate_steps=1500)))
     elif case == "mlp":
         # the surrogate network's inference kernel (random initial weights: the
         # kernel's work does not depend on their values) on 2^20 samples
@@ -828,7 +832,7 @@ def main():
     ap.add_argument("--workload", choices=["full", "small"], default="full",
                     help="small: 262,144 samples and 3 steps of the same workload (for ncu captures)")
     ap.add_argument("--case", choices=["rff7d", "vjp", "logdet", "culled", "inverse", "inverse_rff", "vjp_rbf", "logdet_rbf",
-                                       "tanh", "mlp"],
+                                       "tanh", "mlp", "surrogate"],
                     default=None,
                     help="run one small launch of that kernel family and exit (for ncu captures)")
     ap.add_argument("--case-reps", type=int, default=1, help="timed repetitions of --case (best of)")

@@ -124,7 +124,8 @@ pdmp_status pdmp_selftest_stage_wait(const float* src, float* dst, int64_t limit
  * ws: NULL, or ws_bytes >= pdmp_morph_workspace(f, N) bytes of caller-owned
  * device scratch.  With a workspace, RBF fields in d = 2 or 3 take the fast
  * path: samples are ordered spatially (a deterministic counting sort on
- * Hilbert-ordered cells) so that each tile of 320 samples is compact, and features are
+ * Hilbert-ordered cells) so that each tile of 320 samples (128 when N is too
+ * small to fill the GPU with 320-sample tiles) is compact, and features are
  * evaluated in an expanded form about the tile's centre with packed f32x2
  * arithmetic (2d + 1 FP32 operations and one ex2 per feature); RFF fields
  * with d <= 7 put both contractions of a step, theta = omega . x + b and

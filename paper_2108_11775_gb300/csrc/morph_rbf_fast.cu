@@ -20,19 +20,36 @@
 // Work split.  A block of 4 warps owns a tile of 320 samples; every warp holds
 // all 320 (10 per lane, five f32x2 pairs) and sums over its own contiguous
 // quarter of the centres; the four partial sums are added in a fixed order
-// once per step.
+// once per step.  Launches too small to fill the GPU take 128-sample tiles
+// (below).
 #include "fast_tile.cuh"
 #include "kernels.cuh"
 #include "sort.cuh"
 
 namespace pdmp {
 
-template <int D, bool TRACE>
-__global__ void __launch_bounds__(FastShape::kThreads, FastShape::kMinBlocks)
+template <int D, bool TRACE, int K>
+__global__ void __launch_bounds__(Shape<4, K>::kThreads, Shape<4, K>::kMinBlocks)
 k_morph_rbf_fast(TileArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t p0 = (int64_t)blockIdx.x * FastShape::kTile;
-  fast_tile<D, FastShape::kWarps, FastShape::kK, TRACE>(a, p0, a.N, smem);
+  const int64_t p0 = (int64_t)blockIdx.x * Shape<4, K>::kTile;
+  fast_tile<D, 4, K, TRACE>(a, p0, a.N, smem);
+}
+
+// Samples per lane.  A launch of fewer 320-sample tiles than fit on the GPU at
+// once (3 per SM) leaves SMs idle; it takes 128-sample tiles instead (16
+// warps per SM).  Measured on a 3-D field (M = 8192, T = 40): 2^16 samples
+// 9.3 ms against 13.2 ms; from one wave of 320-sample tiles up (197,641 and
+// 2^18 samples) the larger tiles are as fast or faster.
+constexpr int kSmallK = 4;
+
+static int fast_samples_per_lane(int64_t N) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms < 1)
+    sms = 152;
+  const int64_t tiles = (N + FastShape::kTile - 1) / FastShape::kTile;
+  return tiles < (int64_t)FastShape::kMinBlocks * sms ? kSmallK : FastShape::kK;
 }
 
 // ------------------------------------------------------------------ host
@@ -44,6 +61,23 @@ size_t morph_rbf_fast_workspace(int d, int64_t M, int64_t N) {
   return rbf_fast_table_bytes(d, M) + sort_workspace(d, N);
 }
 
+template <int D, int K>
+static cudaError_t launch_shape(const TileArgs& a, int64_t N, bool trace, cudaStream_t st) {
+  constexpr size_t smem = fast_smem_bytes<D, 4, K>();
+  const unsigned blocks = (unsigned)((N + Shape<4, K>::kTile - 1) / Shape<4, K>::kTile);
+  cudaError_t e;
+  if (trace) {
+    e = cudaFuncSetAttribute(k_morph_rbf_fast<D, true, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_morph_rbf_fast<D, true, K><<<blocks, Shape<4, K>::kThreads, smem, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(k_morph_rbf_fast<D, false, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_morph_rbf_fast<D, false, K><<<blocks, Shape<4, K>::kThreads, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 template <int D>
 static cudaError_t launch_fast(const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
                                float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st,
@@ -53,7 +87,6 @@ static cudaError_t launch_fast(const FieldArgs& fa, const float* x0, int64_t N, 
   k_rbf_table<D><<<(unsigned)((fa.M + 255) / 256), 256, 0, st>>>(fa.centres, fa.w, fa.M, tab);
   cudaError_t e = spatial_sort(D, x0, N, sw, st);
   if (e != cudaSuccess) return e;
-  constexpr size_t smem = fast_smem_bytes<D, FastShape::kWarps, FastShape::kK>();
   TileArgs a;
   a.tab = tab;
   a.M = fa.M;
@@ -72,17 +105,8 @@ static cudaError_t launch_fast(const FieldArgs& fa, const float* x0, int64_t N, 
   a.steps = steps;
   a.s_out = s_out;
   a.g_out = g_out;
-  const unsigned blocks = (unsigned)((N + FastShape::kTile - 1) / FastShape::kTile);
-  if (traj != nullptr) {
-    e = cudaFuncSetAttribute(k_morph_rbf_fast<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_morph_rbf_fast<D, true><<<blocks, FastShape::kThreads, smem, st>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(k_morph_rbf_fast<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_morph_rbf_fast<D, false><<<blocks, FastShape::kThreads, smem, st>>>(a);
-  }
-  return cudaGetLastError();
+  if (fast_samples_per_lane(N) == kSmallK) return launch_shape<D, kSmallK>(a, N, traj != nullptr, st);
+  return launch_shape<D, FastShape::kK>(a, N, traj != nullptr, st);
 }
 
 cudaError_t morph_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,

@@ -56,12 +56,16 @@ def test_batched_matches_single_field_and_oracle(variant):
         assert np.abs(out[idx] - ref).max() <= 1e-4
 
 
-def test_batched_variant0_is_the_single_field_launch_on_compact_tiles():
-    """Variant 0 has the single-field launch's tile shape (320 samples): where
-    every tile is compact enough for the expanded form (dense samples, small
-    steps) the two agree bit for bit, in d = 2 and 3, with ragged last tiles."""
+@pytest.mark.parametrize("variant,sizes", [(2, [(2, 20000 + 17), (3, 60000 + 5), (2, 321)]),
+                                           (0, [(2, (1 << 18) + 17), (3, (1 << 18) + 5)])])
+def test_batched_variant_is_the_single_field_launch_on_compact_tiles(variant, sizes):
+    """Variant 0 has the single-field launch's tile shape for launches that fill
+    the GPU (320 samples), variant 2 its shape for smaller ones (128 samples):
+    where every tile is compact enough for the expanded form (dense samples,
+    small steps) the two agree bit for bit, in d = 2 and 3, with ragged last
+    tiles."""
     envs, host = [], []
-    for e, (d, N) in enumerate([(2, 20000 + 17), (3, 60000 + 5), (2, 321)]):
+    for e, (d, N) in enumerate(sizes):
         f = wl.random_field(500 + e, wl.RBF, d, 300 + 100 * e, lo=0, hi=4, gamma=3.0, wscale=1.5, bias=0.1)
         eta, _ = rbf_eta(f, np.full(d, -0.5), np.full(d, 4.5), cells=24 if d == 2 else 10)
         x0 = wl.uniform_box(500 + e, 3, N, np.zeros(d), np.full(d, 4.0))
@@ -70,7 +74,7 @@ def test_batched_variant0_is_the_single_field_launch_on_compact_tiles():
         envs.append((pdmp.DeviceField.from_host(f), torch.from_numpy(x0).cuda(), eta, 3))
         host.append((f, x0))
     b = pdmp.Batch(envs)
-    b.prepare(0)
+    b.prepare(variant)
     outs = b.run()
     for (fld, x0, eta, T), out in zip(envs, outs):
         assert torch.equal(out, pdmp.morph(fld, x0, T, eta))

@@ -212,8 +212,9 @@ def test_culled_residual_check_matches_the_dense_check():
     (r_cut from cull_radius(f, 1e-6)) decides like the dense check except for
     samples within the culling margin of a threshold (s = 0 or step length =
     tau_r); accepted samples are the network's predictions and fallen-back
-    ones the plain morph, bit for bit where both checks agree on the whole
-    fallback set, within rounding otherwise."""
+    ones the plain morph (within rounding: the fallback morphs its own subset,
+    in other tiles), and the two calls' outputs are equal bit for bit where
+    the checks agree on the whole fallback set."""
     wk, fld, eta, T = _small_world(M=768)
     N = 20000
     x0 = torch.from_numpy(wl.uniform_box(23, 3, N, LO, HI)).cuda()
@@ -242,9 +243,9 @@ def test_culled_residual_check_matches_the_dense_check():
         o_c, o_d, p_ = oc.cpu().numpy(), od.cpu().numpy(), plain.cpu().numpy()
         same = ~differ
         assert np.array_equal(o_c[same & ~fc], pred.cpu().numpy()[same & ~fc])
-        tol = 0.0 if not differ.any() else 1e-5
-        assert np.abs(o_c[same & fc] - p_[same & fc]).max() <= tol
-        assert np.abs(o_c[same] - o_d[same]).max() <= tol
+        # the fallback morphs its own subset, whose tiles differ from the full set's
+        assert np.abs(o_c[same & fc] - p_[same & fc]).max() <= 1e-5
+        assert np.abs(o_c[same] - o_d[same]).max() <= (0.0 if not differ.any() else 1e-5)
     L = pdmp._mlp_sigs()
     m, f = net.struct(), fld.struct()
     ws = torch.empty(int(L.pdmp_surrogate_workspace(ctypes.byref(f), N)), dtype=torch.uint8, device="cuda")
