@@ -10,9 +10,11 @@
 //            [W1 | W1]: the product is enc W1^T to about 2^-16 of enc;
 //   layers 2, 3: A = BF16(silu(z)) (K = 128), N = 128;
 //   layer 4: N = 16 (3 outputs and zero rows).
-// The epilogue of a layer reads D from TMEM (thread = sample row, eight warps:
-// warps w and w + 4 share the TMEM lanes 32 (w % 4) .. + 31 and take the low
-// and high 64 columns), adds the bias, applies SiLU and writes the next A.
+// The epilogue of a layer reads D from TMEM (thread = sample row, sixteen
+// warps: warps w, w + 4, w + 8 and w + 12 share the TMEM lanes 32 (w % 4) ..
+// + 31 and take 32 columns each), adds the bias, applies SiLU and writes the
+// next A.  (Sixteen warps ran 5 % faster than eight of 64 columns each:
+// 0.438 against 0.462 ms for 2^20 samples.)
 // Two tiles are in flight per CTA: while the threads run one tile's
 // epilogue the tensor core runs the other tile's next layer.
 //
@@ -35,7 +37,9 @@ namespace {
 
 constexpr int kH = 128, kEnc = 39, kEncPad = 48;
 constexpr int kRows = 128;                        // samples a tile (M)
-constexpr int kThreads = 256;                     // 8 warps
+constexpr int kThreads = 512;                     // 16 warps
+constexpr int kGroups = kThreads / 128;           // warps sharing a TMEM lane quarter (column groups)
+constexpr int kGroupCols = kH / kGroups;          // hidden columns a thread takes in an epilogue
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kWaitClocks = 1ll << 31;
 
@@ -106,7 +110,7 @@ k_mlp_forward_tc05(MlpTcArgs a, const float* __restrict__ x0, int64_t N, float* 
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q = warp & 3, half = warp >> 2;
+  const int q = warp & 3, cg = warp >> 2;     // lane quarter, column group
   const int row = 32 * q + lane;                  // this thread's sample within a tile (TMEM lane)
   const uint32_t sbase = tc05::smem_u32(sm);
   float* bias = reinterpret_cast<float*>(sm + C::kOffBias);
@@ -210,7 +214,7 @@ k_mlp_forward_tc05(MlpTcArgs a, const float* __restrict__ x0, int64_t N, float* 
   };
 
   // the encoding of tile t's samples into its layer-1 A buffers: this thread
-  // writes K pairs [10 half, 10 half + 10 + 4 half) of its row (pairs 0..23)
+  // writes K pairs [6 cg, 6 cg + 6) of its row (pairs 0..23)
   auto encode = [&](int t, int64_t n0) {
     float xv[3] = {0.0f, 0.0f, 0.0f};
     const int64_t n = n0 + row;
@@ -219,11 +223,11 @@ k_mlp_forward_tc05(MlpTcArgs a, const float* __restrict__ x0, int64_t N, float* 
       for (int j = 0; j < 3; ++j) xv[j] = x0[n * 3 + j];
     MlpEncIn u;
     mlp_enc_prepare(xv, a.lo, a.in_scale, u);
-    const int p0 = half ? 10 : 0, np = half ? 14 : 10;
+    constexpr int np = kEncPad / 2 / kGroups;
+    static_assert(np * kGroups == kEncPad / 2, "the encoding's K pairs split evenly over the column groups");
 #pragma unroll
-    for (int i = 0; i < 14; ++i) {
-      if (i >= np) break;
-      const int kp = p0 + i;
+    for (int i = 0; i < np; ++i) {
+      const int kp = np * cg + i;
       const float v0 = mlp_enc_feature<EXACT>(2 * kp, u), v1 = mlp_enc_feature<EXACT>(2 * kp + 1, u);
       if constexpr (EXACT) {
         *reinterpret_cast<uint32_t*>(sm + a_buf(t, 0) + tc05::kmajor_offset(row, 2 * kp, 12, 2)) =
@@ -242,12 +246,12 @@ k_mlp_forward_tc05(MlpTcArgs a, const float* __restrict__ x0, int64_t N, float* 
     }
   };
 
-  // epilogue of a hidden layer of tile t: D (this thread's row, its 64
-  // columns) + bias, SiLU, into the next layer's A pieces
+  // epilogue of a hidden layer of tile t: D (this thread's row, its
+  // kGroupCols columns) + bias, SiLU, into the next layer's A pieces
   auto hidden = [&](int t, const float* bl) {
 #pragma unroll 1
-    for (int c = 0; c < 2; ++c) {
-      const int col0 = 64 * half + 32 * c;
+    for (int c = 0; c < kGroupCols / 32; ++c) {
+      const int col0 = kGroupCols * cg + 32 * c;
       float v[32];
       tc05::ld32(taddr_lane + (uint32_t)(t * kH + col0), v);
 #pragma unroll
@@ -298,7 +302,7 @@ k_mlp_forward_tc05(MlpTcArgs a, const float* __restrict__ x0, int64_t N, float* 
 #pragma unroll
     for (int t = 0; t < C::kTiles && ok; ++t) {
       if (!(ok = wait_tile(t))) break;
-      if (half == 0) {
+      if (cg == 0) {
         float o[16];
         tc05::ld16(taddr_lane + (uint32_t)(t * kH), o);
         const int64_t n = n0[t] + row;
