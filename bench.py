@@ -42,6 +42,7 @@ LAUNCHES_PER_MORPH = 9
 FP32_LANES_PER_SM = 128           # FP32 pipe width per SM per clock
 MUFU_EX2_PER_SM = 32              # measured ex2 throughput per SM per clock on GB300
 MUFU_SINCOS_PER_SM = 15.6         # measured sin (or cos) throughput per SM per clock on GB300
+MUFU_TANH_PER_SM = 15.2           # measured tanh.approx throughput per SM per clock on GB300
 MMA_TF32_PER_SM = 480.0           # measured mma.sync TF32 multiply-adds per SM per clock on GB300
 MLP_MACS_PER_SAMPLE = 39 * 128 + 2 * 128 * 128 + 128 * 3   # the surrogate network's multiply-adds per sample
 KERNEL_SOURCES = ["paper_2108_11775_gb300/csrc/morph_rbf_fast.cu", "paper_2108_11775_gb300/csrc/fast_tile.cuh",
@@ -652,16 +653,16 @@ def extra_surrogate(pdmp, torch, args):
     clk = torch.cuda.get_device_properties(0).multi_processor_count * float(
         peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6
     bf16_peak = float(peaks()[0].get("bf16_tflops", 1908.7)) * 1e12
-    # the network's non-tensor work per sample: 384 SiLU (an ex2 and a reciprocal each
-    # on the special-function unit) and 36 sin / cos of the encoding
-    mufu_peak_samples = clk * MUFU_EX2_PER_SM / (2 * 384 + 36)
+    # the network's special-function work per sample: 384 SiLU (one tanh each) and
+    # 36 sin / cos of the encoding
+    mufu_peak_samples = clk / (384 / MUFU_TANH_PER_SM + 36 / MUFU_SINCOS_PER_SM)
     mlp = {"samples_per_s": n_inf / t_net, "ms": 1e3 * t_net, "macs_per_sample": macs,
            "tflops": 2.0 * macs * n_inf / t_net / 1e12,
            "frac_of_bf16_peak": 2.0 * macs * n_inf / t_net / bf16_peak,
            "frac_of_mufu_bound": n_inf / t_net / mufu_peak_samples,
            "train_step_ms": train_step_ms, "train_batch": B,
-           "note": "bf16 peak: MEASURED_PEAKS.json bf16_tflops (cuBLAS, burst); MUFU bound: the SiLU and "
-                   "encoding's special-function operations per sample at 32 per SM per clock"}
+           "note": "bf16 peak: MEASURED_PEAKS.json bf16_tflops (cuBLAS, burst); MUFU bound: 384 tanh (SiLU) at "
+                   "15.2 and 36 sin/cos (encoding) at 15.6 per SM per clock, measured"}
     return {"speedup_vs_plain_morph": t_plain / t_sur, "ms_plain": 1e3 * t_plain, "ms_surrogate": 1e3 * t_sur,
             "check": "culled (r_cut = %.4g from eps = 1e-6)" % r_cut,
             "dense_check": {"ms_surrogate": 1e3 * t_sur_d, "speedup_vs_plain_morph": t_plain / t_sur_d,
