@@ -133,7 +133,11 @@ pdmp_status pdmp_selftest_stage_wait(const float* src, float* dst, int64_t limit
  * splits) and d = 8 takes a packed-pair path.  The RBF fast
  * path needs N < 2^31 (PDMP_ERR_INVALID_ARG otherwise).  Without a
  * workspace every feature is evaluated directly from x - mu (RBF) or
- * omega . x + b (RFF).
+ * omega . x + b (RFF).  With PDMP_RBF_TC05=1 in the environment the RBF
+ * fast path (d = 2, 3) takes a variant whose exponent a_m + b_m . u runs on
+ * the fifth-generation tensor cores (tcgen05.mma, TF32 hi/lo pieces, FP32
+ * accumulators in tensor memory) for groups of 256 samples; it is slower
+ * than the default on the measured workloads and kept for comparison.
  * Sample state stays on chip (registers or shared memory) for all T steps;
  * features are evaluated in
  * FP32 with exp2 / sin / cos on the special-function unit.  Calls that share

@@ -30,6 +30,14 @@ constexpr int kChainMax = 16;
 size_t cspace_workspace(int d, int64_t M, int n, int p, int64_t N);
 cudaError_t cspace_morph(const FieldArgs& fa, int kind, int n, int p, const float* base, const float* len,
                          const float* q0, int64_t N, int T, float eta, float* qT, void* ws, cudaStream_t st);
+// The fast RBF morph with the exponent on tcgen05 (d = 2, 3) over samples in
+// the sorted order perm (N < 2^31); eligible: whether the fast path takes it
+// (only with PDMP_RBF_TC05=1 in the environment: slower than the FP32 tile
+// kernel on the benchmarked workload).
+bool morph_rbf_tc05_eligible(int d, int64_t N);
+cudaError_t morph_rbf_tc05(int d, const FieldArgs& fa, const float* x0, const int32_t* perm, int64_t N, int T,
+                           float eta, float* xT, float* ckpt, int k, float* traj, float* steps, float* s_out,
+                           float* g_out, cudaStream_t st);
 // s_out (optional): the logit at the last step's state, per sample
 cudaError_t morph_rbf_fast(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float* xT,
                            float* ckpt, int k, float* traj, float* steps, void* ws, cudaStream_t st,

@@ -84,9 +84,11 @@ static cudaError_t launch_fast(const FieldArgs& fa, const float* x0, int64_t N, 
                                float* s_out, float* g_out = nullptr) {
   float4* tab = reinterpret_cast<float4*>(ws);
   SortWs sw = sort_layout((char*)ws + rbf_fast_table_bytes(D, fa.M), D, N);
-  k_rbf_table<D><<<(unsigned)((fa.M + 255) / 256), 256, 0, st>>>(fa.centres, fa.w, fa.M, tab);
   cudaError_t e = spatial_sort(D, x0, N, sw, st);
   if (e != cudaSuccess) return e;
+  if (morph_rbf_tc05_eligible(D, N))
+    return morph_rbf_tc05(D, fa, x0, sw.perm, N, T, eta, xT, ckpt, k, traj, steps, s_out, g_out, st);
+  k_rbf_table<D><<<(unsigned)((fa.M + 255) / 256), 256, 0, st>>>(fa.centres, fa.w, fa.M, tab);
   TileArgs a;
   a.tab = tab;
   a.M = fa.M;
