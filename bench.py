@@ -638,7 +638,7 @@ def extra_surrogate(pdmp, torch, args):
     t_sur = _time(torch, run_sur, reps=2)
     run_sur_dense()
     t_sur_d = _time(torch, run_sur_dense, reps=2)
-    # the plain morph culled the same way, for context (not the method the surrogate replaces)
+    # the plain morph culled the same way: the surrogate's check and fallback are culled too
     cws = torch.empty(pdmp.morph_culled_workspace(f, x0.shape[0]), dtype=torch.uint8, device="cuda")
     plain_c = torch.empty_like(x0)
     t_plain_c = _time(torch, lambda: pdmp.morph_culled(f, x0, T, eta, r_cut, out=plain_c, ws=cws), reps=1)
@@ -664,7 +664,8 @@ def extra_surrogate(pdmp, torch, args):
            "note": "bf16 peak: MEASURED_PEAKS.json bf16_tflops (cuBLAS, burst); MUFU bound: 384 tanh (SiLU) at "
                    "15.2 and 36 sin/cos (encoding) at 15.6 per SM per clock, measured"}
     return {"speedup_vs_plain_morph": t_plain / t_sur, "ms_plain": 1e3 * t_plain, "ms_surrogate": 1e3 * t_sur,
-            "check": "culled (r_cut = %.4g from eps = 1e-6)" % r_cut,
+            "speedup_vs_culled_plain_morph": t_plain_c / t_sur,
+            "check": "culled check and fallback (r_cut = %.4g from eps = 1e-6)" % r_cut,
             "dense_check": {"ms_surrogate": 1e3 * t_sur_d, "speedup_vs_plain_morph": t_plain / t_sur_d,
                             "fallback_fraction": res["nf_dense"] / x0.shape[0], "collision_rate": c_sur_d},
             "context_culled_plain_morph": {"ms": 1e3 * t_plain_c, "speedup_of_surrogate": t_plain_c / t_sur},

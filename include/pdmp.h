@@ -317,14 +317,14 @@ pdmp_status pdmp_surrogate_infer(const pdmp_mlp* net, const pdmp_field* f, const
                                  float eta, float tau_r, float* xT, int64_t* n_fallback, void* ws, size_t ws_bytes,
                                  void* stream);
 
-/* pdmp_surrogate_infer with the residual check on the spatially culled
- * kernel (pdmp_morph_culled's features within r_cut of a tile; r_cut > 0
- * and finite, else PDMP_ERR_INVALID_ARG).  With r_cut from
- * pdmp_cull_radius(f, eps), the checked logit and |grad s| are within eps of
- * the dense check's, so only samples within that margin of the thresholds
- * (s = 0, step length = tau_r) can be decided differently; the step is taken
- * as -eta grad c at the prediction.  The fallback is the plain (dense) morph,
- * as there.  Same workspace. */
+/* pdmp_surrogate_infer on the spatially culled kernel (pdmp_morph_culled's
+ * features within r_cut of a tile; r_cut > 0 and finite, else
+ * PDMP_ERR_INVALID_ARG), for the residual check and for the fallback.  With
+ * r_cut from pdmp_cull_radius(f, eps), the checked logit and |grad s| are
+ * within eps of the dense check's, so only samples within that margin of the
+ * thresholds (s = 0, step length = tau_r) can be decided differently; the
+ * step is taken as -eta grad c at the prediction.  Failed samples are morphed
+ * by pdmp_morph_culled with the same r_cut.  Same workspace. */
 pdmp_status pdmp_surrogate_infer_culled(const pdmp_mlp* net, const pdmp_field* f, const float* x0, int64_t N,
                                         int32_t T, float eta, float tau_r, float r_cut, float* xT,
                                         int64_t* n_fallback, void* ws, size_t ws_bytes, void* stream);

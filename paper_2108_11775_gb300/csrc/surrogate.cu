@@ -159,7 +159,13 @@ cudaError_t surrogate_infer(const pdmp_mlp* net, int d, const FieldArgs& fa, con
   if (cnt == 0) return cudaGetLastError();
   const unsigned gb = (unsigned)((cnt * d + 255) / 256);
   k_gather<<<gb, 256, 0, st>>>(x0, w.idx, cnt, d, w.xs);
-  if ((e = morph_rbf_fast(d, fa, w.xs, cnt, T, eta, w.ys, nullptr, 0, nullptr, nullptr, w.fast, st))) return e;
+  // the fallback: the plain morph of the failed samples, culled like the
+  // check when r_cut > 0
+  if (r_cut > 0.0f)
+    e = morph_rbf_cull(d, fa, w.xs, cnt, T, eta, r_cut, w.ys, nullptr, 0, w.fast, nullptr, st);
+  else
+    e = morph_rbf_fast(d, fa, w.xs, cnt, T, eta, w.ys, nullptr, 0, nullptr, nullptr, w.fast, st);
+  if (e) return e;
   k_scatter_rows<<<gb, 256, 0, st>>>(w.ys, w.idx, cnt, d, xT);
   return cudaGetLastError();
 }

@@ -212,9 +212,8 @@ def test_culled_residual_check_matches_the_dense_check():
     (r_cut from cull_radius(f, 1e-6)) decides like the dense check except for
     samples within the culling margin of a threshold (s = 0 or step length =
     tau_r); accepted samples are the network's predictions and fallen-back
-    ones the plain morph (within rounding: the fallback morphs its own subset,
-    in other tiles), and the two calls' outputs are equal bit for bit where
-    the checks agree on the whole fallback set."""
+    ones the culled morph (bit for bit when every sample falls back), within
+    the culled kernel's 1e-4 of the dense plain morph."""
     wk, fld, eta, T = _small_world(M=768)
     N = 20000
     x0 = torch.from_numpy(wl.uniform_box(23, 3, N, LO, HI)).cuda()
@@ -226,10 +225,12 @@ def test_culled_residual_check_matches_the_dense_check():
     s = q["s"].cpu().numpy()
     slen = (eta * q["grad"]).norm(dim=1).cpu().numpy()
     plain = pdmp.morph(fld, x0, T, eta)
+    culled = pdmp.morph_culled(fld, x0, T, eta, r_cut)
     # tau_r = 0: every sample falls back under both checks
     oc, nc = net.infer(fld, x0, T, eta, 0.0, r_cut=r_cut)
     od, nd = net.infer(fld, x0, T, eta, 0.0)
-    assert nc == nd == N and torch.equal(oc, od) and torch.equal(oc, plain)
+    assert nc == nd == N and torch.equal(od, plain) and torch.equal(oc, culled)
+    assert (oc - od).abs().max().item() <= 1e-4
     for tau in (1e9, float(np.median(slen[s < 0]))):
         od, nd = net.infer(fld, x0, T, eta, tau)
         oc, nc = net.infer(fld, x0, T, eta, tau, r_cut=r_cut)
@@ -243,9 +244,9 @@ def test_culled_residual_check_matches_the_dense_check():
         o_c, o_d, p_ = oc.cpu().numpy(), od.cpu().numpy(), plain.cpu().numpy()
         same = ~differ
         assert np.array_equal(o_c[same & ~fc], pred.cpu().numpy()[same & ~fc])
-        # the fallback morphs its own subset, whose tiles differ from the full set's
-        assert np.abs(o_c[same & fc] - p_[same & fc]).max() <= 1e-5
-        assert np.abs(o_c[same] - o_d[same]).max() <= (0.0 if not differ.any() else 1e-5)
+        # the fallback morphs its own subset (other tiles), on the culled kernel
+        assert np.abs(o_c[same & fc] - p_[same & fc]).max() <= 1e-4
+        assert np.abs(o_c[same] - o_d[same]).max() <= 1e-4
     L = pdmp._mlp_sigs()
     m, f = net.struct(), fld.struct()
     ws = torch.empty(int(L.pdmp_surrogate_workspace(ctypes.byref(f), N)), dtype=torch.uint8, device="cuda")
