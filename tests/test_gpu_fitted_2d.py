@@ -175,3 +175,28 @@ def test_log_density_in_one_kernel_at_the_bench_size(fitted):
     rl, _, _ = oracle.logdet(wk.field, yh[idx], T, eta)
     assert np.abs(lp[idx] - (-log_vol - rl)).max() <= 1e-4 * T
     assert np.abs(rl).max() > 1e-3
+
+
+def test_tensor_core_morph_per_step_and_final_at_full_size(fitted, monkeypatch):
+    """The opt-in tensor-core form (PDMP_RBF_TC05=1: the exponent on tcgen05)
+    on the benchmarked field at full size: each of the 50 steps of 200
+    sampled samples at the per-step tolerance, their x_T against the oracle's
+    chain (1e-4), and every x_T within 1e-4 of the default FP32 kernel's."""
+    wk, params, eta, fld = fitted
+    N, T = wk.x0.shape[0], wk.T
+    x0 = dev(wk.x0)
+    monkeypatch.setenv("PDMP_RBF_TC05", "0")
+    xT_fp32 = pdmp.morph(fld, x0, T, eta)
+    monkeypatch.setenv("PDMP_RBF_TC05", "1")
+    traj, steps = pdmp.morph_trace(fld, x0, T, eta)
+    xT = pdmp.morph(fld, x0, T, eta)
+    assert torch.equal(traj[-1], xT), "the trace twin and the timed kernel disagree"
+    assert (xT - xT_fp32).abs().max().item() <= 1e-4
+    idx = sample_idx(N, 200, 23)
+    it = torch.from_numpy(idx).cuda()
+    tr = traj[:, it].cpu().numpy()
+    st = steps[:, it].cpu().numpy()
+    del traj, steps
+    assert per_step_check(wk.field, tr, st, eta) <= 1.0
+    ref = oracle.morph(wk.field, wk.x0[idx], T, eta)
+    assert max_abs(tr[-1], ref) <= 1e-4
