@@ -10,7 +10,9 @@ algebra fails here as well as in the GPU parity tests:
 * RFF tensor-core VJP: (Hess s) v = 2 pi sum_m cos(theta_m) (omega_m . v / 2 pi)(-w_m omega_m);
 * the sorted tiles' weight-gradient pass: cA phi_m + cB grad phi_m . g =
   phi_m (alpha + beta . c_m) with alpha = cA - 2 gamma cB (u . g) and
-  beta = 2 gamma cB g."""
+  beta = 2 gamma cB g;
+* the tensor-core RBF form: its TF32 K slots sum to the expanded exponent
+  a + b . u, and its weighted records' moments give s and grad s."""
 import numpy as np
 import pytest
 
@@ -111,3 +113,60 @@ def test_rbf_weight_gradient_terms(d):
         alpha = cA - 2.0 * gamma * cB * (u @ g)
         beta = 2.0 * gamma * cB * g
         np.testing.assert_allclose(phi * (alpha + c @ beta), plain, rtol=1e-12, atol=1e-14)
+
+
+def _tf32(v):
+    """round to TF32 (10 explicit mantissa bits), nearest with ties away, as
+    cvt.rna.tf32.f32 does on a float32 input"""
+    b = np.asarray(v, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x1000) & 0xFFFFE000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _tc05_rows(a, b, u):
+    """The tensor-core form's K slots: A row (sample) [1, 1, u_jh, u_jh, u_jl ..]
+    and B row (centre) [a_h, a_l, b_jh, b_jl, b_jh ..], each a TF32 piece of
+    the FP32 value."""
+    A, B = [1.0, 1.0], [_tf32(a), _tf32(np.float32(a) - np.float32(_tf32(a)))]
+    for uj, bj in zip(u, b):
+        uh, bh = _tf32(uj), _tf32(bj)
+        A += [uh, uh, _tf32(np.float32(uj) - np.float32(uh))]
+        B += [bh, _tf32(np.float32(bj) - np.float32(bh)), bh]
+    return np.array(A, np.float64), np.array(B, np.float64)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_tc05_slots_give_the_expanded_exponent_and_the_weighted_records_the_moments(d):
+    """morph_rbf_tc05.cu: the K-slot products sum to a + b . u (a = -g'|c|^2,
+    b = 2 g' c) to about 2^-21 of |a| + |b . u| (only the lo x lo products are
+    left out), while dropping any one slot breaks that; and the moments it sums
+    with the weights in the records, S = sum w e, G = sum w e c, give s and
+    grad s exactly as the plain definitions."""
+    f = wl.random_field(21 + d, wl.RBF, d, 200, lo=0.0, hi=3.0, gamma=4.0, wscale=1.5, bias=0.1)
+    rng = np.random.default_rng(5 + d)
+    mu, w, gamma = f.centres.astype(np.float64), f.w.astype(np.float64), float(f.gamma)
+    gl2e = gamma * LOG2E
+    for _ in range(4):
+        o = rng.uniform(0.8, 2.2, d)
+        x = o + rng.uniform(-0.25, 0.25, d)
+        u, c = x - o, mu - o
+        a = -gl2e * (c * c).sum(1)
+        b = 2.0 * gl2e * c
+        for m in range(0, mu.shape[0], 17):
+            A, B = _tc05_rows(np.float32(a[m]), b[m].astype(np.float32), u.astype(np.float32))
+            exact = float(np.float32(a[m])) + float(b[m].astype(np.float32).astype(np.float64) @ u.astype(np.float32))
+            scale = abs(a[m]) + abs(b[m] @ u)
+            assert abs(A @ B - exact) <= 2.0 ** -20 * scale
+            for k in range(2, A.size):                  # every u, b slot carries its share
+                drop = A.copy()
+                drop[k] = 0.0
+                if abs(A[k] * B[k]) > 2.0 ** -16 * scale:
+                    assert abs(drop @ B - exact) > 2.0 ** -20 * scale
+        e = np.exp2(a + b @ u)                            # e_m = 2^(a_m + b_m . u)
+        f_u = np.exp2(-gl2e * (u @ u))
+        S, G = (w * e).sum(), (w * e) @ c                 # the weighted records' sums
+        s_k = f_u * S + f.bias
+        grad_k = -2.0 * gamma * f_u * (u * S - G)
+        s, gs, _ = _plain_s(f, x)
+        assert abs(s_k - s) <= 1e-12 * max(1.0, abs(s))
+        np.testing.assert_allclose(grad_k, gs, rtol=0, atol=1e-11 * max(1.0, np.abs(gs).max()))
