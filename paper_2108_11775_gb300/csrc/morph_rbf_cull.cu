@@ -32,9 +32,9 @@ __host__ __device__ constexpr int64_t cull_cell_capacity() {
   return D == 2 ? (int64_t)512 * 512 : (int64_t)64 * 64 * 64;
 }
 
-template <int D>
+template <int D, int K>
 __host__ __device__ constexpr size_t cull_smem_bytes() {
-  return fast_smem_bytes<D, 4, 8>() + (size_t)4 * kCullRowWords * sizeof(uint32_t);
+  return fast_smem_bytes<D, 4, K>() + (size_t)4 * kCullRowWords * sizeof(uint32_t);
 }
 
 // cell index of v along axis j (values outside the grid, and NaN, clamp to it)
@@ -250,14 +250,28 @@ __device__ __forceinline__ void cull_tile(const TileArgs& a, const CullGrid& g, 
   tile_store<D, K, false>(a, p0, act, x, warp, lane);
 }
 
-template <int D>
-__global__ void __launch_bounds__(Shape<4, 8>::kThreads, Shape<4, 8>::kMinBlocks)
+template <int D, int K>
+__global__ void __launch_bounds__(Shape<4, K>::kThreads, Shape<4, K>::kMinBlocks)
 k_morph_rbf_cull(TileArgs a, const CullGrid* __restrict__ grid, const uint32_t* __restrict__ start,
                  unsigned long long* work) {
   extern __shared__ __align__(16) unsigned char smem[];
   const CullGrid g = *grid;
-  const int64_t p0 = (int64_t)blockIdx.x * Shape<4, 8>::kTile;
-  cull_tile<D, 4, 8>(a, g, start, p0, a.N, smem, work);
+  const int64_t p0 = (int64_t)blockIdx.x * Shape<4, K>::kTile;
+  cull_tile<D, 4, K>(a, g, start, p0, a.N, smem, work);
+}
+
+// Samples per lane: 8 (256-sample tiles, 4 blocks per SM), and 4 (128-sample
+// tiles) for launches of fewer than two waves of the larger ones.
+template <int D, int K>
+static cudaError_t launch_cull_shape(const TileArgs& a, const CullGrid* grid, const uint32_t* offs,
+                                     unsigned long long* work, cudaStream_t st) {
+  constexpr size_t smem = cull_smem_bytes<D, K>();
+  cudaError_t e =
+      cudaFuncSetAttribute(k_morph_rbf_cull<D, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((a.N + Shape<4, K>::kTile - 1) / Shape<4, K>::kTile);
+  k_morph_rbf_cull<D, K><<<blocks, Shape<4, K>::kThreads, smem, st>>>(a, grid, offs, work);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ host
@@ -327,12 +341,13 @@ static cudaError_t launch_cull(const FieldArgs& fa, const float* x0, int64_t N, 
   a.kck = k;
   a.s_out = s_out;
   a.g_out = g_out;
-  constexpr size_t smem = cull_smem_bytes<D>();
-  e = cudaFuncSetAttribute(k_morph_rbf_cull<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((N + Shape<4, 8>::kTile - 1) / Shape<4, 8>::kTile);
-  k_morph_rbf_cull<D><<<blocks, Shape<4, 8>::kThreads, smem, st>>>(a, c.grid, c.offs, work);
-  return cudaGetLastError();
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms < 1)
+    sms = 152;
+  const int64_t tiles = (N + Shape<4, 8>::kTile - 1) / Shape<4, 8>::kTile;
+  if (tiles < 2 * (int64_t)Shape<4, 8>::kMinBlocks * sms) return launch_cull_shape<D, 4>(a, c.grid, c.offs, work, st);
+  return launch_cull_shape<D, 8>(a, c.grid, c.offs, work, st);
 }
 
 cudaError_t morph_rbf_cull(int d, const FieldArgs& fa, const float* x0, int64_t N, int T, float eta, float r_cut,
