@@ -289,13 +289,28 @@ __device__ __forceinline__ void inverse_tile(const TileArgs& a, float tol, int m
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(FastShape::kThreads, FastShape::kMinBlocks)
+template <int D, int K>
+__global__ void __launch_bounds__(Shape<4, K>::kThreads, Shape<4, K>::kMinBlocks)
 k_morph_inverse_fast(TileArgs a, float tol, int maxit, int32_t* __restrict__ iters,
                      unsigned long long* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t p0 = (int64_t)blockIdx.x * FastShape::kTile;
-  inverse_tile<D, FastShape::kWarps, FastShape::kK>(a, tol, maxit, iters, work, p0, a.N, smem);
+  const int64_t p0 = (int64_t)blockIdx.x * Shape<4, K>::kTile;
+  inverse_tile<D, 4, K>(a, tol, maxit, iters, work, p0, a.N, smem);
+}
+
+// Samples per lane: 10 (320-sample tiles, 3 blocks per SM), and 4 (128-sample
+// tiles, 4 blocks per SM) for launches of fewer than two waves of the larger
+// ones, which then fill the GPU and stop iterating tile by tile.
+template <int D, int K>
+static cudaError_t launch_inverse_shape(const TileArgs& a, float tol, int maxit, int32_t* iters,
+                                        unsigned long long* work, cudaStream_t st) {
+  constexpr size_t smem = fast_smem_bytes<D, 4, K>() + 3 * (size_t)Shape<4, K>::kTile * D * sizeof(float);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_morph_inverse_fast<D, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((a.N + Shape<4, K>::kTile - 1) / Shape<4, K>::kTile);
+  k_morph_inverse_fast<D, K><<<blocks, Shape<4, K>::kThreads, smem, st>>>(a, tol, maxit, iters, work);
+  return cudaGetLastError();
 }
 
 template <int D>
@@ -319,13 +334,13 @@ static cudaError_t launch_inverse_fast(const FieldArgs& fa, const float* z, int6
   a.perm_base = 0;
   a.N = N;
   a.xT = y;
-  constexpr size_t smem =
-      fast_smem_bytes<D, FastShape::kWarps, FastShape::kK>() + 3 * (size_t)FastShape::kTile * D * sizeof(float);
-  e = cudaFuncSetAttribute(k_morph_inverse_fast<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((N + FastShape::kTile - 1) / FastShape::kTile);
-  k_morph_inverse_fast<D><<<blocks, FastShape::kThreads, smem, st>>>(a, tol, maxit, iters, work);
-  return cudaGetLastError();
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms < 1)
+    sms = 152;
+  const int64_t tiles = (N + FastShape::kTile - 1) / FastShape::kTile;
+  if (tiles < 2 * (int64_t)FastShape::kMinBlocks * sms) return launch_inverse_shape<D, 4>(a, tol, maxit, iters, work, st);
+  return launch_inverse_shape<D, FastShape::kK>(a, tol, maxit, iters, work, st);
 }
 
 // ---------------------------------------------------------------- direct

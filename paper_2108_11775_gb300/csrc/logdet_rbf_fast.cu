@@ -18,27 +18,29 @@
 
 namespace pdmp {
 
-template <int D>
+template <int D, int KK = (D == 2 ? 8 : 6)>
 struct LdRbf {
   static constexpr int kH = D * (D + 1) / 2;             // lower-triangle entries
   static constexpr int kUsed = 2 * D + 2 + kH;           // u64 pairs a record uses
   static constexpr int kPairs = (kUsed + 1) / 2 * 2;     // padded to whole 16-byte chunks
   static constexpr int kSums = 1 + D + kH;               // S, G, H per sample
-  static constexpr int kK = D == 2 ? 8 : 6;              // samples per lane
+  static constexpr int kK = KK;                          // samples per lane (8 for d = 2, 6 for d = 3)
   static constexpr int kW = 4;                           // warps per tile
   static constexpr int kTile = 32 * kK;
 };
+template <int D>
+constexpr int kLdK = LdRbf<D>::kK;
 
-template <int D>
+template <int D, int K = kLdK<D>>
 __host__ __device__ constexpr size_t ld_rbf_region0() {
-  return (size_t)LdRbf<D>::kW * 2 * kWarpStage * LdRbf<D>::kPairs * 8 >
-                 (size_t)LdRbf<D>::kW * LdRbf<D>::kSums * LdRbf<D>::kTile * 4
-             ? (size_t)LdRbf<D>::kW * 2 * kWarpStage * LdRbf<D>::kPairs * 8
-             : (size_t)LdRbf<D>::kW * LdRbf<D>::kSums * LdRbf<D>::kTile * 4;
+  using L = LdRbf<D, K>;
+  return (size_t)L::kW * 2 * kWarpStage * L::kPairs * 8 > (size_t)L::kW * L::kSums * L::kTile * 4
+             ? (size_t)L::kW * 2 * kWarpStage * L::kPairs * 8
+             : (size_t)L::kW * L::kSums * L::kTile * 4;
 }
-template <int D>
+template <int D, int K = kLdK<D>>
 __host__ __device__ constexpr size_t ld_rbf_smem() {
-  return ld_rbf_region0<D>() + (size_t)LdRbf<D>::kW * kWarpStage * FastRec<D>::kTab * sizeof(float4);
+  return ld_rbf_region0<D, K>() + (size_t)LdRbf<D, K>::kW * kWarpStage * FastRec<D>::kTab * sizeof(float4);
 }
 
 // lower-triangle entry q <-> (a, b), a >= b
@@ -177,15 +179,15 @@ __device__ __forceinline__ void ld_stage_accumulate(const u64* rec, bool expande
 // the expanded form, with its origin in o.  Ends with a block barrier after
 // the sums are written; the caller must pass another barrier before the next
 // sweep rebuilds the stages.
-template <int D>
-__device__ __forceinline__ bool ld_sweep(const TileArgs& a, const float (&x)[LdRbf<D>::kK][D],
-                                         const bool (&act)[LdRbf<D>::kK], float (&o)[D], unsigned char* smem,
-                                         int warp, int lane) {
-  constexpr int W = LdRbf<D>::kW, K = LdRbf<D>::kK, P = K / 2, RP = LdRbf<D>::kPairs, NH = LdRbf<D>::kH;
-  constexpr int NS = LdRbf<D>::kSums, kTile = LdRbf<D>::kTile, KT = FastRec<D>::kTab;
+template <int D, int K = kLdK<D>>
+__device__ __forceinline__ bool ld_sweep(const TileArgs& a, const float (&x)[K][D], const bool (&act)[K],
+                                         float (&o)[D], unsigned char* smem, int warp, int lane) {
+  using L = LdRbf<D, K>;
+  constexpr int W = L::kW, P = K / 2, RP = L::kPairs, NH = L::kH;
+  constexpr int NS = L::kSums, kTile = L::kTile, KT = FastRec<D>::kTab;
   u64* wbuf = reinterpret_cast<u64*>(smem) + (size_t)warp * 2 * kWarpStage * RP;
   float* red = reinterpret_cast<float*>(smem);
-  float4* wraw = reinterpret_cast<float4*>(smem + ld_rbf_region0<D>()) + (size_t)warp * kWarpStage * KT;
+  float4* wraw = reinterpret_cast<float4*>(smem + ld_rbf_region0<D, K>()) + (size_t)warp * kWarpStage * KT;
   const int64_t M = a.M;
   const float gl2e = a.gamma * kLog2e;
   const int64_t Mw = ((M + W - 1) / W + kWarpStage - 1) / kWarpStage * kWarpStage;
@@ -244,11 +246,12 @@ __device__ __forceinline__ bool ld_sweep(const TileArgs& a, const float (&x)[LdR
 
 // Sample k of this lane after ld_sweep: s - bias (shat), grad s (gs) and the
 // lower triangle of Hess s (hs) at x.
-template <int D>
+template <int D, int K = kLdK<D>>
 __device__ __forceinline__ void ld_sample_terms(const float* red, int k, int lane, const float (&x)[D],
                                                 const float (&o)[D], bool expanded, float gamma, float& shat,
                                                 float (&gs)[D], float (&hs)[D][D]) {
-  constexpr int W = LdRbf<D>::kW, NH = LdRbf<D>::kH, NS = LdRbf<D>::kSums, kTile = LdRbf<D>::kTile;
+  using L = LdRbf<D, K>;
+  constexpr int W = L::kW, NH = L::kH, NS = L::kSums, kTile = L::kTile;
   const float gl2e = gamma * kLog2e;
   float sum[NS];
 #pragma unroll
@@ -375,17 +378,17 @@ k_logdet_rbf_fast(TileArgs a, float* __restrict__ logdet) {
 // sorted-tile inverse (z + 2 delta_{t+1} - delta_{t+2} once two corrections
 // are known).  a.x0 holds z; a.xT receives y = phi^{-1}(z); logdet receives
 // sum_t log det J_t.
-template <int D>
-__global__ void __launch_bounds__(LdRbf<D>::kW * 32, 3)
+template <int D, int K>
+__global__ void __launch_bounds__(LdRbf<D, K>::kW * 32, 3)
 k_log_density_rbf_fast(TileArgs a, float tol, int maxit, float* __restrict__ logdet, int32_t* __restrict__ iters,
                        unsigned long long* __restrict__ work) {
-  constexpr int K = LdRbf<D>::kK, kTile = LdRbf<D>::kTile;
+  constexpr int kTile = LdRbf<D, K>::kTile;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float* red = reinterpret_cast<const float*>(smem);
   const int64_t p0 = (int64_t)blockIdx.x * kTile;
   const float eta = a.eta;
-  float* zs = reinterpret_cast<float*>(smem + ld_rbf_smem<D>());   // kTile x D: the step's target z
+  float* zs = reinterpret_cast<float*>(smem + ld_rbf_smem<D, K>());   // kTile x D: the step's target z
   float* ds = zs + kTile * D;    // the corrections of the two steps undone before, kTile x D each
   float* ds2 = ds + kTile * D;
 
@@ -425,12 +428,12 @@ k_log_density_rbf_fast(TileArgs a, float tol, int maxit, float* __restrict__ log
     bool moving = true;
     while (moving && it < maxit) {
       float o[D];
-      const bool expanded = ld_sweep<D>(a, y, act, o, smem, warp, lane);
+      const bool expanded = ld_sweep<D, K>(a, y, act, o, smem, warp, lane);
       bool mv = false;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         float shat, gs[D], hs[D][D];
-        ld_sample_terms<D>(red, k, lane, y[k], o, expanded, a.gamma, shat, gs, hs);
+        ld_sample_terms<D, K>(red, k, lane, y[k], o, expanded, a.gamma, shat, gs, hs);
         float d1, d2;
         sigmoid_d12(shat + a.bias, d1, d2);
         ld[k] = step_logdet<D>(d1, d2, gs, hs, eta);
@@ -515,6 +518,18 @@ static cudaError_t launch_logdet_rbf_fast(const FieldArgs& fa, const float* x0, 
   return cudaGetLastError();
 }
 
+template <int D, int K>
+static cudaError_t launch_log_density_shape(const TileArgs& a, float tol, int maxit, float* ld, int32_t* iters,
+                                            unsigned long long* work, cudaStream_t st) {
+  constexpr size_t smem = ld_rbf_smem<D, K>() + 3 * (size_t)LdRbf<D, K>::kTile * D * sizeof(float);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_log_density_rbf_fast<D, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((a.N + LdRbf<D, K>::kTile - 1) / LdRbf<D, K>::kTile);
+  k_log_density_rbf_fast<D, K><<<blocks, LdRbf<D, K>::kW * 32, smem, st>>>(a, tol, maxit, ld, iters, work);
+  return cudaGetLastError();
+}
+
 template <int D>
 static cudaError_t launch_log_density_rbf_fast(const FieldArgs& fa, const float* z, int64_t N, int T, float eta,
                                                float tol, int maxit, float* y, float* ld, int32_t* iters,
@@ -536,12 +551,15 @@ static cudaError_t launch_log_density_rbf_fast(const FieldArgs& fa, const float*
   a.perm_base = 0;
   a.N = N;
   a.xT = y;
-  constexpr size_t smem = ld_rbf_smem<D>() + 3 * (size_t)LdRbf<D>::kTile * D * sizeof(float);
-  e = cudaFuncSetAttribute(k_log_density_rbf_fast<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((N + LdRbf<D>::kTile - 1) / LdRbf<D>::kTile);
-  k_log_density_rbf_fast<D><<<blocks, LdRbf<D>::kW * 32, smem, st>>>(a, tol, maxit, ld, iters, work);
-  return cudaGetLastError();
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms < 1)
+    sms = 152;
+  // 128-sample tiles for launches of fewer than two waves of the larger ones
+  // (3 blocks per SM), which then fill the GPU and stop iterating tile by tile
+  const int64_t tiles = (N + LdRbf<D>::kTile - 1) / LdRbf<D>::kTile;
+  if (tiles < 2 * 3 * (int64_t)sms) return launch_log_density_shape<D, 4>(a, tol, maxit, ld, iters, work, st);
+  return launch_log_density_shape<D, kLdK<D>>(a, tol, maxit, ld, iters, work, st);
 }
 
 cudaError_t log_density_rbf_fast(int d, const FieldArgs& fa, const float* z, int64_t N, int T, float eta, float tol,
