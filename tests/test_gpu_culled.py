@@ -108,13 +108,15 @@ def test_culled_edges_outside_box_ragged_in_place_and_checkpoints():
         assert max_abs(ck[0].cpu().numpy(), refk) <= 1e-4
 
 
-def test_culled_fitted_shape_sampled_at_scale():
-    """2^18 samples of the fitted-like 2-D field (16,384 centres, T = 50),
-    the launch configuration of the throughput measurement, on sampled outputs."""
+@pytest.mark.parametrize("N", [1 << 18, 1 << 19])
+def test_culled_fitted_shape_sampled_at_scale(N):
+    """The fitted-like 2-D field (16,384 centres, T = 50) on sampled outputs:
+    2^18 samples (the throughput measurement's size; under two waves of
+    256-sample tiles, so the kernel takes 128-sample tiles) and 2^19 (256)."""
     f, lo, hi = fitted_like_2d()
     eta, L = rbf_eta(f, lo - 0.5, hi + 0.5, cells=128)
     fld = pdmp.DeviceField.from_host(f, lipschitz=L)
-    N, T = 1 << 18, 50
+    T = 50
     x0 = wl.uniform_box(7, 3, N, lo, hi)
     r, _ = pdmp.cull_radius(fld, 1e-6)
     xc = pdmp.morph_culled(fld, dev(x0), T, eta, r).cpu().numpy()

@@ -661,6 +661,38 @@ def test_inverse_sorted_tiles_ragged_in_place_and_work(d, N):
     assert np.abs(zc.cpu().numpy() - x0).max() > 1e-3
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_inverse_and_log_density_large_launch_tiles(d):
+    """2^19 samples: enough tiles that the sorted-tile inverse (320-sample
+    tiles) and the one-kernel log-density (256 / 192) keep their larger tiles
+    (smaller launches take 128-sample tiles). Sampled points against the
+    oracle's inverse (1e-4) and its log-det at the recovered points (abs
+    1e-4 T); the inverse also against the direct kernel on those points."""
+    lo, hi = np.zeros(d), np.full(d, 10.0)
+    fld_h = wl.random_field(60 + d, wl.RBF, d, 500, gamma=2.0, wscale=2.0, bias=-0.5)
+    eta, _ = rbf_eta(fld_h, lo - 1.0, hi + 1.0, cells=32 if d == 2 else 10)
+    T, N = 6, 1 << 19
+    fld = pdmp.DeviceField.from_host(fld_h)
+    x0 = wl.uniform_box(61 + d, 3, N, lo, hi)
+    z = pdmp.morph(fld, dev(x0), T, eta)
+    y = pdmp.morph_inverse(fld, z, T, eta, tol=1e-6, maxit=60).cpu().numpy()
+    lp, yl = pdmp.log_density(fld, z, T, eta, lo, hi, tol=1e-6, maxit=60)
+    lp, yl = lp.cpu().numpy(), yl.cpu().numpy()
+    idx = np.sort(wl.rng(62 + d, 1).choice(N, 48, replace=False))
+    zs = z.cpu().numpy()[idx]
+    ry, _ = oracle.morph_inverse(fld_h, zs, T, eta, tol=1e-13, maxit=200)
+    assert max_abs(y[idx], ry) <= 1e-4 and max_abs(yl[idx], ry) <= 1e-4
+    yd = pdmp.morph_inverse(fld, dev(zs), T, eta, tol=1e-6, maxit=60, fast=False).cpu().numpy()
+    assert max_abs(y[idx], yd) <= 1e-4
+    inside = np.all((yl[idx] > lo + 1e-3) & (yl[idx] < hi - 1e-3), axis=1)
+    sel = idx[inside]
+    rl, _, mindet = oracle.logdet(fld_h, yl[sel], T, eta)
+    assert np.all(mindet > 0) and sel.size > 30
+    log_vol = float(np.log(np.prod(hi - lo)))
+    assert np.abs(lp[sel] - (-log_vol - rl)).max() <= 1e-4 * T
+    assert pdmp.stream_status()[0] == 0
+
+
 @pytest.mark.parametrize("d,N", [(7, 257), (3, 300)])
 def test_inverse_tensor_cores_rff(d, N):
     """RFF, d <= 7, with the workspace: the inverse on the tensor cores
